@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark: time to a 1e-4 relative KKT residual of the GeNIOS solver on one GB300, with the
+fused Hessian-vector rowpass's achieved HBM bandwidth, plain (FP32) vs mixed (BF16 / FP8 Hessian
+streams).
+
+One step = one full solve from x = z = u = 0 (gradient passes, Nystrom sketches, PCG with fused
+Hv, z/u updates, residual / KKT checks) on the default workload: l1-logistic regression,
+A 20000 x 8000 low rank (50) + 0.1 noise, 400-sparse truth, lambda = 0.02 lambda_max, Nystrom
+rank 100 (A is 640 MB in FP32, larger than the 129 MB L2, so no flush is needed between steps).
+
+Contract: prints ONE JSON line on rank 0.  Under torchrun (N > 1) every rank solves its own
+replica (its own seed), no collective on the data path: "scaling": "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import problems  # noqa: E402
+
+METRIC = "time-to-1e-4 KKT solve & Hv HBM GB/s: plain vs mixed/batched, same GB300"
+WORKLOADS = {
+    # name: (generator kwargs, rho, description)
+    "logistic_20000x8000": (dict(m=20000, n=8000), 30.0,
+                            "l1-logistic 20000x8000 low-rank(50)+0.1 noise, 400 nnz, lambda=0.02 lambda_max, rank 100"),
+    "lasso_1000x10000": (None, 1.0, "Lasso 1000x10000 AR(1) rows, 200 nnz, lambda=0.05 lambda_max, rank 50"),
+}
+PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def make_problem(name: str, seed_k: int = 0):
+    if name == "logistic_20000x8000":
+        return problems.logistic_lowrank(20000, 8000, k=seed_k)
+    if name == "lasso_1000x10000":
+        return problems.lasso_ar1(k=seed_k)
+    raise ValueError(name)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return PEAK_FALLBACK, "fallback"
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ------------------------------------------------------------------------------------------
+def oracle_baseline(P, lam: float, rho: float, budget_s: float = 25.0) -> dict:
+    """Estimate the float64 oracle's time to a 1e-4 relative KKT residual on this workload:
+    (seconds per exact-solve ADMM iteration, timed at full size) x (iterations the oracle needs
+    to reach 1e-4 on a 1/5-scale instance of the same generator).  Both legs run the oracle
+    unchanged; the sample is bounded to about `budget_s` seconds."""
+    from oracle import admm, checks
+    cores = os.cpu_count()
+    A = P.A
+    b = P.b
+    t0 = time.perf_counter()
+    r = admm.solve(A, b, P.loss, lam, P.mu, rho=rho, max_iter=2, check_every=10 ** 9,
+                   polish_below=None, rho_update_every=0)
+    per_iter = (time.perf_counter() - t0) / max(1, r["iters"])
+    # iteration count on a reduced instance of the same structure
+    if P.loss == "logistic":
+        Ps = problems.logistic_lowrank(P.m // 5, P.n // 5, nnz=80, seed=problems.seed_for(3, 77))
+    else:
+        Ps = problems.lasso_ar1(P.m // 5, P.n // 5, nnz=40, seed=problems.seed_for(2, 77))
+    lam_s = Ps.lam_frac * checks.lambda_max(Ps.A, Ps.b, Ps.loss)
+    t1 = time.perf_counter()
+    rs = admm.solve(Ps.A, Ps.b, Ps.loss, lam_s, Ps.mu, rho=rho, tol=1e-4, max_iter=3000,
+                    check_every=1, polish_below=None, time_limit=budget_s)
+    small_t = time.perf_counter() - t1
+    iters = rs["iters"]
+    return {"value": per_iter * iters, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": (f"2 exact-solve ADMM iterations at full size ({per_iter:.2f} s/iter, float64 "
+                       f"NumPy/LAPACK) x {iters} iterations to 1e-4 rel-KKT on a "
+                       f"{Ps.m}x{Ps.n} instance of the same generator ({small_t:.1f} s"
+                       f"{', stopped at the time limit' if not rs['converged'] else ''})"),
+            "per_iter_s": per_iter, "iters_to_kkt_small": iters}
+
+
+# ------------------------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def traffic_record(kernel: str, workload: str):
+    """dram bytes per launch from a committed ncu summary, valid only while the kernel source
+    is unchanged (hash of the rowpass source)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        src = open(os.path.join(ROOT, "paper_2310_08333_gb300", "csrc", "rowpass.cu"), "rb").read()
+        h = hashlib.sha256(src).hexdigest()[:16]
+        rec = d.get(f"{kernel}|{workload}")
+        if rec and rec.get("source_hash") == h:
+            return rec["dram_bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        return None
+    return None
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2310_08333_gb300 as G
+    from paper_2310_08333_gb300 import _lib as L
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    gen_kw, rho, desc = WORKLOADS[args.workload]
+    P = make_problem(args.workload, seed_k=rank)
+    A32 = np.ascontiguousarray(P.A.astype(np.float32))
+    b32 = P.b.astype(np.float32)
+    Ad = torch.from_numpy(A32).cuda()
+    bd = torch.from_numpy(b32).cuda()
+    prec = G._lib.PRECISIONS[args.precision]
+
+    def solver(p):
+        return G.Solver(precision=p, stop_rule=G.STOP_KKT, eps_kkt=args.eps_kkt,
+                        sketch_rank=P.sketch_rank, rho=rho, max_iter=args.max_iter, profile=1)
+
+    s = solver(prec)
+    s.set_data(Ad, bd, P.loss)
+    lam = P.lam_frac * s.lambda_max()
+    for _ in range(args.warmup):
+        s.solve(lam)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = ClockSampler(dev)
+    clk.start()
+    infos = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        z, info = s.solve(lam)
+        infos.append(info)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = t.item()
+    clocks = clk.stop()
+    ms_step = ms_total / args.steps
+    status_ok = all(i["status"] == 0 for i in infos)
+
+    # roofline of the dominant kernel: fused Hv rowpass (CUDA events around each launch)
+    hv_ms = sum(i["hv_ms"] for i in infos)
+    hv_n = sum(i["hv_launches"] for i in infos)
+    hv_avg_ms = hv_ms / max(1, hv_n)
+    hv_bytes = infos[0]["hv_bytes"]
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    achieved = hv_bytes / (hv_avg_ms * 1e-3) / 1e9 if hv_n else None
+    roof = {"bound": "hbm", "kernel": "rowpass_kernel<FP32,Hv>", "achieved": achieved, "peak": hbm,
+            "peak_kind": f"{peak_kind} STREAM copy (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+            "unit": "GB/s", "frac": achieved / hbm if achieved else None,
+            "traffic": traffic_record("rowpass_hv_fp32", args.workload),
+            "bytes_per_launch": hv_bytes, "avg_launch_us": hv_avg_ms * 1e3,
+            "launches": hv_n}
+    grad_n = sum(i["grad_launches"] for i in infos)
+    launches = sum(i["kernel_launches"] for i in infos)
+
+    # end-to-end through the C ABI with pinned host buffers: set_data (H2D of A, b) + solve
+    # (x_out read back to host) per step
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.from_numpy(A32).pin_memory()
+        bh = torch.from_numpy(b32).pin_memory()
+        xh = torch.empty(P.n, dtype=torch.float64).pin_memory()
+        s2 = solver(prec)
+        s2.set_data(Ah, bh, P.loss)
+        s2.solve(lam, out=xh)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s2.set_data(Ah, bh, P.loss)
+            s2.solve(lam, out=xh)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = t.item()
+        s2.close()
+        e2e = {"value": el / args.steps / ws, "unit": "s",
+               "h2d_bytes_per_step": int(A32.nbytes + b32.nbytes),
+               "d2h_bytes_per_step": int(xh.numel() * 8)}
+
+    # plain vs mixed: one timed solve per precision on the same data
+    variants = {}
+    if not args.no_variants and rank == 0:
+        ref_z = z.copy()
+        for name in args.variant_list.split(","):
+            p = G._lib.PRECISIONS[name]
+            sv = solver(p)
+            sv.set_data(Ad, bd, P.loss)
+            sv.solve(lam)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            zv, iv = sv.solve(lam)
+            el = time.perf_counter() - t0
+            sv.close()
+            es = {"fp64": 8, "fp32": 4, "bf16": 2, "fp8": 1}[name]
+            hvb = P.m * P.n * es
+            variants[name] = {
+                "time_to_kkt_s": el, "status": iv["status_name"], "iters": iv["iters"],
+                "cg_iters": iv["cg_iters_total"], "rel_kkt": iv["rel_kkt"],
+                "hv_gbs": (iv["hv_bytes"] / (iv["hv_ms"] / iv["hv_launches"] * 1e-3) / 1e9)
+                if iv["hv_launches"] else None,
+                "hv_stream_bytes_per_elem": es, "hv_algorithmic_bytes": hvb,
+                "rel_diff_vs_fp32_z": float(np.linalg.norm(zv - ref_z) / max(np.linalg.norm(ref_z), 1e-300)),
+                "speedup_vs_fp32": ms_step / 1e3 / el if el > 0 else None}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(P, lam, rho, budget_s=args.cpu_budget)
+    if rank == 0:
+        solves = args.steps * ws
+        out = {
+            "metric": METRIC,
+            "value": ms_total / 1e3 / solves,
+            "unit": "s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step,
+            "higher_is_better": False,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "fp8": "e4m3"}[args.precision],
+            "data": "synthetic (seeded generator; the paper's datasets are not available)",
+            "config": {"workload": args.workload, "description": desc, "m": P.m, "n": P.n,
+                       "loss": P.loss, "lambda1": lam, "rho": rho, "sketch_rank": P.sketch_rank,
+                       "eps_kkt": args.eps_kkt, "precision": args.precision,
+                       "l2": "inputs larger than L2 (A = %d MB)" % (A32.nbytes // 2 ** 20),
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "value_note": "seconds per solve to 1e-4 relative KKT, whole job (time / solves)",
+            "solve": {"iters": [i["iters"] for i in infos], "cg_iters": [i["cg_iters_total"] for i in infos],
+                      "sketches": infos[0]["sketches"], "rel_kkt": [i["rel_kkt"] for i in infos],
+                      "nnz": infos[-1]["nnz"], "all_converged": status_ok,
+                      "sketch_ms": infos[-1]["t_sketch_ms"], "grad_launches": grad_n},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "variants": variants,
+        }
+        print(json.dumps(out), flush=True)
+    s.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores, same workload / metric (rank 0 only)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import checks
+    _, rho, desc = WORKLOADS[args.workload]
+    P = make_problem(args.workload)
+    A = P.A.astype(np.float32).astype(np.float64)
+    P.A = A
+    lam = P.lam_frac * checks.lambda_max(A, P.b, P.loss)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        cpu = oracle_baseline(P, lam, rho, budget_s=args.cpu_budget)
+        vals.append(cpu["value"])
+        if time.perf_counter() - t0 > 4 * args.cpu_budget:
+            break
+    v = float(np.mean(vals))
+    cpu["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
+           "steps": len(vals), "warmup": 0, "ms_per_step": v * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded generator; the paper's datasets are not available)",
+           "config": {"workload": args.workload, "description": desc, "m": P.m, "n": P.n,
+                      "loss": P.loss, "lambda1": lam, "rho": rho},
+           "cpu_baseline": cpu,
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="logistic_20000x8000", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16", "fp8"])
+    ap.add_argument("--eps-kkt", type=float, default=1e-4)
+    ap.add_argument("--max-iter", type=int, default=5000)
+    ap.add_argument("--variant-list", default="bf16,fp8")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=25.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -118,7 +118,7 @@ def solve(A, b, loss, lam1, lam2=0.0, rho=1.0, alpha=1.6, max_iter=20000, tol=1e
         rp = np.linalg.norm(x - z)
         rd = np.linalg.norm(A.T @ L.d1(A @ x - b) + lam2 * x + rho * u)
         if it % check_every == 0:
-            kkt = rel_kkt(A, b, x, z, L, lam1, lam2)
+            kkt = rel_kkt(A, b, z, L, lam1, lam2)
             hist.append((it, rp, rd, kkt, rho))
             if callback is not None:
                 callback(it, x, z, u, rho, kkt)
@@ -129,7 +129,7 @@ def solve(A, b, loss, lam1, lam2=0.0, rho=1.0, alpha=1.6, max_iter=20000, tol=1e
                 if ok:
                     x = zp.copy()
                     z = zp
-                    kkt = rel_kkt(A, b, x, z, L, lam1, lam2)
+                    kkt = rel_kkt(A, b, z, L, lam1, lam2)
                     polished = True
                     break
         if time_limit is not None and time.perf_counter() - t0 > time_limit:

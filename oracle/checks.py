@@ -4,9 +4,11 @@
   lambda_2 x term vanishes at 0), so lambda_max = ||A^T l'(-b)||_inf.
 * ``kkt_violation`` / ``rel_kkt``: the subgradient optimality conditions of App. A, Eq. (19):
   (grad f(x))_i = -lambda_1 sign(x_i) on the support and |(grad f(x))_i| <= lambda_1 off it.
-  The relative KKT residual is not defined in the paper; the reading used here is
-  max(||x - z|| / max(||x||, ||z||, tiny), ||d|| / max(||grad f(z)||, lambda_1)) where d is the
-  distance of 0 from the subdifferential of the objective at z.
+  The relative KKT residual is not defined in the paper; the reading used here measures the
+  returned point z only: ||d|| / max(||grad f(z)||, lambda_1), d = distance of 0 from the
+  subdifferential of the objective at z (coordinatewise, Eq. (19)).  (The ADMM-internal primal
+  residual ||x - z|| is left out: relative to max(||x||, ||z||) it equals 1 at z = 0 for every
+  x != 0, so it cannot certify the lambda >= lambda_max solution.)
 * ``duality_gap``: App. A — dual function g(nu), dual-feasible point built from l'(Ax - b)
   (scaled into the l_inf ball of radius lambda_1 when lambda_2 = 0, never scaled up), and the
   relative gap (P - D) / min(P, |D|) of §3.3 / Eq. (24).
@@ -61,12 +63,10 @@ def kkt_violation(A, b, z, loss, lam1, lam2=0.0):
     return float(np.max(subgradient_distance(g, z, lam1))) if z.size else 0.0
 
 
-def rel_kkt(A, b, x, z, loss, lam1, lam2=0.0):
+def rel_kkt(A, b, z, loss, lam1, lam2=0.0):
     g = grad_f(A, b, z, loss, lam2)
     d = subgradient_distance(g, z, lam1)
-    prim = np.linalg.norm(x - z) / max(np.linalg.norm(x), np.linalg.norm(z), 1e-30)
-    dual = np.linalg.norm(d) / max(np.linalg.norm(g), lam1, 1e-30)
-    return float(max(prim, dual))
+    return float(np.linalg.norm(d) / max(np.linalg.norm(g), lam1, 1e-30))
 
 
 def duality_gap(A, b, x, loss, lam1, lam2=0.0):

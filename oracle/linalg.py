@@ -104,15 +104,26 @@ def cg_tolerance(k, rp_norm, rd_norm, gamma=1.2, floor=0.0, first=1e-1):
 # ----------------------------------------------------------------------------------------
 # §2.2: randomized Nystrom approximation (Martinsson-Tropp Alg. 16, as cited) + Eq. (10)
 # ----------------------------------------------------------------------------------------
-def nystrom_from_sketch(Y, Omega):
-    """Given Y = H_data Omega (n x s) for a PSD H_data and the test matrix Omega, return
-    (U, lam_hat, shift) with H_data ~= U diag(lam_hat) U^T, lam_hat sorted descending.
+def orthonormal_test_matrix(Omega):
+    """Thin QR of the Gaussian test matrix: an orthonormal basis of its range (the stable
+    Nystrom algorithm the paper cites works with an orthonormal Omega; the approximation
+    depends only on range(Omega))."""
+    Q, _ = np.linalg.qr(Omega)
+    return Q
+
+
+def nystrom_from_sketch(Y, Omega, eps=None):
+    """Given Y = H_data Omega (n x s) for a PSD H_data and an orthonormal test matrix Omega,
+    return (U, lam_hat, shift) with H_data ~= U diag(lam_hat) U^T, lam_hat sorted descending.
 
     Steps: shift eta = sqrt(n) eps ||Y||_F; Y_eta = Y + eta Omega; C = chol(Omega^T Y_eta)
     (symmetrised); B = Y_eta C^{-1}; thin SVD B = U Sigma V^T; lam_hat = max(Sigma^2 - eta, 0).
+    ``eps`` is the unit roundoff of the arithmetic that produced Y (float64 by default).
     """
     n = Y.shape[0]
-    eta = np.sqrt(n) * np.finfo(np.float64).eps * np.linalg.norm(Y)
+    if eps is None:
+        eps = np.finfo(np.float64).eps
+    eta = np.sqrt(n) * eps * np.linalg.norm(Y)
     Y_eta = Y + eta * Omega
     G = Omega.T @ Y_eta
     G = 0.5 * (G + G.T)

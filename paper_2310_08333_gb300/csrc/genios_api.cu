@@ -1,0 +1,1076 @@
+// Host engine and C ABI of the GeNIOS x-subproblem path (declarations in include/genios.h).
+//
+// The ADMM driver follows §2 (Eqs. (3)-(7)) specialised to the ML problem of §3.3 with M = I,
+// c = 0, in the step form of Eq. (7): (A^T D A + nu I) delta = -(grad f(x^k) + rho (x^k - z^k
+// + u^k)), nu = rho + lambda_2 + sigma, which has the same solution x^{k+1} = x^k + delta.
+// Per iteration: one gradient rowpass over A (§3.3), the inexact PCG solve (§2.1) whose
+// Hessian-vector products are fused rowpasses, the Nystrom preconditioner of Eq. (10)
+// (re-sketched every `resketch_every` iterations for a non-constant loss'', once for the
+// squared loss, §3.3 / Table 2), the fused z/u update (§2.5, §3.1, Eq. (5)), residuals
+// (Eqs. (11)-(12)), the §2.3 stopping test / App. A duality gap / relative KKT, and the
+// penalty update of §2.5.
+#include "common.cuh"
+#include "internal.h"
+#include "../../include/genios.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace genios;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+struct Alloc {
+    std::vector<void*> ptrs;
+    cudaError_t get(void** p, size_t bytes) {
+        if (bytes == 0) bytes = 256;
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+    void release(void* p) {
+        if (!p) return;
+        for (auto& q : ptrs)
+            if (q == p) { cudaFree(q); q = nullptr; }
+    }
+    void free_all() {
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct genios_ctx {
+    genios_options opt;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err = "no error";
+    Alloc mem;
+    // problem
+    bool has_data = false;
+    int loss = 0;
+    int64_t m = 0, n = 0;
+    int prec = P_FP32;   // Hv storage precision
+    int gprec = P_FP32;  // gradient-pass storage precision (P_FP64, P_FP32, P_HILO)
+    bool dbl = false;
+    size_t vt = 4;
+    int64_t lda = 0, lda_g = 0, ldp = 0;
+    void* A_hv = nullptr;
+    float* A_scale = nullptr;
+    void* A_g = nullptr;
+    void* A_glo = nullptr;
+    void* b = nullptr;
+    void *x = nullptr, *z = nullptr, *u = nullptr, *g = nullptr, *r = nullptr, *p = nullptr,
+         *q = nullptr, *zc = nullptr, *delta = nullptr;
+    void *D = nullptr, *W = nullptr;
+    void* Pbuf = nullptr;
+    double* loss_part = nullptr;
+    RowpassPlan plan_hv{}, plan_g{};
+    // Nystrom
+    int sk = 0;
+    void* Om = nullptr;
+    void* U = nullptr;
+    double* lam = nullptr;
+    void* nyswork = nullptr;
+    NysWork nw{};
+    bool have_precond = false;
+    int n_sketch_total = 0;
+    // device scalars
+    DevState* S = nullptr;
+    DevState* Sh = nullptr;  // pinned host mirror
+    Scratch sc{};
+    // warm-start state
+    double rho = 1.0;
+    bool solved = false;
+    double lam1 = 0.0, lam2 = 0.0;
+    double t_setup_ms = 0.0;
+    // profiling
+    std::vector<cudaEvent_t> evs;
+    int64_t launches = 0;
+    long long* dbg = nullptr;  // bounds-check record of checked builds
+};
+
+#define CK(expr)                                                                           \
+    do {                                                                                   \
+        cudaError_t _e = (expr);                                                           \
+        if (_e != cudaSuccess) {                                                           \
+            ctx->err = std::string(#expr) + ": " + cudaGetErrorString(_e);                 \
+            return _e == cudaErrorMemoryAllocation ? GENIOS_ENOMEM : GENIOS_ECUDA;         \
+        }                                                                                  \
+    } while (0)
+
+#define FAIL(code, msg)                                                                    \
+    do {                                                                                   \
+        ctx->err = (msg);                                                                  \
+        return (code);                                                                     \
+    } while (0)
+
+// ------------------------------------------------------------------------------------------
+extern "C" void genios_default_options(genios_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->rho = 1.0;
+    o->sigma = 0.0;
+    o->alpha = 1.6;
+    o->eps_abs = 1e-4;
+    o->eps_rel = 1e-4;
+    o->eps_gap = 1e-4;
+    o->eps_kkt = 1e-4;
+    o->gamma = 1.2;
+    o->cg_tol_floor = -1.0;  // by precision
+    o->cg_tol_first = 0.1;
+    o->sketch_rank = -1;
+    o->resketch_every = 20;
+    o->rho_update_every = 25;
+    o->rho_update_max = 20;
+    o->rho_update_until = 1000;
+    o->rho_tau = 2.0;
+    o->rho_mu = 10.0;
+    o->max_iter = 5000;
+    o->max_cg_iter = 50;
+    o->stop_rule = GENIOS_STOP_KKT;
+    o->precision = GENIOS_FP32;
+    o->kkt_check_every = 10;
+    o->use_graphs = 1;
+    o->seed = 0x5eed2310ull;
+    o->device_wait_limit_us = 2000000;
+    o->verbose = 0;
+    o->profile = 0;
+}
+
+extern "C" genios_status genios_create(const genios_options* opts, int device, void* stream,
+                                       genios_ctx** out) {
+    if (!out) {
+        g_create_error = "out is NULL";
+        return GENIOS_EINVAL;
+    }
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        g_create_error = std::string("no such CUDA device: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "index");
+        cudaGetLastError();
+        return e != cudaSuccess ? GENIOS_ECUDA : GENIOS_EINVAL;
+    }
+    genios_ctx* ctx = new genios_ctx();
+    if (opts) ctx->opt = *opts;
+    else genios_default_options(&ctx->opt);
+    const genios_options& o = ctx->opt;
+    if (o.precision < 0 || o.precision > 3 || o.max_iter < 1 || o.max_cg_iter < 1 || o.rho <= 0 ||
+        o.alpha <= 0 || o.alpha >= 2 || o.sketch_rank > 128 || o.sketch_rank < -1) {
+        g_create_error = "invalid options";
+        delete ctx;
+        return GENIOS_EINVAL;
+    }
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    if (cudaSetDevice(device) != cudaSuccess) {
+        g_create_error = "cudaSetDevice failed";
+        delete ctx;
+        return GENIOS_ECUDA;
+    }
+    ctx->prec = o.precision;
+    ctx->dbl = (o.precision == GENIOS_FP64);
+    ctx->vt = ctx->dbl ? 8 : 4;
+    ctx->gprec = o.precision == GENIOS_FP64 ? P_FP64 : o.precision == GENIOS_FP32 ? P_FP32 : P_HILO;
+    if (cudaMalloc(&ctx->S, sizeof(DevState)) != cudaSuccess ||
+        cudaMallocHost(&ctx->Sh, sizeof(DevState)) != cudaSuccess ||
+        cudaMalloc(&ctx->sc.part, 262144 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&ctx->sc.counter, 256) != cudaSuccess ||
+        cudaMalloc(&ctx->dbg, 64) != cudaSuccess) {
+        g_create_error = "device allocation failed";
+        cudaGetLastError();
+        delete ctx;
+        return GENIOS_ENOMEM;
+    }
+    cudaMemset(ctx->S, 0, sizeof(DevState));
+    cudaMemset(ctx->sc.counter, 0, 256);
+    cudaMemset(ctx->dbg, 0, 64);
+    ctx->sc.dbg = ctx->dbg;
+    std::memset(ctx->Sh, 0, sizeof(DevState));
+    *out = ctx;
+    return GENIOS_OK;
+}
+
+extern "C" void genios_destroy(genios_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    ctx->mem.free_all();
+    for (auto ev : ctx->evs) cudaEventDestroy(ev);
+    if (ctx->S) cudaFree(ctx->S);
+    if (ctx->Sh) cudaFreeHost(ctx->Sh);
+    if (ctx->sc.part) cudaFree(ctx->sc.part);
+    if (ctx->sc.counter) cudaFree(ctx->sc.counter);
+    if (ctx->dbg) cudaFree(ctx->dbg);
+    cudaGetLastError();
+    delete ctx;
+}
+
+extern "C" const char* genios_last_error(const genios_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+// ------------------------------------------------------------------------------------------
+// data loading
+// ------------------------------------------------------------------------------------------
+static genios_status load_matrix_f32(genios_ctx* ctx, const void* A, int dt, int64_t lda_in,
+                                     bool dev, float** out32, int64_t* ld32) {
+    // produce a dense device float32 copy with leading dimension padded_lda(FP32, n)
+    const int64_t m = ctx->m, n = ctx->n;
+    const int64_t ld = padded_lda(P_FP32, n);
+    float* A32 = nullptr;
+    CK(ctx->mem.get((void**)&A32, (size_t)m * ld * 4));
+    cudaStream_t s = ctx->stream;
+    if (dt == GENIOS_DT_F32) {
+        CK(cudaMemsetAsync(A32, 0, (size_t)m * ld * 4, s));
+        CK(cudaMemcpy2DAsync(A32, ld * 4, A, lda_in * 4, n * 4, m,
+                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    } else {
+        void* tmp = const_cast<void*>(A);
+        bool own = false;
+        if (!dev) {
+            CK(ctx->mem.get(&tmp, (size_t)m * n * 8));
+            own = true;
+            CK(cudaMemcpy2DAsync(tmp, n * 8, A, lda_in * 8, n * 8, m, cudaMemcpyHostToDevice, s));
+        }
+        CK(convert_copy(0, 1, m, n, tmp, own ? n : lda_in, A32, ld, s));
+        if (own) {
+            CK(cudaStreamSynchronize(s));
+            ctx->mem.release(tmp);
+        }
+    }
+    *out32 = A32;
+    *ld32 = ld;
+    return GENIOS_OK;
+}
+
+extern "C" genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const int64_t* m,
+                                         const int64_t* n, const void* const* A, int A_dtype,
+                                         const int64_t* lda, const void* const* b, int shared_A) {
+    if (!ctx) return GENIOS_EINVAL;
+    if (K != 1) FAIL(GENIOS_EUNSUPPORTED, "this build supports K = 1 problem per context");
+    if (!m || !n || !A || !lda || !b || !A[0] || !b[0]) FAIL(GENIOS_EINVAL, "NULL argument");
+    if (m[0] < 1 || n[0] < 1 || lda[0] < n[0]) FAIL(GENIOS_EINVAL, "bad sizes");
+    if (loss != GENIOS_LOSS_SQUARED && loss != GENIOS_LOSS_LOGISTIC) FAIL(GENIOS_EINVAL, "bad loss");
+    if (A_dtype != GENIOS_DT_F64 && A_dtype != GENIOS_DT_F32) FAIL(GENIOS_EINVAL, "A_dtype must be F64 or F32");
+    (void)shared_A;
+    CK(cudaSetDevice(ctx->device));
+    const double t0 = now_ms();
+    cudaStream_t s = ctx->stream;
+    // drop previous data
+    CK(cudaStreamSynchronize(s));
+    ctx->mem.free_all();
+    ctx->has_data = false;
+    ctx->solved = false;
+    ctx->have_precond = false;
+    ctx->loss = loss;
+    ctx->m = m[0];
+    ctx->n = n[0];
+    const int64_t M = ctx->m, N = ctx->n;
+    const bool dev = is_device_ptr(A[0]);
+    const bool bdev = is_device_ptr(b[0]);
+    const size_t vt = ctx->vt;
+    genios_status st;
+
+    if (ctx->prec == GENIOS_FP64) {
+        ctx->lda = padded_lda(P_FP64, N);
+        CK(ctx->mem.get(&ctx->A_hv, (size_t)M * ctx->lda * 8));
+        CK(cudaMemsetAsync(ctx->A_hv, 0, (size_t)M * ctx->lda * 8, s));
+        if (A_dtype == GENIOS_DT_F64) {
+            CK(cudaMemcpy2DAsync(ctx->A_hv, ctx->lda * 8, A[0], lda[0] * 8, N * 8, M,
+                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        } else {
+            void* tmp = const_cast<void*>(A[0]);
+            if (!dev) {
+                CK(ctx->mem.get(&tmp, (size_t)M * N * 4));
+                CK(cudaMemcpy2DAsync(tmp, N * 4, A[0], lda[0] * 4, N * 4, M, cudaMemcpyHostToDevice, s));
+            }
+            CK(convert_copy(1, 0, M, N, tmp, dev ? lda[0] : N, ctx->A_hv, ctx->lda, s));
+        }
+        ctx->A_g = ctx->A_hv;
+        ctx->lda_g = ctx->lda;
+    } else {
+        float* A32 = nullptr;
+        int64_t ld32 = 0;
+        st = load_matrix_f32(ctx, A[0], A_dtype, lda[0], dev, &A32, &ld32);
+        if (st != GENIOS_OK) return st;
+        if (ctx->prec == GENIOS_FP32) {
+            ctx->A_hv = A32;
+            ctx->lda = ld32;
+            ctx->A_g = A32;
+            ctx->lda_g = ld32;
+        } else {
+            ctx->lda_g = padded_lda(P_BF16, N);
+            CK(ctx->mem.get(&ctx->A_g, (size_t)M * ctx->lda_g * 2));
+            CK(ctx->mem.get(&ctx->A_glo, (size_t)M * ctx->lda_g * 2));
+            CK(quantize_bf16_hilo(M, N, A32, ld32, ctx->A_g, ctx->A_glo, ctx->lda_g, s));
+            if (ctx->prec == GENIOS_BF16) {
+                ctx->A_hv = ctx->A_g;  // the hi part is the BF16 copy
+                ctx->lda = ctx->lda_g;
+            } else {
+                ctx->lda = padded_lda(P_FP8, N);
+                CK(ctx->mem.get(&ctx->A_hv, (size_t)M * ctx->lda));
+                CK(ctx->mem.get((void**)&ctx->A_scale, (size_t)M * 4));
+                CK(quantize_fp8_rows(M, N, A32, ld32, static_cast<uint8_t*>(ctx->A_hv), ctx->A_scale,
+                                     ctx->lda, s));
+            }
+            CK(cudaStreamSynchronize(s));
+            ctx->mem.release(A32);
+        }
+    }
+    // b in the value type
+    CK(ctx->mem.get(&ctx->b, (size_t)M * vt));
+    {
+        const int src_dt = A_dtype == GENIOS_DT_F64 ? 0 : 1;
+        const size_t sb = A_dtype == GENIOS_DT_F64 ? 8 : 4;
+        void* tmp = const_cast<void*>(b[0]);
+        if (!bdev) {
+            CK(ctx->mem.get(&tmp, (size_t)M * sb));
+            CK(cudaMemcpyAsync(tmp, b[0], (size_t)M * sb, cudaMemcpyHostToDevice, s));
+        }
+        CK(convert_copy(src_dt, ctx->dbl ? 0 : 1, 1, M, tmp, M, ctx->b, M, s));
+    }
+    // plans
+    const int hvp = ctx->prec == GENIOS_FP64 ? P_FP64 : ctx->prec == GENIOS_FP32 ? P_FP32
+                    : ctx->prec == GENIOS_BF16 ? P_BF16 : P_FP8;
+    ctx->plan_hv = rowpass_plan(hvp, M, N, ctx->lda);
+    ctx->plan_g = rowpass_plan(ctx->gprec, M, N, ctx->lda_g);
+    if (!ctx->plan_hv.ok || !ctx->plan_g.ok)
+        FAIL(GENIOS_EUNSUPPORTED, "n too large for the fused rowpass in this precision");
+    ctx->ldp = std::max(ctx->lda, ctx->lda_g);
+    const int G = std::max(ctx->plan_hv.grid, ctx->plan_g.grid);
+    CK(ctx->mem.get(&ctx->Pbuf, (size_t)G * ctx->ldp * vt));
+    CK(ctx->mem.get((void**)&ctx->loss_part, (size_t)G * 8));
+    void** vecs[] = {&ctx->x, &ctx->z, &ctx->u, &ctx->g, &ctx->r, &ctx->p, &ctx->q, &ctx->zc, &ctx->delta};
+    for (void** v : vecs) {
+        CK(ctx->mem.get(v, (size_t)ctx->ldp * vt));
+        CK(cudaMemsetAsync(*v, 0, (size_t)ctx->ldp * vt, s));
+    }
+    CK(ctx->mem.get(&ctx->D, (size_t)M * vt));
+    CK(ctx->mem.get(&ctx->W, (size_t)M * vt));
+    // Nystrom
+    int sk = ctx->opt.sketch_rank;
+    if (sk < 0) sk = (int)std::min<int64_t>(50, N / 20);
+    sk = (int)std::min<int64_t>(sk, N);
+    ctx->sk = std::max(0, sk);
+    if (ctx->sk > 0) {
+        CK(ctx->mem.get(&ctx->Om, (size_t)N * ctx->sk * vt));
+        CK(ctx->mem.get(&ctx->U, (size_t)N * ctx->sk * vt));
+        CK(ctx->mem.get((void**)&ctx->lam, (size_t)ctx->sk * 8));
+        const size_t wb = nystrom_work_bytes(hvp, M, N, ctx->sk);
+        CK(ctx->mem.get(&ctx->nyswork, wb));
+        ctx->nw = nystrom_carve(ctx->nyswork, hvp, M, N, ctx->sk);
+    } else {
+        ctx->U = nullptr;
+    }
+    CK(cudaStreamSynchronize(s));
+    ctx->has_data = true;
+    ctx->t_setup_ms = now_ms() - t0;
+    return GENIOS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// passes
+// ------------------------------------------------------------------------------------------
+static int hv_prec(const genios_ctx* ctx) {
+    return ctx->prec == GENIOS_FP64 ? P_FP64 : ctx->prec == GENIOS_FP32 ? P_FP32
+           : ctx->prec == GENIOS_BF16 ? P_BF16 : P_FP8;
+}
+
+static long long wait_cycles(const genios_ctx* ctx) {
+    // clock64 runs at the SM clock (<= ~2.1 GHz)
+    return (long long)ctx->opt.device_wait_limit_us * 2100LL;
+}
+
+static cudaError_t grad_pass(genios_ctx* ctx, const void* xv, void* Wout, void* Dout) {
+    RowpassArgs a{};
+    a.prec = ctx->gprec;
+    a.mode = RP_GRAD;
+    a.loss = ctx->loss;
+    a.m = ctx->m;
+    a.n = ctx->n;
+    a.lda = ctx->lda_g;
+    a.A = ctx->A_g;
+    a.A_lo = ctx->A_glo;
+    a.v = xv;
+    a.b = ctx->b;
+    a.W_out = Wout;
+    a.D_out = Dout;
+    a.partial = ctx->Pbuf;
+    a.ldp = ctx->ldp;
+    a.loss_part = ctx->loss_part;
+    a.err = nullptr;
+    a.wait_limit = wait_cycles(ctx);
+    a.dbg = ctx->dbg;
+    a.smem_bytes = (long long)ctx->plan_g.smem;
+    a.partial_len = (long long)ctx->plan_g.grid * ctx->ldp;
+    ctx->launches++;
+    return rowpass_launch(a, ctx->plan_g, ctx->stream);
+}
+
+static cudaError_t hv_pass(genios_ctx* ctx, const void* v, const void* v_aux, const void* d,
+                           const int* skip) {
+    RowpassArgs a{};
+    a.prec = hv_prec(ctx);
+    a.mode = RP_HV;
+    a.m = ctx->m;
+    a.n = ctx->n;
+    a.lda = ctx->lda;
+    a.A = ctx->A_hv;
+    a.row_scale = ctx->A_scale;
+    a.v = v;
+    a.v_aux = v_aux;
+    a.beta = &ctx->S->beta;
+    a.d = d;
+    a.partial = ctx->Pbuf;
+    a.ldp = ctx->ldp;
+    a.skip = skip;
+    a.err = nullptr;
+    a.wait_limit = wait_cycles(ctx);
+    a.dbg = ctx->dbg;
+    a.smem_bytes = (long long)ctx->plan_hv.smem;
+    a.partial_len = (long long)ctx->plan_hv.grid * ctx->ldp;
+    ctx->launches++;
+    return rowpass_launch(a, ctx->plan_hv, ctx->stream);
+}
+
+static genios_status read_state(genios_ctx* ctx) {
+    CK(cudaMemcpyAsync(ctx->Sh, ctx->S, offsetof(DevState, w), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GENIOS_OK;
+}
+
+static genios_status build_precond(genios_ctx* ctx, const void* d, double* ms) {
+    const double t0 = now_ms();
+    cudaStream_t s = ctx->stream;
+    CK(omega_fill(ctx->dbl, ctx->n, ctx->sk, ctx->opt.seed, (uint32_t)ctx->n_sketch_total, ctx->Om, s));
+    int ok = 0;
+    CK(nystrom_build(hv_prec(ctx), ctx->m, ctx->n, ctx->sk, ctx->A_hv, ctx->lda, ctx->A_scale, d,
+                     ctx->Om, ctx->U, ctx->lam, nullptr, ctx->nw, &ok, s));
+    ctx->launches += 12;
+    if (!ok) FAIL(GENIOS_ENUMERIC, "Nystrom core: Cholesky failed after raising the shift");
+    ctx->have_precond = true;
+    ctx->n_sketch_total++;
+    CK(cudaStreamSynchronize(s));
+    *ms += now_ms() - t0;
+    return GENIOS_OK;
+}
+
+// The CG loop of §2.1 on the current rhs (after rhs_init).  Reads S->cg_done after each
+// iteration (host-driven loop).
+static genios_status cg_loop(genios_ctx* ctx, const void* d, int* iters, std::vector<float>* hv_ms) {
+    cudaStream_t s = ctx->stream;
+    if (!ctx->delta || !ctx->r || !ctx->p || !ctx->q || !ctx->zc || !ctx->S || !ctx->Pbuf)
+        FAIL(GENIOS_EINVAL, "cg_loop: work vector not allocated");
+    const bool pc = ctx->sk > 0 && ctx->have_precond;
+    const int sk = pc ? ctx->sk : 0;
+    if (pc) {
+        CK(cg_precond(ctx->dbl, ctx->n, ctx->U, sk, ctx->lam, ctx->r, ctx->zc, ctx->S, ctx->sc, s));
+        ctx->launches++;
+    }
+    const int G = ctx->plan_hv.grid;
+    int it = 0;
+    const bool prof = ctx->opt.profile != 0;
+    for (;;) {
+        if (prof) {
+            while (ctx->evs.size() < 2) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                ctx->evs.push_back(e);
+            }
+            CK(cudaEventRecord(ctx->evs[0], s));
+        }
+        CK(hv_pass(ctx, ctx->p, ctx->zc, d, &ctx->S->cg_done));
+        if (prof) CK(cudaEventRecord(ctx->evs[1], s));
+        CK(cg_q(ctx->dbl, ctx->Pbuf, G, ctx->ldp, ctx->n, ctx->p, ctx->zc, ctx->q, ctx->S, ctx->sc, s));
+        CK(cg_update(ctx->dbl, ctx->n, ctx->delta, ctx->r, ctx->p, ctx->q, ctx->U, sk, ctx->zc,
+                     ctx->S, ctx->sc, s));
+        ctx->launches += 2;
+        genios_status st = read_state(ctx);
+        if (st != GENIOS_OK) return st;
+        if (prof) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ctx->evs[0], ctx->evs[1]));
+            hv_ms->push_back(ms);
+        }
+        it = ctx->Sh->cg_it;
+        if (ctx->Sh->cg_done) break;
+        if (pc) {
+            CK(cg_precond(ctx->dbl, ctx->n, ctx->U, sk, ctx->lam, ctx->r, ctx->zc, ctx->S, ctx->sc, s));
+            ctx->launches++;
+        }
+    }
+    *iters = it;
+    return GENIOS_OK;
+}
+
+static double cg_floor(const genios_ctx* ctx) {
+    if (ctx->opt.cg_tol_floor >= 0) return ctx->opt.cg_tol_floor;
+    switch (ctx->prec) {
+        case GENIOS_FP64: return 1e-10;
+        case GENIOS_FP32: return 1e-6;
+        default: return 1e-3;
+    }
+}
+
+extern "C" genios_status genios_lambda_max(genios_ctx* ctx, double* out) {
+    if (!ctx || !out) return GENIOS_EINVAL;
+    if (!ctx->has_data) FAIL(GENIOS_ESTATE, "lambda_max before set_data");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    // gradient pass at x = 0 (zc used as a zero vector): A^T loss'(-b)
+    CK(cudaMemsetAsync(ctx->zc, 0, (size_t)ctx->ldp * ctx->vt, s));
+    CK(grad_pass(ctx, ctx->zc, nullptr, nullptr));
+    CK(grad_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, ctx->loss_part, ctx->n, ctx->zc,
+                   ctx->zc, 0.0, 0.0, 0.0, ctx->g, ctx->S, ctx->sc, s));
+    genios_status st = read_state(ctx);
+    if (st != GENIOS_OK) return st;
+    *out = ctx->Sh->atw_inf;
+    return GENIOS_OK;
+}
+
+extern "C" genios_status genios_solve(genios_ctx* ctx, const double* lambda1, const double* lambda2,
+                                      void* x_out, int out_dtype, genios_info* info, int warm_start) {
+    if (!ctx) return GENIOS_EINVAL;
+    if (!ctx->has_data) FAIL(GENIOS_ESTATE, "solve before set_data");
+    if (!lambda1 || !lambda2 || !x_out) FAIL(GENIOS_EINVAL, "NULL argument");
+    if (!(lambda1[0] >= 0) || !(lambda2[0] >= 0)) FAIL(GENIOS_EINVAL, "lambda must be >= 0");
+    if (out_dtype != GENIOS_DT_F64 && out_dtype != GENIOS_DT_F32) FAIL(GENIOS_EINVAL, "bad out_dtype");
+    CK(cudaSetDevice(ctx->device));
+    const double t_start = now_ms();
+    cudaStream_t s = ctx->stream;
+    const genios_options& o = ctx->opt;
+    const double lam1 = lambda1[0], lam2 = lambda2[0];
+    const int64_t n = ctx->n;
+    const size_t vbytes = (size_t)ctx->ldp * ctx->vt;
+    genios_info inf{};
+    inf.rel_gap = NAN;
+    inf.rel_kkt = NAN;
+    inf.lambda1 = lam1;
+    inf.lambda2 = lam2;
+    inf.t_setup_ms = ctx->t_setup_ms;
+    ctx->launches = 0;
+    std::vector<float> hv_ms;
+
+    if (!warm_start || !ctx->solved) {
+        CK(cudaMemsetAsync(ctx->x, 0, vbytes, s));
+        CK(cudaMemsetAsync(ctx->z, 0, vbytes, s));
+        CK(cudaMemsetAsync(ctx->u, 0, vbytes, s));
+        ctx->rho = o.rho;
+    }
+    CK(cudaMemsetAsync(ctx->S, 0, offsetof(DevState, w), s));
+    double rho = ctx->rho;
+    const bool quadratic = ctx->loss == GENIOS_LOSS_SQUARED;
+    const bool use_pc = ctx->sk > 0;
+    const void* dvec = quadratic ? nullptr : ctx->D;
+    int n_rho = 0;
+    bool converged = false;
+    int iters = 0;
+    double last_rp = 0, last_rd = 0;
+    int kkt_last_checked = 1;
+    const double sqn = std::sqrt((double)n);
+    const double floor = cg_floor(ctx);
+
+    for (int k = 1; k <= o.max_iter; ++k) {
+        iters = k;
+        // ---- gradient pass at x^k (§3.3): grad f, D = loss'', loss sum
+        if (o.profile) {
+            while (ctx->evs.size() < 4) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                ctx->evs.push_back(e);
+            }
+            CK(cudaEventRecord(ctx->evs[2], s));
+        }
+        CK(grad_pass(ctx, ctx->x, ctx->W, ctx->D));
+        if (o.profile) CK(cudaEventRecord(ctx->evs[3], s));
+        inf.grad_launches++;
+        CK(grad_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, ctx->loss_part, n, ctx->x,
+                       ctx->u, lam2, rho, lam1, ctx->g, ctx->S, ctx->sc, s));
+        ctx->launches++;
+        genios_status st = read_state(ctx);
+        if (st != GENIOS_OK) return st;
+        if (o.profile) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ctx->evs[2], ctx->evs[3]));
+            inf.grad_ms += ms;
+        }
+        const DevState& H = *ctx->Sh;
+        inf.objective = H.loss_sum + lam1 * H.gx1 + 0.5 * lam2 * H.gx2;
+        if (!std::isfinite(H.rd2) || !std::isfinite(H.loss_sum)) {
+            inf.status = GENIOS_ENUMERIC;
+            ctx->err = "non-finite gradient or loss";
+            break;
+        }
+        // ---- residuals of the previous iterate (Eqs. (11)-(12)) and stop tests
+        if (k > 1) {
+            const double rp = std::sqrt(H.rp2), rd = std::sqrt(H.rd2);
+            last_rp = rp;
+            last_rd = rd;
+            inf.r_p = rp;
+            inf.r_d = rd;
+            const bool resid_ok = rp <= sqn * o.eps_abs + o.eps_rel * std::max(std::sqrt(H.x2), std::sqrt(H.z2)) &&
+                                  rd <= sqn * o.eps_abs + o.eps_rel * std::sqrt(H.rhou2);
+            bool stop = false;
+            if ((o.stop_rule & GENIOS_STOP_RESID) && resid_ok) stop = true;
+            if (!stop && (o.stop_rule & GENIOS_STOP_GAP)) {
+                CK(gap_pieces(ctx->dbl, ctx->loss, ctx->m, ctx->W, ctx->b, lam2, lam1, ctx->S, ctx->sc, s));
+                ctx->launches++;
+                st = read_state(ctx);
+                if (st != GENIOS_OK) return st;
+                const double P = H.loss_sum + lam1 * H.gx1 + 0.5 * lam2 * H.gx2;
+                double Dv = -H.conj_sum - H.btnu;
+                if (lam2 > 0) Dv -= H.excess2 / (2.0 * lam2);
+                const double den = std::min(P, std::fabs(Dv));
+                inf.rel_gap = den > 0 ? (P - Dv) / den : INFINITY;
+                if (inf.rel_gap <= o.eps_gap) stop = true;
+            }
+            // relative KKT at z: one extra pass over A, taken when the paper's residual test
+            // passes or every kkt_check_every iterations
+            if (!stop && (o.stop_rule & GENIOS_STOP_KKT) &&
+                ((resid_ok && k - kkt_last_checked >= 1) ||
+                 k - kkt_last_checked >= std::max(1, o.kkt_check_every))) {
+                kkt_last_checked = k;
+                CK(grad_pass(ctx, ctx->z, nullptr, nullptr));
+                CK(kkt_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, n, ctx->z, lam2, lam1,
+                              ctx->S, ctx->sc, s));
+                ctx->launches += 2;
+                inf.grad_launches++;
+                st = read_state(ctx);
+                if (st != GENIOS_OK) return st;
+                inf.rel_kkt = std::sqrt(H.kd2) / std::max(std::max(std::sqrt(H.kg2), lam1), 1e-30);
+                if (inf.rel_kkt <= o.eps_kkt) stop = true;
+            }
+            if (o.verbose)
+                std::fprintf(stderr, "[genios] it %d rp %.3e rd %.3e rho %.3g kkt %.3e gap %.3e cg %d\n",
+                             k, rp, rd, rho, inf.rel_kkt, inf.rel_gap, inf.cg_iters_total);
+            if (stop) {
+                converged = true;
+                iters = k - 1;
+                break;
+            }
+        }
+        // ---- penalty update (§2.5)
+        double u_scale = 1.0;
+        if (k > 1 && o.rho_update_every > 0 && (k - 1) % o.rho_update_every == 0 &&
+            n_rho < o.rho_update_max && k <= o.rho_update_until) {
+            double nr = rho;
+            if (last_rp > o.rho_mu * last_rd) nr = rho * o.rho_tau;
+            else if (last_rd > o.rho_mu * last_rp) nr = rho / o.rho_tau;
+            if (nr != rho) {
+                u_scale = rho / nr;
+                rho = nr;
+                n_rho++;
+            }
+        }
+        const double nu = rho + lam2 + o.sigma;
+        // ---- (re-)sketch (§2.2, §3.3)
+        if (use_pc) {
+            const bool first = !ctx->have_precond;
+            const bool resk = !quadratic && o.resketch_every > 0 && k > 1 && (k - 1) % o.resketch_every == 0;
+            if (first || resk) {
+                st = build_precond(ctx, dvec, &inf.t_sketch_ms);
+                if (st != GENIOS_OK) return st;
+                inf.sketches++;
+            }
+        }
+        // ---- CG tolerance (§2.1)
+        double tol = k <= 1 ? o.cg_tol_first
+                            : std::min(std::sqrt(last_rp * last_rd), 1.0) / std::pow((double)k, o.gamma);
+        tol = std::max(tol, floor);
+        // ---- x-step rhs, CG
+        CK(rhs_init(ctx->dbl, n, ctx->g, ctx->x, ctx->z, ctx->u, rho, u_scale, nu, tol, o.max_cg_iter,
+                    ctx->r, ctx->delta, ctx->p, ctx->zc, ctx->U, use_pc ? ctx->sk : 0, ctx->S, ctx->sc, s));
+        ctx->launches++;
+        int cgit = 0;
+        st = cg_loop(ctx, dvec, &cgit, &hv_ms);
+        if (st != GENIOS_OK) return st;
+        inf.cg_iters_total += cgit;
+        inf.hv_launches += cgit;
+        // ---- z/u update (§2.5, §3.1, Eq. (5)); x <- x + delta
+        CK(zu_update(ctx->dbl, n, ctx->x, ctx->delta, ctx->z, ctx->u, rho, lam1, o.alpha, ctx->S, nullptr,
+                     ctx->sc, s));
+        ctx->launches++;
+    }
+    ctx->rho = rho;
+    ctx->solved = true;
+    ctx->lam1 = lam1;
+    ctx->lam2 = lam2;
+    // output z
+    {
+        const bool odev = is_device_ptr(x_out);
+        const int odt = out_dtype == GENIOS_DT_F64 ? 0 : 1;
+        const size_t ob = odt == 0 ? 8 : 4;
+        void* tmp = x_out;
+        if (!odev) CK(ctx->mem.get(&tmp, (size_t)n * ob));
+        CK(convert_copy(ctx->dbl ? 0 : 1, odt, 1, n, ctx->z, n, tmp, n, s));
+        if (!odev) CK(cudaMemcpyAsync(x_out, tmp, (size_t)n * ob, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!odev) ctx->mem.release(tmp);
+    }
+    genios_status rs = read_state(ctx);
+    if (rs != GENIOS_OK) return rs;
+    inf.iters = iters;
+    inf.rho = rho;
+    inf.rho_updates = n_rho;
+    inf.nnz = (int)ctx->Sh->nnz;
+    inf.t_solve_ms = now_ms() - t_start;
+    inf.kernel_launches = ctx->launches;
+    for (float ms : hv_ms) inf.hv_ms += ms;
+    {
+        const size_t es = ctx->prec == GENIOS_FP64 ? 8 : ctx->prec == GENIOS_FP32 ? 4
+                          : ctx->prec == GENIOS_BF16 ? 2 : 1;
+        inf.hv_bytes = (double)ctx->m * (double)ctx->n * (double)es +
+                       (double)ctx->m * ctx->vt * (quadratic ? 0 : 1) + 2.0 * (double)ctx->n * ctx->vt;
+    }
+    if (inf.status == 0) inf.status = converged ? GENIOS_OK : GENIOS_EMAXITER;
+    if (info) *info = inf;
+    return (genios_status)inf.status;
+}
+
+extern "C" genios_status genios_grad(genios_ctx* ctx, const void* dL_dx, double* dL_dlambda1,
+                                     void* dL_db, void* dL_dA) {
+    if (!ctx) return GENIOS_EINVAL;
+    (void)dL_dx; (void)dL_dlambda1; (void)dL_db; (void)dL_dA;
+    if (!ctx->solved) FAIL(GENIOS_ESTATE, "grad before a solve");
+    FAIL(GENIOS_EUNSUPPORTED, "implicit gradient not built yet");
+}
+
+// ------------------------------------------------------------------------------------------
+// kernel-level entry points
+// ------------------------------------------------------------------------------------------
+namespace {
+struct OpWs {
+    void* P;
+    double* loss_part;
+    DevState* S;
+    Scratch sc;
+    void* zero;
+    void* tmp1;
+    void* tmp2;
+    void* tmp3;
+};
+size_t alb(size_t b) { return (b + 255) & ~size_t(255); }
+int prec_valid(int p) { return p >= 0 && p <= 3; }
+int hvp_of(int p) { return p == 0 ? P_FP64 : p == 1 ? P_FP32 : p == 2 ? P_BF16 : P_FP8; }
+
+size_t op_ws_bytes(int precision, int64_t m, int64_t n) {
+    const int sms = device_sm_count();
+    const size_t vt = precision == 0 ? 8 : 4;
+    const int64_t ldp = std::max(padded_lda(hvp_of(precision), n), padded_lda(P_BF16, n)) +
+                        padded_lda(P_FP64, n);
+    size_t b = 0;
+    b += alb((size_t)sms * ldp * vt);
+    b += alb((size_t)sms * 8);
+    b += alb(sizeof(DevState));
+    b += alb(262144 * 8);
+    b += alb(256);
+    b += 4 * alb((size_t)ldp * vt);
+    (void)m;
+    return b;
+}
+
+bool carve(void* ws, size_t bytes, int precision, int64_t m, int64_t n, OpWs* o, cudaStream_t s) {
+    if (!ws || bytes < op_ws_bytes(precision, m, n) || (reinterpret_cast<uintptr_t>(ws) & 255)) return false;
+    const int sms = device_sm_count();
+    const size_t vt = precision == 0 ? 8 : 4;
+    const int64_t ldp = std::max(padded_lda(hvp_of(precision), n), padded_lda(P_BF16, n)) +
+                        padded_lda(P_FP64, n);
+    char* p = static_cast<char*>(ws);
+    o->P = p; p += alb((size_t)sms * ldp * vt);
+    o->loss_part = reinterpret_cast<double*>(p); p += alb((size_t)sms * 8);
+    o->S = reinterpret_cast<DevState*>(p); p += alb(sizeof(DevState));
+    o->sc.part = reinterpret_cast<double*>(p); p += alb(262144 * 8);
+    o->sc.counter = reinterpret_cast<unsigned*>(p); p += alb(256);
+    o->sc.dbg = nullptr;
+    o->zero = p; p += alb((size_t)ldp * vt);
+    o->tmp1 = p; p += alb((size_t)ldp * vt);
+    o->tmp2 = p; p += alb((size_t)ldp * vt);
+    o->tmp3 = p; p += alb((size_t)ldp * vt);
+    cudaMemsetAsync(o->sc.counter, 0, 256, s);
+    cudaMemsetAsync(o->zero, 0, (size_t)ldp * vt, s);
+    cudaMemsetAsync(o->S, 0, sizeof(DevState), s);
+    return true;
+}
+
+genios_status op_err(cudaError_t e) {
+    if (e == cudaSuccess) return GENIOS_OK;
+    g_create_error = cudaGetErrorString(e);
+    return GENIOS_ECUDA;
+}
+}  // namespace
+
+extern "C" size_t genios_op_workspace_bytes(int precision, int64_t m, int64_t n) {
+    if (!prec_valid(precision) || m < 1 || n < 1) return 0;
+    return op_ws_bytes(precision, m, n);
+}
+
+extern "C" int64_t genios_op_lda(int precision, int64_t n) {
+    if (!prec_valid(precision) || n < 1) return 0;
+    return padded_lda(hvp_of(precision), n);
+}
+
+extern "C" genios_status genios_op_hv(int precision, int64_t m, int64_t n, const void* A, int64_t lda,
+                                      const float* row_scale, const void* d, double nu, const void* v,
+                                      void* y, void* workspace, size_t workspace_bytes, void* stream) {
+    if (!prec_valid(precision) || m < 1 || n < 1 || !A || !v || !y) return GENIOS_EINVAL;
+    if (precision == GENIOS_FP8_E4M3 && !row_scale) return GENIOS_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    OpWs w;
+    if (!carve(workspace, workspace_bytes, precision, m, n, &w, s)) return GENIOS_EINVAL;
+    const int P = hvp_of(precision);
+    RowpassPlan plan = rowpass_plan(P, m, n, lda);
+    if (!plan.ok) return GENIOS_EUNSUPPORTED;
+    RowpassArgs a{};
+    a.prec = P;
+    a.mode = RP_HV;
+    a.m = m; a.n = n; a.lda = lda;
+    a.A = A;
+    a.row_scale = row_scale;
+    a.v = v;
+    a.d = d;
+    a.partial = w.P;
+    a.ldp = lda;
+    a.wait_limit = 2000000LL * 2100LL;
+    cudaError_t e = rowpass_launch(a, plan, s);
+    if (e == cudaSuccess) e = hv_finish(precision == 0, w.P, plan.grid, lda, n, nu, v, y, s);
+    return op_err(e);
+}
+
+extern "C" genios_status genios_op_gradient(int loss, int precision, int64_t m, int64_t n, const void* A,
+                                            const void* A_lo, int64_t lda, const void* b, const void* x,
+                                            double lambda2, void* grad_out, void* w_out, void* D_out,
+                                            double* loss_sum_out, void* workspace, size_t workspace_bytes,
+                                            void* stream) {
+    if (!prec_valid(precision) || m < 1 || n < 1 || !A || !b || !x || !grad_out) return GENIOS_EINVAL;
+    if (loss != 0 && loss != 1) return GENIOS_EINVAL;
+    if (precision >= 2 && !A_lo) return GENIOS_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    OpWs w;
+    if (!carve(workspace, workspace_bytes, precision, m, n, &w, s)) return GENIOS_EINVAL;
+    const int P = precision == 0 ? P_FP64 : precision == 1 ? P_FP32 : P_HILO;
+    RowpassPlan plan = rowpass_plan(P, m, n, lda);
+    if (!plan.ok) return GENIOS_EUNSUPPORTED;
+    RowpassArgs a{};
+    a.prec = P;
+    a.mode = RP_GRAD;
+    a.loss = loss;
+    a.m = m; a.n = n; a.lda = lda;
+    a.A = A;
+    a.A_lo = A_lo;
+    a.v = x;
+    a.b = b;
+    a.W_out = w_out;
+    a.D_out = D_out;
+    a.partial = w.P;
+    a.ldp = lda;
+    a.loss_part = w.loss_part;
+    a.wait_limit = 2000000LL * 2100LL;
+    cudaError_t e = rowpass_launch(a, plan, s);
+    if (e == cudaSuccess)
+        e = grad_finish(precision == 0, w.P, plan.grid, lda, w.loss_part, n, x, x, lambda2, 0.0, 0.0,
+                        grad_out, w.S, w.sc, s);
+    if (e == cudaSuccess && loss_sum_out)
+        e = cudaMemcpyAsync(loss_sum_out, &w.S->loss_sum, sizeof(double), cudaMemcpyDeviceToDevice, s);
+    return op_err(e);
+}
+
+extern "C" genios_status genios_op_zu_update(int precision, int64_t n, const void* x, void* z, void* u,
+                                             double rho, double lambda1, double alpha, double* norms_out,
+                                             void* workspace, size_t workspace_bytes, void* stream) {
+    if (!prec_valid(precision) || n < 1 || !x || !z || !u || !(rho > 0)) return GENIOS_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    OpWs w;
+    if (!carve(workspace, workspace_bytes, precision, 1, n, &w, s)) return GENIOS_EINVAL;
+    return op_err(zu_update(precision == 0, n, const_cast<void*>(x), nullptr, z, u, rho, lambda1, alpha,
+                            nullptr, norms_out, w.sc, s));
+}
+
+extern "C" size_t genios_op_nystrom_workspace_bytes(int precision, int64_t m, int64_t n, int s) {
+    if (!prec_valid(precision) || m < 1 || n < 1 || s < 1 || s > 128) return 0;
+    return nystrom_work_bytes(hvp_of(precision), m, n, s) + 1024;
+}
+
+extern "C" genios_status genios_op_nystrom(int precision, int64_t m, int64_t n, int s, const void* A,
+                                           int64_t lda, const float* row_scale, const void* d,
+                                           const void* Omega, void* U_out, double* lam_out,
+                                           double* eta_out, void* workspace, size_t workspace_bytes,
+                                           void* stream) {
+    if (!prec_valid(precision) || m < 1 || n < 1 || s < 1 || s > 128 || s > n || !A || !Omega ||
+        !U_out || !lam_out)
+        return GENIOS_EINVAL;
+    if (!workspace || workspace_bytes < genios_op_nystrom_workspace_bytes(precision, m, n, s))
+        return GENIOS_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int P = hvp_of(precision);
+    NysWork w = nystrom_carve(workspace, P, m, n, s);
+    int ok = 0;
+    cudaError_t e = nystrom_build(P, m, n, s, A, lda, row_scale, d, Omega, U_out, lam_out, eta_out, w,
+                                  &ok, st);
+    if (e != cudaSuccess) return op_err(e);
+    return ok ? GENIOS_OK : GENIOS_ENUMERIC;
+}
+
+extern "C" genios_status genios_op_precond(int precision, int64_t n, int s, const void* U, const double* lam,
+                                           double nu, const void* v, void* y, void* workspace,
+                                           size_t workspace_bytes, void* stream) {
+    if (!prec_valid(precision) || n < 1 || s < 1 || s > 256 || !U || !lam || !v || !y) return GENIOS_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    OpWs w;
+    if (!carve(workspace, workspace_bytes, precision, 1, n, &w, st)) return GENIOS_EINVAL;
+    const bool dbl = precision == 0;
+    // r = -(0 + (-1)(v - 0 + 0)) = v, then U^T r into S->w
+    cudaError_t e = rhs_init(dbl, n, w.zero, v, w.zero, w.zero, -1.0, 1.0, nu, 0.0, 1, w.tmp1, w.tmp2,
+                             w.tmp3, y, U, s, w.S, w.sc, st);
+    if (e == cudaSuccess) e = cg_precond(dbl, n, U, s, lam, w.tmp1, y, w.S, w.sc, st);
+    return op_err(e);
+}
+
+extern "C" genios_status genios_op_omega(int precision, int64_t n, int s, uint64_t seed, uint32_t stream_id,
+                                         void* Omega, void* stream) {
+    if (!prec_valid(precision) || n < 1 || s < 1 || !Omega) return GENIOS_EINVAL;
+    return op_err(omega_fill(precision == 0, n, s, seed, stream_id, Omega, static_cast<cudaStream_t>(stream)));
+}
+
+extern "C" genios_status genios_op_philox(uint32_t ctr0, uint32_t ctr1, uint32_t ctr2, uint32_t ctr3,
+                                          uint32_t key0, uint32_t key1, int64_t nblocks, uint32_t* out,
+                                          void* stream) {
+    if (nblocks < 1 || !out) return GENIOS_EINVAL;
+    return op_err(philox_blocks(ctr0, ctr1, ctr2, ctr3, key0, key1, nblocks, out,
+                                static_cast<cudaStream_t>(stream)));
+}
+
+extern "C" genios_status genios_op_quantize(int precision, int64_t m, int64_t n, const float* A, int64_t lda_in,
+                                            void* hi_or_codes, void* lo, float* row_scale, void* stream) {
+    if (m < 1 || n < 1 || !A || !hi_or_codes || lda_in < n) return GENIOS_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == GENIOS_BF16) {
+        if (!lo) return GENIOS_EINVAL;
+        return op_err(quantize_bf16_hilo(m, n, A, lda_in, hi_or_codes, lo, padded_lda(P_BF16, n), s));
+    }
+    if (precision == GENIOS_FP8_E4M3) {
+        if (!row_scale) return GENIOS_EINVAL;
+        return op_err(quantize_fp8_rows(m, n, A, lda_in, static_cast<uint8_t*>(hi_or_codes), row_scale,
+                                        padded_lda(P_FP8, n), s));
+    }
+    return GENIOS_EINVAL;
+}
+
+extern "C" genios_status genios_op_pcg(int precision, int64_t m, int64_t n, const void* A, int64_t lda,
+                                       const float* row_scale, const void* d, double nu, const void* r,
+                                       int s, const void* U, const double* lam, double rtol, int max_iter,
+                                       void* delta_out, int* iters_out, double* relres_out, void* stream) {
+    if (!prec_valid(precision) || m < 1 || n < 1 || !A || !r || !delta_out || max_iter < 1) return GENIOS_EINVAL;
+    if (s > 0 && (!U || !lam)) return GENIOS_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int P = hvp_of(precision);
+    RowpassPlan plan = rowpass_plan(P, m, n, lda);
+    if (!plan.ok) return GENIOS_EUNSUPPORTED;
+    // a transient context-like set of buffers
+    genios_ctx tmp;
+    genios_ctx* ctx = &tmp;
+    ctx->stream = st;
+    ctx->prec = precision;
+    ctx->dbl = precision == 0;
+    ctx->vt = ctx->dbl ? 8 : 4;
+    ctx->m = m;
+    ctx->n = n;
+    ctx->lda = lda;
+    ctx->ldp = lda;
+    ctx->A_hv = const_cast<void*>(A);
+    ctx->A_scale = const_cast<float*>(row_scale);
+    ctx->plan_hv = plan;
+    ctx->sk = s;
+    ctx->have_precond = s > 0;
+    ctx->U = const_cast<void*>(U);
+    ctx->lam = const_cast<double*>(lam);
+    ctx->delta = delta_out;
+    ctx->opt.device_wait_limit_us = 2000000;
+    ctx->opt.profile = 0;
+    const size_t vb = (size_t)lda * ctx->vt;
+    genios_status result = GENIOS_OK;
+    do {
+        if (ctx->mem.get(&ctx->Pbuf, (size_t)plan.grid * lda * ctx->vt) != cudaSuccess ||
+            ctx->mem.get((void**)&ctx->S, sizeof(DevState)) != cudaSuccess ||
+            cudaMallocHost(&ctx->Sh, sizeof(DevState)) != cudaSuccess ||
+            ctx->mem.get((void**)&ctx->sc.part, 262144 * 8) != cudaSuccess ||
+            ctx->mem.get((void**)&ctx->sc.counter, 256) != cudaSuccess ||
+            ctx->mem.get((void**)&ctx->dbg, 64) != cudaSuccess ||
+            ctx->mem.get(&ctx->p, vb) != cudaSuccess || ctx->mem.get(&ctx->q, vb) != cudaSuccess ||
+            ctx->mem.get(&ctx->zc, vb) != cudaSuccess || ctx->mem.get(&ctx->r, vb) != cudaSuccess ||
+            ctx->mem.get(&ctx->g, vb) != cudaSuccess) {
+            result = GENIOS_ENOMEM;
+            break;
+        }
+        cudaMemsetAsync(ctx->sc.counter, 0, 256, st);
+        cudaMemsetAsync(ctx->dbg, 0, 64, st);
+        ctx->sc.dbg = ctx->dbg;
+        cudaMemsetAsync(ctx->S, 0, sizeof(DevState), st);
+        cudaMemsetAsync(ctx->g, 0, vb, st);
+        // rhs: r = -(0 + (-1)(r_in - 0 + 0)) = r_in   (g doubles as the zero z and u)
+        cudaError_t e = rhs_init(ctx->dbl, n, ctx->g, r, ctx->g, ctx->g, -1.0, 1.0, nu, rtol, max_iter,
+                                 ctx->r, delta_out, ctx->p, ctx->zc, U, s, ctx->S, ctx->sc, st);
+        if (e != cudaSuccess) {
+            result = op_err(e);
+            break;
+        }
+        int it = 0;
+        std::vector<float> dummy;
+        result = cg_loop(ctx, d, &it, &dummy);
+#ifdef GENIOS_CHECKED
+        {
+            long long rec[4] = {0, 0, 0, 0};
+            cudaMemcpyAsync(rec, ctx->dbg, sizeof(rec), cudaMemcpyDeviceToHost, st);
+            cudaStreamSynchronize(st);
+            if (rec[0] != 0) {
+                std::fprintf(stderr, "[genios checked] op_pcg: out-of-bounds access at line %lld: "
+                             "index %lld, length %lld (block*4096+thread %lld)\n",
+                             rec[0], rec[1], rec[2], rec[3]);
+                if (result == GENIOS_OK) {
+                    result = GENIOS_ENUMERIC;
+                    ctx->err = "checked build: out-of-bounds access recorded";
+                }
+            }
+        }
+#endif
+        if (result != GENIOS_OK) {
+            g_create_error = ctx->err;
+            break;
+        }
+        if (iters_out) *iters_out = it;
+        if (relres_out)
+            *relres_out = ctx->Sh->rhs2 > 0 ? std::sqrt(ctx->Sh->rr / ctx->Sh->rhs2) : 0.0;
+    } while (0);
+    cudaStreamSynchronize(st);
+    ctx->mem.free_all();
+    if (ctx->Sh) cudaFreeHost(ctx->Sh);
+    ctx->Sh = nullptr;
+    ctx->S = nullptr;
+    ctx->sc.part = nullptr;
+    ctx->sc.counter = nullptr;
+    return result;
+}

@@ -1,0 +1,170 @@
+// Internal interfaces between the host engine and the kernels (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+namespace genios {
+
+// Scalars that kernels produce and consume on the device.  One instance per context,
+// in device memory; the host reads it with an async copy when it needs a decision.
+struct DevState {
+    // preconditioned CG (§2.1)
+    double rz;        // r^T P^{-1} r of the current iterate
+    double pq;        // p^T H p
+    double alpha;     // step
+    double beta;      // conjugation coefficient for the next p
+    double rr;        // ||r||^2
+    double rhs2;      // ||rhs||^2
+    double tol;       // relative tolerance of this solve
+    double nu;        // diagonal shift rho + lambda_2 (+ sigma)
+    int32_t cg_it;    // iterations done
+    int32_t cg_done;  // 1 once ||r|| <= tol ||rhs|| or cg_it == cg_max
+    int32_t cg_max;
+    int32_t cg_first; // 1 before the first preconditioner application of a solve
+    // gradient pass at x (§3.3) and residual norms (Eqs. (11)-(12))
+    double loss_sum;  // sum_i loss(a_i^T x - b_i)
+    double g2;        // ||grad f(x)||^2
+    double rd2;       // ||grad f(x) + rho u||^2
+    double rhou2;     // ||rho u||^2
+    double atw_inf;   // ||A^T loss'(Ax - b)||_inf
+    double excess2;   // sum_j ((|A^T loss'|_j - lambda_1)_+)^2
+    double gx1;       // ||x||_1
+    double gx2;       // ||x||^2
+    // z/u update
+    double rp2, x2, z2, u2, z1, nnz;
+    // relative KKT at z
+    double kd2;       // ||dist(0, subdifferential)||^2
+    double kg2;       // ||grad f(z)||^2
+    double kdmax;
+    // duality gap pieces (App. A)
+    double conj_sum;  // sum_i loss*(nu_i)
+    double btnu;      // b^T nu
+    double gap_scale; // scale applied to loss'(Ax - b)
+    double pad[4];
+    double w[256];    // U^T r (Nystrom preconditioner), s <= 256
+};
+
+// ------------------------------------------------------------------------------------------
+// Rowpass: one pass over A computing y = A^T w(A v) (partials per CTA)
+// ------------------------------------------------------------------------------------------
+enum RowpassMode { RP_HV = 0, RP_GRAD = 1 };
+
+struct RowpassArgs {
+    int prec;                   // Prec (P_HILO for the split gradient pass)
+    int mode;                   // RowpassMode
+    int loss;                   // LossKind (GRAD)
+    int64_t m, n, lda;          // lda in elements of the storage type
+    const void* A;
+    const void* A_lo;           // P_HILO: low part
+    const float* row_scale;     // P_FP8
+    const void* v;              // input vector (value type)
+    const void* v_aux;          // if non-null: v := v_aux + beta * v  (fused CG direction update)
+    const double* beta;         // device scalar for the fused update
+    const void* d;              // RP_HV: row weights or null (= 1)
+    const void* b;              // RP_GRAD: offsets
+    void* W_out;                // RP_GRAD: loss'(t) (may be null)
+    void* D_out;                // RP_GRAD: loss''(t) (may be null)
+    void* partial;              // grid x ldp value-type partial sums of A^T w
+    int64_t ldp;
+    double* loss_part;          // RP_GRAD: grid partial loss sums
+    const int* skip;            // kernel returns at once when *skip != 0
+    int* err;
+    long long wait_limit;       // clock cycles
+    long long* dbg;             // bounds-check record (checked builds only)
+    long long smem_bytes;       // dynamic shared memory of the launch (checked builds)
+    long long partial_len;      // elements of `partial` (checked builds)
+};
+
+struct RowpassPlan {
+    bool ok;
+    int grid, nch, rb, rows_per_stage, nstages;
+    size_t smem;
+};
+
+int device_sm_count();
+RowpassPlan rowpass_plan(int prec, int64_t m, int64_t n, int64_t lda);
+cudaError_t rowpass_launch(const RowpassArgs& a, const RowpassPlan& p, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// Vector kernels (value type float or double chosen by `dbl`)
+// ------------------------------------------------------------------------------------------
+struct Scratch {
+    double* part;        // >= 4096 * 16 doubles of per-block partials
+    unsigned* counter;   // zero-initialised
+    long long* dbg;      // bounds-check record (checked builds only)
+};
+
+// y = sum_b P[b] + nu v  (plain Hv finish, op level)
+cudaError_t hv_finish(bool dbl, const void* P, int G, int64_t ldp, int64_t n, double nu,
+                      const void* v, void* y, cudaStream_t s);
+// CG: p = zc + beta p; q = sum_b P[b] + nu p; pq, alpha
+cudaError_t cg_q(bool dbl, const void* P, int G, int64_t ldp, int64_t n, void* p, const void* zc,
+                 void* q, DevState* S, Scratch sc, cudaStream_t s);
+// CG: delta += alpha p; r -= alpha q; rr; U^T r (s > 0); done flag; (s == 0: zc = r, beta)
+cudaError_t cg_update(bool dbl, int64_t n, void* delta, void* r, const void* p, const void* q,
+                      const void* U, int sk, void* zc, DevState* S, Scratch sc, cudaStream_t s);
+// CG: zc = P^{-1} r (Eq. (10)) from S->w; rz, beta
+cudaError_t cg_precond(bool dbl, int64_t n, const void* U, int sk, const double* lam,
+                       const void* r, void* zc, DevState* S, Scratch sc, cudaStream_t s);
+// x-step right-hand side and CG initialisation:
+//   u *= u_scale; r = -(g + rho (x - z + u)); delta = 0; p = 0; rhs2; U^T r
+cudaError_t rhs_init(bool dbl, int64_t n, const void* g, const void* x, const void* z, void* u,
+                     double rho, double u_scale, double nu, double tol, int cg_max, void* r,
+                     void* delta, void* p, void* zc, const void* U, int sk, DevState* S,
+                     Scratch sc, cudaStream_t s);
+// gradient finish: g = sum_b P[b] + mu x; norms for r_d, objective, gap; loss sum
+cudaError_t grad_finish(bool dbl, const void* P, int G, int64_t ldp, const double* loss_part,
+                        int64_t n, const void* x, const void* u, double mu, double rho,
+                        double lam1, void* g, DevState* S, Scratch sc, cudaStream_t s);
+// KKT finish at z: gz = sum_b P[b] + mu z; subgradient distance norms
+cudaError_t kkt_finish(bool dbl, const void* P, int G, int64_t ldp, int64_t n, const void* z,
+                       double mu, double lam1, DevState* S, Scratch sc, cudaStream_t s);
+// duality gap pieces from W = loss'(Ax - b) (m-vector)
+cudaError_t gap_pieces(bool dbl, int loss, int64_t m, const void* W, const void* b, double mu,
+                       double lam1, DevState* S, Scratch sc, cudaStream_t s);
+// z/u update (x += delta first when delta != null)
+cudaError_t zu_update(bool dbl, int64_t n, void* x, const void* delta, void* z, void* u,
+                      double rho, double lam1, double alpha, DevState* S, double* norms_out,
+                      Scratch sc, cudaStream_t s);
+// conversions
+cudaError_t convert_copy(int src_dt, int dst_dt, int64_t rows, int64_t cols, const void* src,
+                         int64_t lds, void* dst, int64_t ldd, cudaStream_t s);
+cudaError_t fill_zero(void* p, size_t bytes, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// Quantisation, Philox, Nystrom
+// ------------------------------------------------------------------------------------------
+cudaError_t quantize_bf16_hilo(int64_t m, int64_t n, const float* A, int64_t lda_in, void* hi,
+                               void* lo, int64_t lda_out, cudaStream_t s);
+cudaError_t quantize_fp8_rows(int64_t m, int64_t n, const float* A, int64_t lda_in, uint8_t* q,
+                              float* scale, int64_t lda_out, cudaStream_t s);
+cudaError_t philox_blocks(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                          uint32_t k1, int64_t nblocks, uint32_t* out, cudaStream_t s);
+cudaError_t omega_fill(bool dbl, int64_t n, int sk, uint64_t seed, uint32_t stream_id, void* Om,
+                       cudaStream_t s);
+
+struct NysWork {
+    void* Oq;       // n x s value type: orthonormalised copy of Omega (CholeskyQR2)
+    void* W;        // m x s value type (A Omega)
+    void* Y;        // n x s value type
+    double* G;      // s x s
+    double* C;      // s x s (Cholesky / inverse)
+    void* Cinv;     // s x s value type
+    void* B;        // n x s value type
+    double* M;      // s x s (B^T B), then eigenvectors
+    double* ev;     // s eigenvalues
+    double* gpart;  // partial Gram sums
+    double* scal;   // scalars: [0] ||Y||_F^2, [1] eta, [2] status
+    int* status;
+};
+size_t nystrom_work_bytes(int prec, int64_t m, int64_t n, int sk);
+NysWork nystrom_carve(void* base, int prec, int64_t m, int64_t n, int sk);
+// Builds U (n x s) and lam (s, descending) for H = A^T diag(d) A; returns cudaSuccess and
+// *chol_ok = 1 on success (the shift is raised up to 6 times if the Cholesky fails).
+cudaError_t nystrom_build(int prec, int64_t m, int64_t n, int sk, const void* A, int64_t lda,
+                          const float* row_scale, const void* d, const void* Om, void* U,
+                          double* lam, double* eta_out, NysWork w, int* chol_ok, cudaStream_t s);
+
+}  // namespace genios

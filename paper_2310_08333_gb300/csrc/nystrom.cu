@@ -1,0 +1,763 @@
+// Randomized Nystrom approximation of A^T diag(d) A (§2.2, §3.3) and the test matrix (sm_103a).
+//
+//   Omega   : Philox4x32-10 (Salmon et al. 2011) + Box-Muller standard normals.
+//   sketch  : W = A Omega (m x s), W <- diag(d) W, Y = A^T W (n x s)    [tiled CUDA-core GEMMs]
+//   core    : eta = sqrt(n) eps ||Y||_F; Y_eta = Y + eta Omega; G = Omega^T Y_eta (FP64 sums);
+//             G = C^T C (FP64 Cholesky, one CTA); B = Y_eta C^{-1}; B^T B = V Sigma^2 V^T
+//             (cyclic Jacobi with round-robin parallel ordering, Golub & Van Loan §8.5, FP64,
+//             one CTA); U = B V Sigma^{-1}; lam = max(Sigma^2 - eta, 0), sorted descending.
+// The shift uses the machine epsilon of the value type (float64 or float32).
+#include "common.cuh"
+#include "internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+namespace genios {
+
+static bool sync_check();
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10
+// ------------------------------------------------------------------------------------------
+GENIOS_DEV uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        if (r < 9) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+    }
+    return c;
+}
+
+__global__ void philox_kernel(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                              uint32_t k1, int64_t nb, uint32_t* out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint4 r = philox4x32_10(make_uint4(c0 + (uint32_t)i, c1, c2, c3), make_uint2(k0, k1));
+        out[4 * i + 0] = r.x;
+        out[4 * i + 1] = r.y;
+        out[4 * i + 2] = r.z;
+        out[4 * i + 3] = r.w;
+    }
+}
+
+template <typename VT>
+__global__ void omega_kernel(int64_t total, uint32_t sid, uint32_t k0, uint32_t k1, VT* Om) {
+    const int64_t nb = (total + 3) / 4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint4 r = philox4x32_10(make_uint4((uint32_t)i, sid, 0u, 0u), make_uint2(k0, k1));
+        const double two32 = 4294967296.0;
+        const double ua = ((double)r.x + 0.5) / two32, ub = ((double)r.y + 0.5) / two32;
+        const double uc = ((double)r.z + 0.5) / two32, ud = ((double)r.w + 0.5) / two32;
+        const double ra = sqrt(-2.0 * log(ua)), rb = sqrt(-2.0 * log(uc));
+        double sa, ca, sb, cb;
+        sincospi(2.0 * ub, &sa, &ca);
+        sincospi(2.0 * ud, &sb, &cb);
+        const double g[4] = {ra * ca, ra * sa, rb * cb, rb * sb};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t e = 4 * i + q;
+            if (e < total) Om[e] = (VT)g[q];
+        }
+    }
+}
+
+cudaError_t philox_blocks(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                          uint32_t k1, int64_t nblocks, uint32_t* out, cudaStream_t s) {
+    int grid = (int)std::min<int64_t>(1024, (nblocks + 255) / 256);
+    if (grid < 1) grid = 1;
+    philox_kernel<<<grid, 256, 0, s>>>(c0, c1, c2, c3, k0, k1, nblocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t omega_fill(bool dbl, int64_t n, int sk, uint64_t seed, uint32_t sid, void* Om,
+                       cudaStream_t s) {
+    const int64_t total = n * (int64_t)sk;
+    int grid = (int)std::min<int64_t>(2048, ((total + 3) / 4 + 255) / 256);
+    if (grid < 1) grid = 1;
+    const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    if (dbl) omega_kernel<double><<<grid, 256, 0, s>>>(total, sid, k0, k1, static_cast<double*>(Om));
+    else omega_kernel<float><<<grid, 256, 0, s>>>(total, sid, k0, k1, static_cast<float*>(Om));
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Sketch GEMMs (CUDA cores): W = diag(d) A Omega and Y = A^T W.
+// 64 x 64 output tiles, K tiles of 32, 256 threads, 4 x 4 outputs per thread.
+// ------------------------------------------------------------------------------------------
+template <int P> GENIOS_DEV float load_a(const void* A, int64_t idx);
+template <> GENIOS_DEV float load_a<P_FP32>(const void* A, int64_t idx) { return static_cast<const float*>(A)[idx]; }
+template <> GENIOS_DEV float load_a<P_BF16>(const void* A, int64_t idx) {
+    return __bfloat162float(static_cast<const __nv_bfloat16*>(A)[idx]);
+}
+template <> GENIOS_DEV float load_a<P_FP8>(const void* A, int64_t idx) {
+    __half_raw h = __nv_cvt_fp8_to_halfraw(static_cast<const uint8_t*>(A)[idx], __NV_E4M3);
+    return __half2float(*reinterpret_cast<__half*>(&h));
+}
+
+template <int P, typename VT>
+GENIOS_DEV VT load_av(const void* A, int64_t idx) {
+    if constexpr (P == P_FP64) return static_cast<const double*>(A)[idx];
+    else return (VT)load_a<P>(A, idx);
+}
+
+constexpr int GT = 64, GK = 32;
+
+// W[i, c] = d_i * scale_i * sum_k A[i, k] Omega[k, c]
+template <int P, typename VT>
+__global__ void __launch_bounds__(256) sketch_a_omega(int64_t m, int64_t n, int sk, const void* A,
+                                                     int64_t lda, const float* rs, const VT* d,
+                                                     const VT* Om, VT* W) {
+    __shared__ VT As[GK][GT + 1];  // [k][i]
+    __shared__ VT Bs[GK][GT];      // [k][c]
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int64_t i0 = (int64_t)blockIdx.x * GT;
+    const int c0 = blockIdx.y * GT;
+    VT acc[4][4] = {};
+    for (int64_t k0 = 0; k0 < n; k0 += GK) {
+        for (int e = threadIdx.x; e < GT * GK; e += 256) {
+            const int ii = e / GK, kk = e % GK;
+            const int64_t i = i0 + ii, k = k0 + kk;
+            As[kk][ii] = (i < m && k < n) ? load_av<P, VT>(A, i * lda + k) : VT(0);
+        }
+        for (int e = threadIdx.x; e < GT * GK; e += 256) {
+            const int kk = e / GT, cc = e % GT;
+            const int64_t k = k0 + kk;
+            const int c = c0 + cc;
+            Bs[kk][cc] = (k < n && c < sk) ? Om[k * sk + c] : VT(0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < GK; ++kk) {
+            VT a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t i = i0 + ty * 4 + r;
+        if (i >= m) continue;
+        VT sc = d != nullptr ? d[i] : VT(1);
+        if constexpr (P == P_FP8) sc *= (VT)rs[i];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int cc = c0 + tx * 4 + c;
+            if (cc < sk) W[i * sk + cc] = acc[r][c] * sc;
+        }
+    }
+}
+
+// Y[j, c] = sum_i A[i, j] scale_i W[i, c]
+template <int P, typename VT>
+__global__ void __launch_bounds__(256) sketch_at_w(int64_t m, int64_t n, int sk, const void* A,
+                                                  int64_t lda, const float* rs, const VT* W, VT* Y) {
+    __shared__ VT As[GK][GT + 1];  // [i][j]
+    __shared__ VT Bs[GK][GT];      // [i][c]
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int64_t j0 = (int64_t)blockIdx.x * GT;
+    const int c0 = blockIdx.y * GT;
+    VT acc[4][4] = {};
+    for (int64_t i0 = 0; i0 < m; i0 += GK) {
+        for (int e = threadIdx.x; e < GT * GK; e += 256) {
+            const int ii = e / GT, jj = e % GT;
+            const int64_t i = i0 + ii, j = j0 + jj;
+            VT v = (i < m && j < n) ? load_av<P, VT>(A, i * lda + j) : VT(0);
+            if constexpr (P == P_FP8) v = (i < m) ? v * (VT)rs[i] : v;
+            As[ii][jj] = v;
+        }
+        for (int e = threadIdx.x; e < GT * GK; e += 256) {
+            const int ii = e / GT, cc = e % GT;
+            const int64_t i = i0 + ii;
+            const int c = c0 + cc;
+            Bs[ii][cc] = (i < m && c < sk) ? W[i * sk + c] : VT(0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int ii = 0; ii < GK; ++ii) {
+            VT a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[ii][ty * 4 + r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[ii][tx * 4 + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t j = j0 + ty * 4 + r;
+        if (j >= n) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int cc = c0 + tx * 4 + c;
+            if (cc < sk) Y[j * sk + cc] = acc[r][c];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Tall-skinny helpers
+// ------------------------------------------------------------------------------------------
+// sum of squares of an n x s matrix -> out (double), deterministic two-level
+template <typename VT>
+__global__ void sumsq_kernel(int64_t total, const VT* X, double* part, unsigned* counter, double* out) {
+    double v[1] = {0.0};
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double x = (double)X[e];
+        v[0] += x * x;
+    }
+    double o[1];
+    if (grid_sum<1>(v, part, counter, o))
+        if (threadIdx.x == 0) *out = o[0];
+}
+
+// Yeta = Y + eta * Omega, eta = sqrt(n) * eps * sqrt(fro2) * mult (written to eta_out by block 0)
+template <typename VT>
+__global__ void shift_kernel(int64_t total, int64_t n, double eps, double mult, const double* fro2,
+                             const VT* Y, const VT* Om, VT* Ye, double* eta_out) {
+    const double eta = sqrt((double)n) * eps * sqrt(*fro2) * mult;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *eta_out = eta;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x)
+        Ye[e] = Y[e] + (VT)eta * Om[e];
+}
+
+// Gram partials: part[b][a*s + c] = sum over the block's rows of X[j,a] * Y[j,c] (float64)
+constexpr int GR_THREADS = 512, GR_ROWS = 16, GR_EPT = 32;
+template <typename VT>
+__global__ void __launch_bounds__(GR_THREADS) gram_partial(int64_t n, int sk, const VT* X,
+                                                          const VT* Y, double* part) {
+    extern __shared__ __align__(16) unsigned char gsm[];
+    VT* xs = reinterpret_cast<VT*>(gsm);
+    VT* ys = xs + GR_ROWS * sk;
+    const int ss = sk * sk;
+    const int64_t rows_per_block = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t j0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t j1 = min(n, j0 + rows_per_block);
+    double accd[GR_EPT];
+    VT acc[GR_EPT];
+#pragma unroll
+    for (int q = 0; q < GR_EPT; ++q) accd[q] = 0.0;
+    for (int64_t jt = j0; jt < j1; jt += GR_ROWS) {
+        const int rows = (int)min((int64_t)GR_ROWS, j1 - jt);
+        for (int e = threadIdx.x; e < GR_ROWS * sk; e += GR_THREADS) {
+            const int r = e / sk;
+            xs[e] = r < rows ? X[(jt + r) * sk + e % sk] : VT(0);
+            ys[e] = r < rows ? Y[(jt + r) * sk + e % sk] : VT(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < GR_EPT; ++q) acc[q] = VT(0);
+        for (int r = 0; r < GR_ROWS; ++r) {
+#pragma unroll
+            for (int q = 0; q < GR_EPT; ++q) {
+                const int e = threadIdx.x + q * GR_THREADS;
+                if (e < ss) acc[q] = fma(xs[r * sk + e / sk], ys[r * sk + e % sk], acc[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < GR_EPT; ++q) accd[q] += (double)acc[q];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < GR_EPT; ++q) {
+        const int e = threadIdx.x + q * GR_THREADS;
+        if (e < ss) part[(int64_t)blockIdx.x * ss + e] = accd[q];
+    }
+}
+
+__global__ void gram_reduce(int nb, int ss, const double* part, double* G, int symmetrize, int sk) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ss; e += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int b = 0; b < nb; ++b) acc += part[(int64_t)b * ss + e];
+        G[e] = acc;
+    }
+    (void)symmetrize;
+    (void)sk;
+}
+
+// C (n x s) = X (n x s) * Wm (s x s, value type), 16 rows per block, in place allowed
+template <typename VT>
+__global__ void __launch_bounds__(256) ts_gemm(int64_t n, int sk, const VT* X, const VT* Wm, VT* Cout) {
+    extern __shared__ __align__(16) unsigned char tsm[];
+    VT* ws = reinterpret_cast<VT*>(tsm);
+    VT* xs = ws + sk * sk;
+    for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) ws[e] = Wm[e];
+    for (int64_t j0 = (int64_t)blockIdx.x * 16; j0 < n; j0 += (int64_t)gridDim.x * 16) {
+        const int rows = (int)min((int64_t)16, n - j0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 16 * sk; e += blockDim.x) {
+            const int r = e / sk;
+            xs[e] = r < rows ? X[(j0 + r) * sk + e % sk] : VT(0);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * sk; e += blockDim.x) {
+            const int r = e / sk, c = e % sk;
+            VT acc = VT(0);
+            for (int k = 0; k < sk; ++k) acc = fma(xs[r * sk + k], ws[k * sk + c], acc);
+            Cout[(j0 + r) * sk + c] = acc;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// One-CTA FP64 kernels on s x s matrices (s <= 256)
+// ------------------------------------------------------------------------------------------
+// In: G (s x s, symmetric part used).  Out: Cinv (value type, upper triangular inverse of the
+// Cholesky factor C with G = C^T C); status[0] = 1 on success, 0 if G is not positive definite.
+template <typename VT>
+__global__ void __launch_bounds__(1024) chol_inv_kernel(int sk, const double* G, double* Cw, VT* Cinv,
+                                                       int* status) {
+    extern __shared__ __align__(16) unsigned char csm[];
+    double* c = reinterpret_cast<double*>(csm);  // s x s
+    __shared__ int ok;
+    for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) {
+        const int i = e / sk, j = e % sk;
+        c[e] = 0.5 * (G[i * sk + j] + G[j * sk + i]);
+    }
+    if (threadIdx.x == 0) ok = 1;
+    __syncthreads();
+    for (int k = 0; k < sk; ++k) {
+        if (threadIdx.x == 0) {
+            const double d = c[k * sk + k];
+            if (!(d > 0.0)) ok = 0;
+            c[k * sk + k] = d > 0.0 ? sqrt(d) : 1.0;
+        }
+        __syncthreads();
+        if (!ok) break;
+        const double piv = c[k * sk + k];
+        for (int j = k + 1 + threadIdx.x; j < sk; j += blockDim.x) c[k * sk + j] /= piv;
+        __syncthreads();
+        const int rem = sk - k - 1;
+        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+            const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+            if (j >= i) c[i * sk + j] -= c[k * sk + i] * c[k * sk + j];
+        }
+        __syncthreads();
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) status[0] = 0;
+        return;
+    }
+    // upper-triangular inverse, one column per thread (back substitution C X = I)
+    for (int j = threadIdx.x; j < sk; j += blockDim.x) {
+        for (int i = sk - 1; i >= 0; --i) {
+            double acc = (i == j) ? 1.0 : 0.0;
+            if (i > j) {
+                Cw[i * sk + j] = 0.0;
+                continue;
+            }
+            for (int l = i + 1; l <= j; ++l) acc -= c[i * sk + l] * Cw[l * sk + j];
+            Cw[i * sk + j] = acc / c[i * sk + i];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) Cinv[e] = (VT)Cw[e];
+    if (threadIdx.x == 0) status[0] = 1;
+}
+
+// Cyclic Jacobi eigendecomposition of the symmetric s x s matrix M (FP64, one CTA).
+// Round-robin ordering: each round rotates s/2 disjoint pairs in parallel.
+// Out: V (s x s, global, columns = eigenvectors), ev (s eigenvalues, unsorted).
+__global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min, double* V, double* ev,
+                                                     int max_sweeps, double rel_tol) {
+    extern __shared__ __align__(16) unsigned char jsm[];
+    const int se = sk + (sk & 1);  // even size (dummy index se-1 when s is odd)
+    double* M = reinterpret_cast<double*>(jsm);        // s x s
+    double* cs = M + sk * sk;                           // se/2
+    double* sn = cs + se / 2;                           // se/2
+    int* pos = reinterpret_cast<int*>(sn + se / 2);     // se
+    int* pp = pos + se;                                 // se/2
+    int* qq = pp + se / 2;                              // se/2
+    __shared__ int done;
+    for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) {
+        const int i = e / sk, j = e % sk;
+        M[e] = 0.5 * (Min[i * sk + j] + Min[j * sk + i]);
+        V[e] = (i == j) ? 1.0 : 0.0;
+    }
+    for (int e = threadIdx.x; e < se; e += blockDim.x) pos[e] = e;
+    __syncthreads();
+    const int half = se / 2;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        // convergence: off-diagonal vs total Frobenius norm
+        double off = 0.0, tot = 0.0;
+        for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) {
+            const double v = M[e] * M[e];
+            tot += v;
+            if (e / sk != e % sk) off += v;
+        }
+        double a2[2] = {off, tot};
+        block_sum<2>(a2);
+        if (threadIdx.x == 0) done = (a2[0] <= rel_tol * rel_tol * a2[1]) ? 1 : 0;
+        __syncthreads();
+        if (done) break;
+        for (int round = 0; round < se - 1; ++round) {
+            for (int k = threadIdx.x; k < half; k += blockDim.x) {
+                int p = pos[k], q = pos[se - 1 - k];
+                if (p > q) { int t = p; p = q; q = t; }
+                double c = 1.0, s = 0.0;
+                if (q < sk) {
+                    const double apq = M[p * sk + q];
+                    if (fabs(apq) > 1e-300) {
+                        const double tau = (M[q * sk + q] - M[p * sk + p]) / (2.0 * apq);
+                        const double t = tau >= 0.0 ? 1.0 / (tau + sqrt(1.0 + tau * tau))
+                                                    : -1.0 / (-tau + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                    }
+                }
+                cs[k] = c; sn[k] = s; pp[k] = p; qq[k] = q;
+            }
+            __syncthreads();
+            // rows: M <- J^T M
+            for (int e = threadIdx.x; e < half * sk; e += blockDim.x) {
+                const int k = e / sk, j = e % sk;
+                const int p = pp[k], q = qq[k];
+                if (q >= sk || sn[k] == 0.0) continue;
+                const double mp = M[p * sk + j], mq = M[q * sk + j];
+                M[p * sk + j] = cs[k] * mp - sn[k] * mq;
+                M[q * sk + j] = sn[k] * mp + cs[k] * mq;
+            }
+            __syncthreads();
+            // columns: M <- M J, V <- V J
+            for (int e = threadIdx.x; e < half * sk; e += blockDim.x) {
+                const int k = e / sk, i = e % sk;
+                const int p = pp[k], q = qq[k];
+                if (q >= sk || sn[k] == 0.0) continue;
+                const double mp = M[i * sk + p], mq = M[i * sk + q];
+                M[i * sk + p] = cs[k] * mp - sn[k] * mq;
+                M[i * sk + q] = sn[k] * mp + cs[k] * mq;
+                const double vp = V[i * sk + p], vq = V[i * sk + q];
+                V[i * sk + p] = cs[k] * vp - sn[k] * vq;
+                V[i * sk + q] = sn[k] * vp + cs[k] * vq;
+            }
+            __syncthreads();
+            // rotate positions 1..se-1 (position 0 fixed)
+            if (threadIdx.x == 0) {
+                const int last = pos[se - 1];
+                for (int t = se - 1; t > 1; --t) pos[t] = pos[t - 1];
+                pos[1] = last;
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = threadIdx.x; e < sk; e += blockDim.x) ev[e] = M[e * sk + e];
+}
+
+// Sort eigenpairs descending; Vs[k][c] = V[k][perm c] / sigma_c (value type);
+// lam[c] = max(ev[perm c] - eta, 0).  One CTA.
+template <typename VT>
+__global__ void eig_finish_kernel(int sk, const double* V, const double* ev, const double* eta,
+                                  VT* Vs, double* lam) {
+    __shared__ int perm[256];
+    __shared__ double sig[256];
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < sk; ++c) perm[c] = c;
+        for (int a = 0; a < sk; ++a) {  // selection sort, descending
+            int best = a;
+            for (int b = a + 1; b < sk; ++b)
+                if (ev[perm[b]] > ev[perm[best]]) best = b;
+            const int t = perm[a]; perm[a] = perm[best]; perm[best] = t;
+        }
+    }
+    __syncthreads();
+    const double e0 = fmax(ev[perm[0]], 0.0);
+    for (int c = threadIdx.x; c < sk; c += blockDim.x) {
+        const double e = ev[perm[c]];
+        sig[c] = (e > 1e-30 * e0 && e > 0.0) ? sqrt(e) : 0.0;
+        lam[c] = fmax(e - *eta, 0.0);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) {
+        const int k = e / sk, c = e % sk;
+        Vs[e] = sig[c] > 0.0 ? (VT)(V[k * sk + perm[c]] / sig[c]) : VT(0);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// host orchestration
+// ------------------------------------------------------------------------------------------
+static size_t al(size_t b) { return (b + 255) & ~size_t(255); }
+static int gram_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(128, n / 64)); }
+
+size_t nystrom_work_bytes(int prec, int64_t m, int64_t n, int sk) {
+    const size_t vt = prec == P_FP64 ? 8 : 4;
+    const size_t ss = (size_t)sk * sk;
+    size_t b = 0;
+    b += al(n * sk * vt);         // Oq
+    b += al(m * sk * vt);         // W
+    b += al(n * sk * vt);         // Y
+    b += al(n * sk * vt);         // B (Y_eta, then B)
+    b += al(ss * 8) * 3;          // G, C, M
+    b += al(ss * vt);             // Cinv / Vs
+    b += al(sk * 8);              // ev
+    b += al(std::max<size_t>(gram_blocks(n) * ss, 1024) * 8);  // gpart
+    b += al(64 * 8);              // scal
+    b += al(64);                  // status
+    b += al(ss * 8);              // V
+    return b;
+}
+
+NysWork nystrom_carve(void* base, int prec, int64_t m, int64_t n, int sk) {
+    const size_t vt = prec == P_FP64 ? 8 : 4;
+    const size_t ss = (size_t)sk * sk;
+    char* p = static_cast<char*>(base);
+    NysWork w{};
+    w.Oq = p; p += al(n * sk * vt);
+    w.W = p; p += al(m * sk * vt);
+    w.Y = p; p += al(n * sk * vt);
+    w.B = p; p += al(n * sk * vt);
+    w.G = reinterpret_cast<double*>(p); p += al(ss * 8);
+    w.C = reinterpret_cast<double*>(p); p += al(ss * 8);
+    w.M = reinterpret_cast<double*>(p); p += al(ss * 8);
+    w.Cinv = p; p += al(ss * vt);
+    w.ev = reinterpret_cast<double*>(p); p += al(sk * 8);
+    w.gpart = reinterpret_cast<double*>(p); p += al(std::max<size_t>(gram_blocks(n) * ss, 1024) * 8);
+    w.scal = reinterpret_cast<double*>(p); p += al(64 * 8);
+    w.status = reinterpret_cast<int*>(p); p += al(64);
+    // V shares the tail
+    return w;
+}
+
+template <int P, typename VT>
+static void launch_sketch(int64_t m, int64_t n, int sk, const void* A, int64_t lda,
+                          const float* rs, const VT* d, const VT* Om, VT* W, VT* Y, cudaStream_t s) {
+    dim3 g1((unsigned)((m + GT - 1) / GT), (unsigned)((sk + GT - 1) / GT));
+    sketch_a_omega<P, VT><<<g1, 256, 0, s>>>(m, n, sk, A, lda, rs, d, Om, W);
+    dim3 g2((unsigned)((n + GT - 1) / GT), (unsigned)((sk + GT - 1) / GT));
+    sketch_at_w<P, VT><<<g2, 256, 0, s>>>(m, n, sk, A, lda, rs, W, Y);
+    if (sync_check()) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) std::fprintf(stderr, "[genios] sketch: %s\n", cudaGetErrorString(e));
+    }
+}
+
+// GENIOS_SYNC_CHECK=1 synchronises after every kernel of the core and reports the first
+// failing one (diagnostics only; off by default).
+static bool sync_check() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("GENIOS_SYNC_CHECK");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v == 1;
+}
+#define NYS_CHECK(name)                                                                     \
+    do {                                                                                    \
+        if (sync_check()) {                                                                 \
+            cudaError_t _e = cudaStreamSynchronize(s);                                      \
+            if (_e == cudaSuccess) _e = cudaGetLastError();                                 \
+            if (_e != cudaSuccess) {                                                        \
+                std::fprintf(stderr, "[genios] nystrom kernel %s: %s\n", name,              \
+                             cudaGetErrorString(_e));                                       \
+                return _e;                                                                  \
+            }                                                                               \
+        }                                                                                   \
+    } while (0)
+
+// Oq = orthonormal basis of range(Om) by CholeskyQR2: twice { G = Q^T Q (float64 sums);
+// G = R^T R; Q <- Q R^{-1} }.  A Gaussian n x s matrix with s << n is well conditioned, so
+// Cholesky QR is stable here and the second pass brings Q^T Q to the working precision.
+template <typename VT>
+static cudaError_t orthonormalize(int64_t n, int sk, const VT* Om, NysWork w, cudaStream_t s) {
+    const int ss = sk * sk;
+    const int gb = gram_blocks(n);
+    const size_t gsm = 2 * GR_ROWS * sk * sizeof(VT);
+    const size_t tsm = (size_t)(sk * sk + 16 * sk) * sizeof(VT);
+    const size_t csm = (size_t)ss * 8;
+    cudaFuncSetAttribute(ts_gemm<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm + 1024);
+    cudaFuncSetAttribute(chol_inv_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm + 1024);
+    cudaFuncSetAttribute(gram_partial<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm + 1024);
+    VT* Q = static_cast<VT*>(w.Oq);
+    VT* Rinv = static_cast<VT*>(w.Cinv);
+    const VT* src = Om;
+    for (int pass = 0; pass < 2; ++pass) {
+        gram_partial<VT><<<gb, GR_THREADS, gsm, s>>>(n, sk, src, src, w.gpart);
+        gram_reduce<<<(ss + 255) / 256, 256, 0, s>>>(gb, ss, w.gpart, w.G, 1, sk);
+        chol_inv_kernel<VT><<<1, 1024, csm, s>>>(sk, w.G, w.M, Rinv, w.status);
+        NYS_CHECK("orthonormalize");
+        ts_gemm<VT><<<512, 256, tsm, s>>>(n, sk, src, Rinv, Q);
+        NYS_CHECK("orthonormalize ts_gemm");
+        src = Q;
+    }
+    return cudaGetLastError();
+}
+
+template <typename VT>
+static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U, double* lam,
+                        double* eta_out, int* chol_ok, cudaStream_t s) {
+    const int64_t total = n * sk;
+    const double eps = sizeof(VT) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
+    double* fro2 = w.scal;
+    double* eta = w.scal + 1;
+    unsigned* counter = reinterpret_cast<unsigned*>(w.scal + 8);
+    cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+    // partials for the sum of squares reuse gpart (>= 1024 doubles as gram_blocks*ss >= s^2)
+    sumsq_kernel<VT><<<256, 256, 0, s>>>(total, Y, w.gpart, counter, fro2);
+    NYS_CHECK("sumsq");
+    const int ss = sk * sk;
+    const int gb = gram_blocks(n);
+    const size_t gsm = 2 * GR_ROWS * sk * sizeof(VT);
+    const size_t tsm = (size_t)(sk * sk + 16 * sk) * sizeof(VT);
+    const size_t csm = (size_t)ss * 8;
+    const int se = sk + (sk & 1);
+    const size_t jsm = (size_t)ss * 8 + (size_t)se * 8 + (size_t)se * 4 * 2 + 64;
+    cudaFuncSetAttribute(ts_gemm<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm + 1024);
+    cudaFuncSetAttribute(chol_inv_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm + 1024);
+    cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm + 1024);
+    cudaFuncSetAttribute(gram_partial<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm + 1024);
+    VT* Ye = static_cast<VT*>(w.B);
+    VT* Cinv = static_cast<VT*>(w.Cinv);
+    double* V = w.C;  // reuse: C scratch holds eigenvectors after the Cholesky stage
+    *chol_ok = 0;
+    double mult = 1.0;
+    for (int attempt = 0; attempt < 7; ++attempt, mult *= 10.0) {
+        shift_kernel<VT><<<512, 256, 0, s>>>(total, n, eps, mult, fro2, Y, Om, Ye, eta);
+        NYS_CHECK("shift");
+        gram_partial<VT><<<gb, GR_THREADS, gsm, s>>>(n, sk, Om, Ye, w.gpart);
+        NYS_CHECK("gram_partial(Omega, Y_eta)");
+        gram_reduce<<<(ss + 255) / 256, 256, 0, s>>>(gb, ss, w.gpart, w.G, 1, sk);
+        NYS_CHECK("gram_reduce");
+        chol_inv_kernel<VT><<<1, 1024, csm, s>>>(sk, w.G, w.M, Cinv, w.status);
+        NYS_CHECK("chol_inv");
+        int st = 0;
+        cudaMemcpyAsync(&st, w.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        if (st == 1) {
+            *chol_ok = 1;
+            break;
+        }
+    }
+    if (!*chol_ok) return cudaSuccess;
+    // B = Y_eta C^{-1} (in place)
+    ts_gemm<VT><<<512, 256, tsm, s>>>(n, sk, Ye, Cinv, Ye);
+    NYS_CHECK("ts_gemm(B)");
+    // M = B^T B
+    gram_partial<VT><<<gb, GR_THREADS, gsm, s>>>(n, sk, Ye, Ye, w.gpart);
+    NYS_CHECK("gram_partial(B, B)");
+    gram_reduce<<<(ss + 255) / 256, 256, 0, s>>>(gb, ss, w.gpart, w.M, 1, sk);
+    NYS_CHECK("gram_reduce(M)");
+    jacobi_kernel<<<1, 1024, jsm, s>>>(sk, w.M, V, w.ev, 40, 1e-15);
+    NYS_CHECK("jacobi");
+    eig_finish_kernel<VT><<<1, 256, 0, s>>>(sk, V, w.ev, eta, Cinv, lam);
+    NYS_CHECK("eig_finish");
+    // U = B V Sigma^{-1}
+    ts_gemm<VT><<<512, 256, tsm, s>>>(n, sk, Ye, Cinv, U);
+    NYS_CHECK("ts_gemm(U)");
+    if (eta_out) cudaMemcpyAsync(eta_out, eta, sizeof(double), cudaMemcpyDeviceToDevice, s);
+    return cudaGetLastError();
+}
+
+cudaError_t nystrom_build(int prec, int64_t m, int64_t n, int sk, const void* A, int64_t lda,
+                          const float* rs, const void* d, const void* Om, void* U, double* lam,
+                          double* eta_out, NysWork w, int* chol_ok, cudaStream_t s) {
+    if (sk < 1 || sk > 128) return cudaErrorInvalidValue;
+    if (prec == P_FP64) {
+        cudaError_t e = orthonormalize<double>(n, sk, static_cast<const double*>(Om), w, s);
+        if (e != cudaSuccess) return e;
+        const double* Oq = static_cast<const double*>(w.Oq);
+        launch_sketch<P_FP64, double>(m, n, sk, A, lda, rs, static_cast<const double*>(d), Oq,
+                                      static_cast<double*>(w.W), static_cast<double*>(w.Y), s);
+        return core<double>(n, sk, Oq, static_cast<double*>(w.Y), w, static_cast<double*>(U), lam,
+                            eta_out, chol_ok, s);
+    }
+    const float* df = static_cast<const float*>(d);
+    cudaError_t e = orthonormalize<float>(n, sk, static_cast<const float*>(Om), w, s);
+    if (e != cudaSuccess) return e;
+    const float* Of = static_cast<const float*>(w.Oq);
+    float* Wf = static_cast<float*>(w.W);
+    float* Yf = static_cast<float*>(w.Y);
+    if (prec == P_FP32) launch_sketch<P_FP32, float>(m, n, sk, A, lda, rs, df, Of, Wf, Yf, s);
+    else if (prec == P_BF16) launch_sketch<P_BF16, float>(m, n, sk, A, lda, rs, df, Of, Wf, Yf, s);
+    else if (prec == P_FP8) launch_sketch<P_FP8, float>(m, n, sk, A, lda, rs, df, Of, Wf, Yf, s);
+    else return cudaErrorInvalidValue;
+    return core<float>(n, sk, Of, Yf, w, static_cast<float*>(U), lam, eta_out, chol_ok, s);
+}
+
+// ------------------------------------------------------------------------------------------
+// Quantisation of a float32 matrix (setup)
+// ------------------------------------------------------------------------------------------
+__global__ void bf16_hilo_kernel(int64_t m, int64_t n, const float* A, int64_t ldi,
+                                 __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo) {
+    const int64_t total = m * ldo;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / ldo, j = e % ldo;
+        const float a = j < n ? A[i * ldi + j] : 0.0f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(a);
+        hi[e] = h;
+        lo[e] = __float2bfloat16_rn(a - __bfloat162float(h));
+    }
+}
+
+__global__ void fp8_rows_kernel(int64_t m, int64_t n, const float* A, int64_t ldi, uint8_t* q,
+                                float* scale, int64_t ldo) {
+    __shared__ float red[32];
+    for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+        float mx = 0.0f;
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) mx = fmaxf(mx, fabsf(A[i * ldi + j]));
+        mx = warp_max(mx);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            float t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+            t = warp_max(t);
+            if (threadIdx.x == 0) red[0] = t;
+        }
+        __syncthreads();
+        const float amax = red[0];
+        float sc = __fdiv_rn(amax, 448.0f);
+        if (sc == 0.0f) sc = 1.0f;
+        if (threadIdx.x == 0) scale[i] = sc;
+        for (int64_t j = threadIdx.x; j < ldo; j += blockDim.x) {
+            uint8_t code = 0;
+            if (j < n) {
+                const float v = __fdiv_rn(A[i * ldi + j], sc);
+                code = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+            }
+            q[i * ldo + j] = code;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t quantize_bf16_hilo(int64_t m, int64_t n, const float* A, int64_t lda_in, void* hi,
+                               void* lo, int64_t lda_out, cudaStream_t s) {
+    const int64_t total = m * lda_out;
+    int grid = (int)std::min<int64_t>(152 * 32, (total + 255) / 256);
+    if (grid < 1) grid = 1;
+    bf16_hilo_kernel<<<grid, 256, 0, s>>>(m, n, A, lda_in, static_cast<__nv_bfloat16*>(hi),
+                                          static_cast<__nv_bfloat16*>(lo), lda_out);
+    return cudaGetLastError();
+}
+
+cudaError_t quantize_fp8_rows(int64_t m, int64_t n, const float* A, int64_t lda_in, uint8_t* q,
+                              float* scale, int64_t lda_out, cudaStream_t s) {
+    int grid = (int)std::min<int64_t>(152 * 16, m);
+    if (grid < 1) grid = 1;
+    fp8_rows_kernel<<<grid, 256, 0, s>>>(m, n, A, lda_in, q, scale, lda_out);
+    return cudaGetLastError();
+}
+
+}  // namespace genios

@@ -1,0 +1,374 @@
+// Fused single-pass "rowpass" over a dense row-major A (sm_103a).
+//
+// For each row i it forms t_i = a_i^T v, a row weight w_i = phi(t_i), and accumulates
+// y += w_i a_i, reading every element of A from HBM exactly once:
+//   RP_HV   : w_i = d_i t_i                  -> y = A^T diag(d) A v  (§3.1 HessianOperator as
+//             one pass instead of two mat-vecs; §3.3 Hessian A^T diag(l'') A)
+//   RP_GRAD : w_i = l'(t_i - b_i), also l''(t_i - b_i) and l(t_i - b_i)
+//             -> y = A^T l'(Av - b)            (§3.3 gradient)
+//
+// Structure per CTA (one CTA per SM, persistent over a contiguous block of rows):
+//   * a producer warp streams stages of whole rows (contiguous bytes) into shared memory with
+//     cp.async.bulk, completion tracked by "full" mbarriers; consumers release a stage
+//     through "empty" mbarriers (ring of 2..8 stages);
+//   * 16 consumer warps own 16-byte column chunks of the row (thread t: chunks t, t+512, ...),
+//     keep their slice of v and of the partial y in registers, and reduce the row dot
+//     products with warp shuffles plus one named barrier per group of RB rows;
+//   * each CTA writes its partial y (n values) once; a separate finish kernel sums the
+//     partials in a fixed order (deterministic) and applies the diagonal / gradient terms.
+// Every mbarrier wait is bounded (clock64 limit) and reports DERR_TIMEOUT_* on expiry.
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+
+namespace genios {
+
+constexpr int RP_CWARPS = 16;
+constexpr int RP_CTHREADS = RP_CWARPS * 32;
+constexpr int RP_THREADS = RP_CTHREADS + 32;
+constexpr size_t RP_SMEM_BUDGET = 220 * 1024;
+constexpr size_t RP_STAGE_TARGET = 48 * 1024;
+
+// rows per barrier group: 8 held 16-byte chunks per thread, halved for the FP8 and split-BF16
+// streams whose chunks expand to 16 / 2 x 8 values (register pressure)
+__host__ __device__ constexpr int rp_rb(int prec, int nch) {
+    return (nch >= 8 ? 1 : (8 / nch)) / ((prec == P_FP8 || prec == P_HILO) && nch < 8 ? 2 : 1) > 0
+               ? (nch >= 8 ? 1 : (8 / nch)) / ((prec == P_FP8 || prec == P_HILO) && nch < 8 ? 2 : 1)
+               : 1;
+}
+
+template <int P, int NCH, int MODE>
+__global__ void __launch_bounds__(RP_THREADS, 1)
+rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
+    using AS = AStore<P>;
+    constexpr int VEC = AS::VEC;
+    using VT = typename VType<P>::T;
+    constexpr bool HILO = (P == P_HILO);
+    constexpr bool FP8 = (P == P_FP8);
+    constexpr int RB = rp_rb(P, NCH);
+    constexpr bool HOLD = (NCH * RB <= 8);
+    constexpr int SPLIT = HILO ? 2 : 1;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x;
+    const int64_t row_bytes = a.lda * (int64_t)sizeof(typename AS::T);
+    const int nchunk_row = (int)(row_bytes / 16);
+    const int64_t stage_bytes = (int64_t)rps * row_bytes * SPLIT;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nst_cap * stage_bytes);
+    uint64_t* empty = full + nst_cap;
+    VT* red = reinterpret_cast<VT*>(empty + nst_cap);  // [2][RB][RP_CWARPS]
+
+    if (a.skip != nullptr && *a.skip != 0) return;  // uniform across the block
+
+    const int64_t G = gridDim.x;
+    const int64_t r0 = (a.m * (int64_t)blockIdx.x) / G;
+    const int64_t r1 = (a.m * ((int64_t)blockIdx.x + 1)) / G;
+    const int64_t nrows = r1 - r0;
+    const int nstage_work = (int)((nrows + rps - 1) / rps);
+
+    if (tid == 0) {
+        for (int s = 0; s < nst_cap; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], RP_CWARPS);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // ------------------------------------------------------------------ producer warp
+    if (tid >= RP_CTHREADS) {
+        if (tid == RP_CTHREADS) {
+            const char* Ab = static_cast<const char*>(a.A);
+            const char* Al = static_cast<const char*>(a.A_lo);
+            for (int st = 0; st < nstage_work; ++st) {
+                const int s = st % nst_cap;
+                const int use = st / nst_cap;
+                if (use > 0 && !mbar_wait_bounded(&empty[s], (uint32_t)((use - 1) & 1), a.wait_limit)) {
+                    set_err(a.err, DERR_TIMEOUT_EMPTY);
+                    break;
+                }
+                const int64_t rows = min((int64_t)rps, nrows - (int64_t)st * rps);
+                const uint32_t bytes = (uint32_t)(rows * row_bytes);
+                const int64_t off = (r0 + (int64_t)st * rps) * row_bytes;
+                unsigned char* dst = smem + (size_t)s * stage_bytes;
+#ifdef GENIOS_CHECKED
+                if (!GCHK(a.dbg, (long long)s * stage_bytes + (long long)bytes * SPLIT - 1, (long long)nst_cap * stage_bytes) ||
+                    !GCHK(a.dbg, r0 + (long long)st * rps + rows - 1, a.m)) break;
+#endif
+                mbar_arrive_expect_tx(&full[s], bytes * SPLIT);
+                bulk_g2s(dst, Ab + off, bytes, &full[s]);
+                if (HILO) bulk_g2s(dst + (size_t)rps * row_bytes, Al + off, bytes, &full[s]);
+            }
+        }
+        return;
+    }
+
+    // ------------------------------------------------------------------ consumers
+    const int lane = tid & 31, wid = tid >> 5;
+    const VT* vin = static_cast<const VT*>(a.v);
+    const VT* vaux = static_cast<const VT*>(a.v_aux);
+    const VT beta = (vaux != nullptr) ? (VT)(*a.beta) : VT(0);
+    VT vr[NCH][VEC];
+    VT yr[NCH][VEC];
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+        const int c = tid + k * RP_CTHREADS;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            const int64_t j = (int64_t)c * VEC + e;
+            VT val = VT(0);
+            if (c < nchunk_row && j < a.n) {
+                if (GCHK(a.dbg, j, a.n)) {
+                    val = vin[j];
+                    if (vaux != nullptr) val = vaux[j] + beta * val;
+                }
+            }
+            vr[k][e] = val;
+            yr[k][e] = VT(0);
+        }
+    }
+
+    const VT* dvec = static_cast<const VT*>(a.d);
+    const VT* bvec = static_cast<const VT*>(a.b);
+    VT* Wout = static_cast<VT*>(a.W_out);
+    VT* Dout = static_cast<VT*>(a.D_out);
+    double lsum = 0.0;
+    int par = 0;
+
+    for (int st = 0; st < nstage_work; ++st) {
+        const int s = st % nst_cap;
+        const int use = st / nst_cap;
+        // bounded wait; the give-up decision is made block-uniform so that no consumer can be
+        // left alone at the named barrier below
+        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(use & 1), a.wait_limit);
+        if (named_bar_or(2, RP_CTHREADS, !ok)) {
+            set_err(a.err, DERR_TIMEOUT_FULL);
+            break;
+        }
+        const unsigned char* sb = smem + (size_t)s * stage_bytes;
+        const int rows = (int)min((int64_t)rps, nrows - (int64_t)st * rps);
+        for (int rr = 0; rr < rows; rr += RB) {
+            uint4 hold[HOLD ? RB : 1][HOLD ? NCH : 1];
+            uint4 holdlo[(HOLD && HILO) ? RB : 1][(HOLD && HILO) ? NCH : 1];
+            VT dot[RB];
+#pragma unroll
+            for (int q = 0; q < RB; ++q) {
+                dot[q] = VT(0);
+                if (rr + q < rows) {
+                    const unsigned char* rowp = sb + (size_t)(rr + q) * row_bytes;
+#pragma unroll
+                    for (int k = 0; k < NCH; ++k) {
+                        const int c = tid + k * RP_CTHREADS;
+                        if (c < nchunk_row &&
+                            GCHK(a.dbg, (rowp - smem) + (long long)c * 16 + (HILO ? (long long)rps * row_bytes : 0) + 15, a.smem_bytes)) {
+                            const uint4 raw = ld_shared_v4(rowp + (size_t)c * 16);
+                            VT f[VEC];
+                            decode_chunk(raw, f);
+                            if constexpr (HILO) {
+                                const uint4 rl = ld_shared_v4(rowp + (size_t)rps * row_bytes + (size_t)c * 16);
+                                VT g[VEC];
+                                decode_chunk(rl, g);
+#pragma unroll
+                                for (int e = 0; e < VEC; ++e) f[e] += g[e];
+                                if constexpr (HOLD) holdlo[q][k] = rl;
+                            }
+                            if constexpr (HOLD) hold[q][k] = raw;
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) dot[q] = fma(f[e], vr[k][e], dot[q]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RB; ++q) dot[q] = warp_sum(dot[q]);
+            if (lane == 0) {
+#pragma unroll
+                for (int q = 0; q < RB; ++q)
+                    if (GCHK(a.dbg, (long long)(reinterpret_cast<unsigned char*>(red + (par * RB + q) * RP_CWARPS + wid) - smem) + (long long)sizeof(VT) - 1, a.smem_bytes))
+                        red[(par * RB + q) * RP_CWARPS + wid] = dot[q];
+            }
+            named_bar_sync(1, RP_CTHREADS);
+            VT wq[RB];
+#pragma unroll
+            for (int q = 0; q < RB; ++q) {
+                VT t = lane < RP_CWARPS ? red[(par * RB + q) * RP_CWARPS + lane] : VT(0);
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                t = __shfl_sync(0xffffffffu, t, 0);
+                wq[q] = VT(0);
+                if (rr + q < rows) {
+                    const int64_t i = r0 + (int64_t)st * rps + rr + q;
+                    VT sc = VT(1);
+                    if constexpr (FP8) sc = GCHK(a.dbg, i, a.m) ? (VT)__ldg(a.row_scale + i) : VT(1);
+                    t *= sc;
+                    if (MODE == RP_HV) {
+                        VT w = (dvec != nullptr && GCHK(a.dbg, i, a.m)) ? dvec[i] * t : t;
+                        wq[q] = w * sc;
+                    } else {
+                        VT l0, l1, l2;
+                        loss_eval<VT>(a.loss, t - (GCHK(a.dbg, i, a.m) ? bvec[i] : VT(0)), l0, l1, l2);
+                        wq[q] = l1 * sc;
+                        if (tid == 0 && GCHK(a.dbg, i, a.m)) {
+                            if (Wout) Wout[i] = l1;
+                            if (Dout) Dout[i] = l2;
+                            lsum += (double)l0;
+                        }
+                    }
+                }
+            }
+            par ^= 1;
+#pragma unroll
+            for (int q = 0; q < RB; ++q) {
+                if (rr + q < rows) {
+                    const unsigned char* rowp = sb + (size_t)(rr + q) * row_bytes;
+#pragma unroll
+                    for (int k = 0; k < NCH; ++k) {
+                        const int c = tid + k * RP_CTHREADS;
+                        if (c < nchunk_row &&
+                            GCHK(a.dbg, (rowp - smem) + (long long)c * 16 + (HILO ? (long long)rps * row_bytes : 0) + 15, a.smem_bytes)) {
+                            uint4 raw;
+                            if constexpr (HOLD) raw = hold[q][k];
+                            else raw = ld_shared_v4(rowp + (size_t)c * 16);
+                            VT f[VEC];
+                            decode_chunk(raw, f);
+                            if constexpr (HILO) {
+                                uint4 rl;
+                                if constexpr (HOLD) rl = holdlo[q][k];
+                                else rl = ld_shared_v4(rowp + (size_t)rps * row_bytes + (size_t)c * 16);
+                                VT g[VEC];
+                                decode_chunk(rl, g);
+#pragma unroll
+                                for (int e = 0; e < VEC; ++e) f[e] += g[e];
+                            }
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) yr[k][e] = fma(wq[q], f[e], yr[k][e]);
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+
+    VT* Pout = static_cast<VT*>(a.partial) + (int64_t)blockIdx.x * a.ldp;
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+        const int c = tid + k * RP_CTHREADS;
+        if (c < nchunk_row) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const int64_t j = (int64_t)c * VEC + e;
+                if (j < a.ldp && GCHK(a.dbg, (long long)blockIdx.x * a.ldp + j, a.partial_len)) Pout[j] = yr[k][e];
+            }
+        }
+    }
+    if (MODE == RP_GRAD && tid == 0 && a.loss_part != nullptr) a.loss_part[blockIdx.x] = lsum;
+}
+
+// ------------------------------------------------------------------------------------------
+// host side: plan + dispatch
+// ------------------------------------------------------------------------------------------
+static const int kNch[] = {1, 2, 3, 4, 6, 8, 10};
+
+static int max_nch(int prec) { return prec == P_FP64 ? 8 : 10; }
+
+int device_sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+RowpassPlan rowpass_plan(int prec, int64_t m, int64_t n, int64_t lda) {
+    RowpassPlan p{};
+    p.ok = false;
+    const int64_t es = elem_bytes(prec == P_HILO ? P_BF16 : prec);
+    const int64_t row_bytes = lda * es;
+    if (row_bytes % 16 != 0 || lda < n || m < 1 || n < 1) return p;
+    const int64_t nchunks = row_bytes / 16;
+    const int64_t need = (nchunks + RP_CTHREADS - 1) / RP_CTHREADS;
+    int nch = -1;
+    for (int c : kNch)
+        if (c >= need && c <= max_nch(prec)) { nch = c; break; }
+    if (nch < 0) return p;
+    const int rb = rp_rb(prec, nch);
+    const int64_t per_row = row_bytes * (prec == P_HILO ? 2 : 1);
+    int64_t rps = rb * std::max<int64_t>(1, (int64_t)RP_STAGE_TARGET / (rb * per_row));
+    const int sms = device_sm_count();
+    // no stage larger than a CTA's share of rows (rounded up to the barrier group)
+    int64_t share = (m + sms - 1) / sms;
+    share = ((share + rb - 1) / rb) * rb;
+    rps = std::min(rps, std::max<int64_t>(rb, share));
+    const size_t vt = prec == P_FP64 ? 8 : 4;
+    const size_t extra_fixed = 2 * (size_t)rb * RP_CWARPS * vt + 128;
+    int nst = 0;
+    for (;;) {
+        const size_t stage = (size_t)(rps * per_row);
+        nst = (int)std::min<size_t>(8, (RP_SMEM_BUDGET - extra_fixed) / (stage + 16));
+        if (nst >= 2 || rps <= rb) break;
+        rps -= rb;
+    }
+    if (nst < 2) return p;
+    if ((size_t)rps * per_row >= (1u << 20)) return p;  // mbarrier tx-count limit
+    p.nch = nch;
+    p.rb = rb;
+    p.rows_per_stage = (int)rps;
+    p.nstages = nst;
+    p.smem = (size_t)nst * (size_t)(rps * per_row) + (size_t)nst * 16 + extra_fixed;
+    p.grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, (m + rps - 1) / rps));
+    p.ok = true;
+    return p;
+}
+
+template <int P, int NCH, int MODE>
+static cudaError_t launch_one(const RowpassArgs& a, const RowpassPlan& p, cudaStream_t s) {
+    auto kern = rowpass_kernel<P, NCH, MODE>;
+    static bool attr_set = false;  // per instantiation; attribute is per device function
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)RP_SMEM_BUDGET + 4096);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kern<<<p.grid, RP_THREADS, p.smem, s>>>(a, p.rows_per_stage, p.nstages);
+    return cudaGetLastError();
+}
+
+template <int P, int MODE>
+static cudaError_t dispatch_nch(const RowpassArgs& a, const RowpassPlan& p, cudaStream_t s) {
+    switch (p.nch) {
+        case 1: return launch_one<P, 1, MODE>(a, p, s);
+        case 2: return launch_one<P, 2, MODE>(a, p, s);
+        case 3: return launch_one<P, 3, MODE>(a, p, s);
+        case 4: return launch_one<P, 4, MODE>(a, p, s);
+        case 6: return launch_one<P, 6, MODE>(a, p, s);
+        case 8: return launch_one<P, 8, MODE>(a, p, s);
+        case 10:
+            if constexpr (P != P_FP64) return launch_one<P, 10, MODE>(a, p, s);
+            else return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t rowpass_launch(const RowpassArgs& a, const RowpassPlan& p, cudaStream_t s) {
+    if (!p.ok) return cudaErrorInvalidValue;
+    if (a.mode == RP_HV) {
+        switch (a.prec) {
+            case P_FP64: return dispatch_nch<P_FP64, RP_HV>(a, p, s);
+            case P_FP32: return dispatch_nch<P_FP32, RP_HV>(a, p, s);
+            case P_BF16: return dispatch_nch<P_BF16, RP_HV>(a, p, s);
+            case P_FP8:  return dispatch_nch<P_FP8, RP_HV>(a, p, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (a.prec) {
+        case P_FP64: return dispatch_nch<P_FP64, RP_GRAD>(a, p, s);
+        case P_FP32: return dispatch_nch<P_FP32, RP_GRAD>(a, p, s);
+        case P_HILO: return dispatch_nch<P_HILO, RP_GRAD>(a, p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace genios

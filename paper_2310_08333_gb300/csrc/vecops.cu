@@ -1,0 +1,489 @@
+// n-vector and m-vector kernels of the ADMM iteration (sm_103a).
+//
+// All reductions are deterministic: per-block sums in a fixed shape, then the last block to
+// finish adds the block partials in block order (grid_sum).  Scalars that later kernels need
+// stay on the device in DevState.  Kernels of the CG loop return at once when
+// DevState::cg_done is set, so a loop body can be replayed (CUDA graph) after convergence.
+#include "common.cuh"
+#include "internal.h"
+
+namespace genios {
+
+constexpr int VT_THREADS = 256;
+
+static inline int nblocks(int64_t n, int per) { return (int)((n + per - 1) / per); }
+
+// Sum of column j of the G x ldp partial matrix, computed by the 8 warps of a 256-thread block
+// for 32 consecutive columns.  Returns the column sum in warp 0 lanes (others: 0).
+template <typename VT, typename AccT>
+GENIOS_DEV AccT column_sum(const VT* P, int G, int64_t ldp, int64_t j, int64_t n, AccT* sh) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    AccT acc = AccT(0);
+    if (j < n)
+        for (int b = ty; b < G; b += 8) acc += (AccT)P[(int64_t)b * ldp + j];
+    sh[ty * 33 + tx] = acc;
+    __syncthreads();
+    AccT out = AccT(0);
+    if (ty == 0) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) out += sh[k * 33 + tx];
+    }
+    __syncthreads();
+    return out;
+}
+
+// ------------------------------------------------------------------------------------------
+template <typename VT>
+__global__ void hv_finish_kernel(const VT* P, int G, int64_t ldp, int64_t n, double nu,
+                                 const VT* v, VT* y) {
+    __shared__ VT sh[8 * 33];
+    const int64_t j = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+    VT sum = column_sum<VT, VT>(P, G, ldp, j, n, sh);
+    if ((threadIdx.x >> 5) == 0 && j < n) y[j] = sum + (VT)nu * v[j];
+}
+
+template <typename VT>
+__global__ void cg_q_kernel(const VT* P, int G, int64_t ldp, int64_t n, VT* p, const VT* zc, VT* q,
+                            DevState* S, Scratch sc) {
+    if (S->cg_done) return;
+    __shared__ VT sh[8 * 33];
+    const int64_t j = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+    VT sum = column_sum<VT, VT>(P, G, ldp, j, n, sh);
+    double v[1] = {0.0};
+    if ((threadIdx.x >> 5) == 0 && j < n) {
+        const VT pj = zc[j] + (VT)S->beta * p[j];
+        const VT qj = sum + (VT)S->nu * pj;
+        p[j] = pj;
+        q[j] = qj;
+        v[0] = (double)pj * (double)qj;
+    }
+    double out[1];
+    if (grid_sum<1>(v, sc.part, sc.counter, out)) {
+        if (threadIdx.x == 0) {
+            S->pq = out[0];
+            S->alpha = out[0] > 0.0 ? S->rz / out[0] : 0.0;
+            if (!(out[0] > 0.0)) S->cg_done = 1;  // breakdown / exact solution
+        }
+    }
+}
+
+// Block partial of U^T r over the block's 256 rows, plus sum of r^2; last block finalises.
+// Returns true in the last block (after S->w and out2 are final).
+template <typename VT>
+GENIOS_DEV bool ut_r_and_norm(const VT* U, int sk, const VT* rloc_sh, int64_t j0, int64_t n,
+                              double rr_thread, double* part, unsigned* counter,
+                              double* w_out, double& rr_out, long long* dbg) {
+    // rloc_sh: shared copy of r[j0 .. j0+256)
+    const int t = threadIdx.x;
+    double wc = 0.0;
+    if (t < sk) {
+        const int64_t rows = min((int64_t)VT_THREADS, n - j0);
+        for (int64_t jj = 0; jj < rows; ++jj)
+            if (GCHK(dbg, (j0 + jj) * sk + t, n * (long long)sk) && GCHK(dbg, jj, VT_THREADS))
+                wc += (double)U[(j0 + jj) * sk + t] * (double)rloc_sh[jj];
+    }
+    double v[1] = {rr_thread};
+    block_sum<1>(v);
+    const int stride = sk + 1;
+    __shared__ unsigned s_last;
+    __shared__ double s_rr;
+    if (t < sk && GCHK(dbg, (long long)blockIdx.x * stride + t, 262144)) part[(size_t)blockIdx.x * stride + t] = wc;
+    if (t == 0 && GCHK(dbg, (long long)blockIdx.x * stride + sk, 262144)) part[(size_t)blockIdx.x * stride + sk] = v[0];
+    __threadfence();
+    __syncthreads();
+    if (t == 0) {
+        unsigned k = atomicAdd(counter, 1u);
+        s_last = (k == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    for (int c = t; c <= sk; c += blockDim.x) {
+        double acc = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) acc += __ldcg(part + (size_t)b * stride + c);
+        if (c < sk) { if (GCHK(dbg, c, 256)) w_out[c] = acc; }
+        else s_rr = acc;
+    }
+    __syncthreads();
+    rr_out = s_rr;
+    if (t == 0) *counter = 0u;
+    return true;
+}
+
+template <typename VT>
+__global__ void cg_update_kernel(int64_t n, VT* delta, VT* r, const VT* p, const VT* q,
+                                 const VT* U, int sk, VT* zc, DevState* S, Scratch sc) {
+    if (S->cg_done) return;
+    __shared__ VT rsh[VT_THREADS];
+    const int64_t j0 = (int64_t)blockIdx.x * VT_THREADS;
+    const int64_t j = j0 + threadIdx.x;
+    const VT al = (VT)S->alpha;
+    double rr = 0.0;
+    VT rj = VT(0);
+    if (j < n) {
+        delta[j] += al * p[j];
+        rj = r[j] - al * q[j];
+        r[j] = rj;
+        if (sk == 0) zc[j] = rj;
+        rr = (double)rj * (double)rj;
+    }
+    rsh[threadIdx.x] = rj;
+    __syncthreads();
+    double rr_tot;
+    if (ut_r_and_norm<VT>(U, sk, rsh, j0, n, rr, sc.part, sc.counter, S->w, rr_tot, sc.dbg)) {
+        if (threadIdx.x == 0) {
+            S->rr = rr_tot;
+            S->cg_it += 1;
+            if (rr_tot <= S->tol * S->tol * S->rhs2 || S->cg_it >= S->cg_max) S->cg_done = 1;
+            if (sk == 0) {  // no preconditioner: z = r, so r^T z = ||r||^2
+                S->beta = S->rz > 0.0 ? rr_tot / S->rz : 0.0;
+                S->rz = rr_tot;
+            }
+        }
+    }
+}
+
+template <typename VT>
+__global__ void cg_precond_kernel(int64_t n, const VT* U, int sk, const double* lam, const VT* r,
+                                  VT* zc, DevState* S, Scratch sc) {
+    if (S->cg_done) return;
+    __shared__ double coefw[256];
+    const double nu = S->nu;
+    const double ls = lam[sk - 1];
+    for (int c = threadIdx.x; c < sk; c += blockDim.x)
+        if (GCHK(sc.dbg, c, 256)) coefw[c] = ((ls + nu) / (lam[c] + nu) - 1.0) * S->w[c];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    double rz = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * nw + wid; j < n; j += (int64_t)gridDim.x * nw) {
+        double acc = 0.0;
+        for (int c = lane; c < sk; c += 32)
+            if (GCHK(sc.dbg, j * sk + c, n * (long long)sk)) acc += (double)U[j * sk + c] * coefw[c];
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const VT rj = r[j];
+            const VT zj = rj + (VT)acc;
+            zc[j] = zj;
+            rz += (double)rj * (double)zj;
+        }
+    }
+    double v[1] = {rz}, out[1];
+    if (grid_sum<1>(v, sc.part, sc.counter, out)) {
+        if (threadIdx.x == 0) {
+            if (S->cg_first) {
+                S->beta = 0.0;
+                S->cg_first = 0;
+            } else {
+                S->beta = S->rz > 0.0 ? out[0] / S->rz : 0.0;
+            }
+            S->rz = out[0];
+        }
+    }
+}
+
+template <typename VT>
+__global__ void rhs_init_kernel(int64_t n, const VT* g, const VT* x, const VT* z, VT* u, double rho,
+                                double u_scale, double nu, double tol, int cg_max, VT* r, VT* delta,
+                                VT* p, VT* zc, const VT* U, int sk, DevState* S, Scratch sc) {
+    __shared__ VT rsh[VT_THREADS];
+    const int64_t j0 = (int64_t)blockIdx.x * VT_THREADS;
+    const int64_t j = j0 + threadIdx.x;
+    double rr = 0.0;
+    VT rj = VT(0);
+    if (j < n) {
+        const VT uj = u[j] * (VT)u_scale;
+        u[j] = uj;
+        rj = -(g[j] + (VT)rho * (x[j] - z[j] + uj));
+        r[j] = rj;
+        delta[j] = VT(0);
+        p[j] = VT(0);
+        if (sk == 0) zc[j] = rj;
+        rr = (double)rj * (double)rj;
+    }
+    rsh[threadIdx.x] = rj;
+    __syncthreads();
+    double rr_tot;
+    if (ut_r_and_norm<VT>(U, sk, rsh, j0, n, rr, sc.part, sc.counter, S->w, rr_tot, sc.dbg)) {
+        if (threadIdx.x == 0) {
+            S->rhs2 = rr_tot;
+            S->rr = rr_tot;
+            S->nu = nu;
+            S->tol = tol;
+            S->cg_it = 0;
+            S->cg_max = cg_max;
+            S->cg_done = rr_tot > 0.0 ? 0 : 1;
+            S->cg_first = 1;
+            S->beta = 0.0;
+            if (sk == 0) {
+                S->rz = rr_tot;
+                S->cg_first = 0;
+            }
+        }
+    }
+}
+
+template <typename VT>
+__global__ void grad_finish_kernel(const VT* P, int G, int64_t ldp, const double* loss_part,
+                                   int64_t n, const VT* x, const VT* u, double mu, double rho,
+                                   double lam1, VT* g, DevState* S, Scratch sc) {
+    __shared__ double sh[8 * 33];
+    const int64_t j = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+    double sum = column_sum<VT, double>(P, G, ldp, j, n, sh);
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    double mx[1] = {0.0};
+    if ((threadIdx.x >> 5) == 0 && j < n) {
+        const double xj = (double)x[j];
+        const double gj = sum + mu * xj;
+        g[j] = (VT)gj;
+        const double rhou = rho * (double)u[j];
+        const double rd = gj + rhou;
+        const double atw = fabs(sum);
+        const double ex = fmax(atw - lam1, 0.0);
+        v[0] = rd * rd;
+        v[1] = rhou * rhou;
+        v[2] = gj * gj;
+        v[3] = ex * ex;
+        v[4] = fabs(xj);
+        v[5] = xj * xj;
+        mx[0] = atw;
+    }
+    double out[6], outm[1];
+    if (grid_sum_max<6, 1>(v, mx, sc.part, sc.counter, out, outm)) {
+        if (threadIdx.x == 0) {
+            double ls = 0.0;
+            for (int b = 0; b < G; ++b) ls += loss_part[b];
+            S->loss_sum = ls;
+            S->rd2 = out[0];
+            S->rhou2 = out[1];
+            S->g2 = out[2];
+            S->excess2 = out[3];
+            S->gx1 = out[4];
+            S->gx2 = out[5];
+            S->atw_inf = outm[0];
+        }
+    }
+}
+
+template <typename VT>
+__global__ void kkt_finish_kernel(const VT* P, int G, int64_t ldp, int64_t n, const VT* z,
+                                  double mu, double lam1, DevState* S, Scratch sc) {
+    __shared__ double sh[8 * 33];
+    const int64_t j = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+    double sum = column_sum<VT, double>(P, G, ldp, j, n, sh);
+    double v[2] = {0, 0};
+    double mx[1] = {0.0};
+    if ((threadIdx.x >> 5) == 0 && j < n) {
+        const double zj = (double)z[j];
+        const double gj = sum + mu * zj;
+        double d;
+        if (zj > 0.0) d = fabs(gj + lam1);
+        else if (zj < 0.0) d = fabs(gj - lam1);
+        else d = fmax(fabs(gj) - lam1, 0.0);
+        v[0] = d * d;
+        v[1] = gj * gj;
+        mx[0] = d;
+    }
+    double out[2], outm[1];
+    if (grid_sum_max<2, 1>(v, mx, sc.part, sc.counter, out, outm)) {
+        if (threadIdx.x == 0) {
+            S->kd2 = out[0];
+            S->kg2 = out[1];
+            S->kdmax = outm[0];
+        }
+    }
+}
+
+template <typename VT>
+__global__ void gap_kernel(int loss, int64_t m, const VT* W, const VT* b, double mu, double lam1,
+                           DevState* S, Scratch sc) {
+    const double scale = (mu == 0.0 && S->atw_inf > lam1) ? lam1 / S->atw_inf : 1.0;
+    double v[2] = {0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double nu = scale * (double)W[i];
+        v[0] += loss_conj(loss, nu);
+        v[1] += (double)b[i] * nu;
+    }
+    double out[2];
+    if (grid_sum<2>(v, sc.part, sc.counter, out)) {
+        if (threadIdx.x == 0) {
+            S->conj_sum = out[0];
+            S->btnu = out[1];
+            S->gap_scale = scale;
+        }
+    }
+}
+
+template <typename VT>
+__global__ void zu_kernel(int64_t n, VT* x, const VT* delta, VT* z, VT* u, double rho, double lam1,
+                          double alpha, DevState* S, double* norms_out, Scratch sc) {
+    const double kappa = lam1 / rho;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        VT xj = x[j];
+        if (delta != nullptr) {
+            xj += delta[j];
+            x[j] = xj;
+        }
+        const VT zj = z[j];
+        const VT xh = (VT)alpha * xj + (VT)(1.0 - alpha) * zj;
+        const VT vv = xh + u[j];
+        VT zn;
+        if (vv > (VT)kappa) zn = vv - (VT)kappa;
+        else if (vv < -(VT)kappa) zn = vv + (VT)kappa;
+        else zn = VT(0);
+        const VT un = u[j] + xh - zn;
+        z[j] = zn;
+        u[j] = un;
+        const double dxz = (double)xj - (double)zn;
+        v[0] += dxz * dxz;
+        v[1] += (double)xj * (double)xj;
+        v[2] += (double)zn * (double)zn;
+        v[3] += (double)un * (double)un;
+        v[4] += fabs((double)zn);
+        v[5] += zn != VT(0) ? 1.0 : 0.0;
+    }
+    double out[6];
+    if (grid_sum<6>(v, sc.part, sc.counter, out)) {
+        if (threadIdx.x == 0) {
+            if (S) {
+                S->rp2 = out[0];
+                S->x2 = out[1];
+                S->z2 = out[2];
+                S->u2 = out[3];
+                S->z1 = out[4];
+                S->nnz = out[5];
+            }
+            if (norms_out)
+                for (int k = 0; k < 6; ++k) norms_out[k] = out[k];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+template <typename S, typename D>
+__global__ void convert_kernel(int64_t rows, int64_t cols, const S* src, int64_t lds, D* dst,
+                               int64_t ldd) {
+    const int64_t total = rows * ldd;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / ldd, j = e % ldd;
+        dst[e] = j < cols ? (D)src[i * lds + j] : D(0);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// host launchers
+// ------------------------------------------------------------------------------------------
+static int grid_for(int64_t n, int per, int cap = 4096) {
+    int g = nblocks(n, per);
+    return g < 1 ? 1 : (g > cap ? cap : g);
+}
+
+#define DISPATCH_VT(dbl, KERNEL, GRID, BLOCK, ST, ...)                                     \
+    do {                                                                                  \
+        if (dbl) KERNEL<double><<<GRID, BLOCK, 0, ST>>>(__VA_ARGS__);                     \
+        else KERNEL<float><<<GRID, BLOCK, 0, ST>>>(__VA_ARGS__);                          \
+    } while (0)
+
+template <typename VT> static VT* C(void* p) { return static_cast<VT*>(p); }
+template <typename VT> static const VT* CC(const void* p) { return static_cast<const VT*>(p); }
+
+cudaError_t hv_finish(bool dbl, const void* P, int G, int64_t ldp, int64_t n, double nu,
+                      const void* v, void* y, cudaStream_t s) {
+    const int grid = nblocks(n, 32);
+    if (dbl) hv_finish_kernel<double><<<grid, VT_THREADS, 0, s>>>(CC<double>(P), G, ldp, n, nu, CC<double>(v), C<double>(y));
+    else hv_finish_kernel<float><<<grid, VT_THREADS, 0, s>>>(CC<float>(P), G, ldp, n, nu, CC<float>(v), C<float>(y));
+    return cudaGetLastError();
+}
+
+cudaError_t cg_q(bool dbl, const void* P, int G, int64_t ldp, int64_t n, void* p, const void* zc,
+                 void* q, DevState* S, Scratch sc, cudaStream_t s) {
+    const int grid = nblocks(n, 32);
+    if (dbl) cg_q_kernel<double><<<grid, VT_THREADS, 0, s>>>(CC<double>(P), G, ldp, n, C<double>(p), CC<double>(zc), C<double>(q), S, sc);
+    else cg_q_kernel<float><<<grid, VT_THREADS, 0, s>>>(CC<float>(P), G, ldp, n, C<float>(p), CC<float>(zc), C<float>(q), S, sc);
+    return cudaGetLastError();
+}
+
+// per-block partials of U^T r must fit the scratch partial buffer
+static bool utr_fits(int64_t n, int sk) { return (int64_t)nblocks(n, VT_THREADS) * (sk + 1) <= 262144; }
+
+cudaError_t cg_update(bool dbl, int64_t n, void* delta, void* r, const void* p, const void* q,
+                      const void* U, int sk, void* zc, DevState* S, Scratch sc, cudaStream_t s) {
+    if (!utr_fits(n, sk)) return cudaErrorInvalidValue;
+    const int grid = nblocks(n, VT_THREADS);
+    if (dbl) cg_update_kernel<double><<<grid, VT_THREADS, 0, s>>>(n, C<double>(delta), C<double>(r), CC<double>(p), CC<double>(q), CC<double>(U), sk, C<double>(zc), S, sc);
+    else cg_update_kernel<float><<<grid, VT_THREADS, 0, s>>>(n, C<float>(delta), C<float>(r), CC<float>(p), CC<float>(q), CC<float>(U), sk, C<float>(zc), S, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t cg_precond(bool dbl, int64_t n, const void* U, int sk, const double* lam, const void* r,
+                       void* zc, DevState* S, Scratch sc, cudaStream_t s) {
+    const int grid = grid_for(n, 8, 2048);
+    if (dbl) cg_precond_kernel<double><<<grid, VT_THREADS, 0, s>>>(n, CC<double>(U), sk, lam, CC<double>(r), C<double>(zc), S, sc);
+    else cg_precond_kernel<float><<<grid, VT_THREADS, 0, s>>>(n, CC<float>(U), sk, lam, CC<float>(r), C<float>(zc), S, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t rhs_init(bool dbl, int64_t n, const void* g, const void* x, const void* z, void* u,
+                     double rho, double u_scale, double nu, double tol, int cg_max, void* r,
+                     void* delta, void* p, void* zc, const void* U, int sk, DevState* S,
+                     Scratch sc, cudaStream_t s) {
+    if (!utr_fits(n, sk)) return cudaErrorInvalidValue;
+    const int grid = nblocks(n, VT_THREADS);
+    if (dbl) rhs_init_kernel<double><<<grid, VT_THREADS, 0, s>>>(n, CC<double>(g), CC<double>(x), CC<double>(z), C<double>(u), rho, u_scale, nu, tol, cg_max, C<double>(r), C<double>(delta), C<double>(p), C<double>(zc), CC<double>(U), sk, S, sc);
+    else rhs_init_kernel<float><<<grid, VT_THREADS, 0, s>>>(n, CC<float>(g), CC<float>(x), CC<float>(z), C<float>(u), rho, u_scale, nu, tol, cg_max, C<float>(r), C<float>(delta), C<float>(p), C<float>(zc), CC<float>(U), sk, S, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t grad_finish(bool dbl, const void* P, int G, int64_t ldp, const double* loss_part,
+                        int64_t n, const void* x, const void* u, double mu, double rho,
+                        double lam1, void* g, DevState* S, Scratch sc, cudaStream_t s) {
+    const int grid = nblocks(n, 32);
+    if (dbl) grad_finish_kernel<double><<<grid, VT_THREADS, 0, s>>>(CC<double>(P), G, ldp, loss_part, n, CC<double>(x), CC<double>(u), mu, rho, lam1, C<double>(g), S, sc);
+    else grad_finish_kernel<float><<<grid, VT_THREADS, 0, s>>>(CC<float>(P), G, ldp, loss_part, n, CC<float>(x), CC<float>(u), mu, rho, lam1, C<float>(g), S, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t kkt_finish(bool dbl, const void* P, int G, int64_t ldp, int64_t n, const void* z,
+                       double mu, double lam1, DevState* S, Scratch sc, cudaStream_t s) {
+    const int grid = nblocks(n, 32);
+    if (dbl) kkt_finish_kernel<double><<<grid, VT_THREADS, 0, s>>>(CC<double>(P), G, ldp, n, CC<double>(z), mu, lam1, S, sc);
+    else kkt_finish_kernel<float><<<grid, VT_THREADS, 0, s>>>(CC<float>(P), G, ldp, n, CC<float>(z), mu, lam1, S, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t gap_pieces(bool dbl, int loss, int64_t m, const void* W, const void* b, double mu,
+                       double lam1, DevState* S, Scratch sc, cudaStream_t s) {
+    const int grid = grid_for(m, VT_THREADS, 512);
+    if (dbl) gap_kernel<double><<<grid, VT_THREADS, 0, s>>>(loss, m, CC<double>(W), CC<double>(b), mu, lam1, S, sc);
+    else gap_kernel<float><<<grid, VT_THREADS, 0, s>>>(loss, m, CC<float>(W), CC<float>(b), mu, lam1, S, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t zu_update(bool dbl, int64_t n, void* x, const void* delta, void* z, void* u,
+                      double rho, double lam1, double alpha, DevState* S, double* norms_out,
+                      Scratch sc, cudaStream_t s) {
+    const int grid = grid_for(n, VT_THREADS, 512);
+    if (dbl) zu_kernel<double><<<grid, VT_THREADS, 0, s>>>(n, C<double>(x), CC<double>(delta), C<double>(z), C<double>(u), rho, lam1, alpha, S, norms_out, sc);
+    else zu_kernel<float><<<grid, VT_THREADS, 0, s>>>(n, C<float>(x), CC<float>(delta), C<float>(z), C<float>(u), rho, lam1, alpha, S, norms_out, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t convert_copy(int src_dt, int dst_dt, int64_t rows, int64_t cols, const void* src,
+                         int64_t lds, void* dst, int64_t ldd, cudaStream_t s) {
+    const int grid = grid_for(rows * ldd, VT_THREADS, 152 * 16);
+    // dtype codes: 0 f64, 1 f32
+    if (src_dt == 0 && dst_dt == 0) convert_kernel<double, double><<<grid, VT_THREADS, 0, s>>>(rows, cols, CC<double>(src), lds, C<double>(dst), ldd);
+    else if (src_dt == 0 && dst_dt == 1) convert_kernel<double, float><<<grid, VT_THREADS, 0, s>>>(rows, cols, CC<double>(src), lds, C<float>(dst), ldd);
+    else if (src_dt == 1 && dst_dt == 0) convert_kernel<float, double><<<grid, VT_THREADS, 0, s>>>(rows, cols, CC<float>(src), lds, C<double>(dst), ldd);
+    else if (src_dt == 1 && dst_dt == 1) convert_kernel<float, float><<<grid, VT_THREADS, 0, s>>>(rows, cols, CC<float>(src), lds, C<float>(dst), ldd);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t fill_zero(void* p, size_t bytes, cudaStream_t s) { return cudaMemsetAsync(p, 0, bytes, s); }
+
+}  // namespace genios

@@ -1,0 +1,241 @@
+"""Python front-end over the C ABI: a ``Solver`` context and kernel-level ``ops``.
+
+Arrays may be torch tensors (CUDA or CPU) or NumPy arrays; device memory and streams come from
+torch.  Nothing here computes: each call forwards pointers and sizes to libgenios.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from types import SimpleNamespace
+
+import numpy as np
+
+from . import _lib as L
+
+try:  # torch is the device-memory / stream provider; CPU-only use works without a GPU
+    import torch
+except ImportError:  # pragma: no cover
+    torch = None
+
+
+def _stream_ptr():
+    if torch is not None and torch.cuda.is_available():
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(0)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if torch is not None and isinstance(a, torch.Tensor):
+        return C.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        return C.c_void_p(a.ctypes.data)
+    raise TypeError(type(a))
+
+
+def _dt(a) -> int:
+    if torch is not None and isinstance(a, torch.Tensor):
+        return {torch.float64: L.DT_F64, torch.float32: L.DT_F32}[a.dtype]
+    return {np.dtype(np.float64): L.DT_F64, np.dtype(np.float32): L.DT_F32}[a.dtype]
+
+
+class Solver:
+    """One GeNIOS context (one problem, one device, one stream)."""
+
+    def __init__(self, options: L.Options | None = None, device: int = 0, **kw):
+        self._lib = L.lib()
+        self.options = options if options is not None else L.default_options(**kw)
+        self._ctx = C.c_void_p()
+        st = self._lib.genios_create(C.byref(self.options), device, _stream_ptr(), C.byref(self._ctx))
+        L.check(st, None)
+        self.n = 0
+        self.m = 0
+        self._keep = []
+
+    # ------------------------------------------------------------------
+    def set_data(self, A, b, loss: int | str = L.LOSS_SQUARED):
+        if isinstance(loss, str):
+            loss = {"squared": L.LOSS_SQUARED, "logistic": L.LOSS_LOGISTIC}[loss]
+        if isinstance(A, np.ndarray):
+            A = np.ascontiguousarray(A)
+            b = np.ascontiguousarray(b, dtype=A.dtype)
+        m, n = A.shape
+        lda = A.stride(0) if torch is not None and isinstance(A, torch.Tensor) else A.strides[0] // A.itemsize
+        mm, nn, ll = (C.c_int64 * 1)(m), (C.c_int64 * 1)(n), (C.c_int64 * 1)(lda)
+        Ap = (C.c_void_p * 1)(_ptr(A).value)
+        bp = (C.c_void_p * 1)(_ptr(b).value)
+        st = self._lib.genios_set_data(self._ctx, loss, 1, mm, nn, Ap, _dt(A), ll, bp, 0)
+        L.check(st, self._ctx)
+        self.m, self.n = m, n
+        return self
+
+    def lambda_max(self) -> float:
+        out = C.c_double()
+        L.check(self._lib.genios_lambda_max(self._ctx, C.byref(out)), self._ctx)
+        return out.value
+
+    def solve(self, lam1: float, lam2: float = 0.0, out=None, warm_start: bool = False,
+              out_dtype=np.float64):
+        """Returns (z, info dict).  ``out`` (host ndarray or torch tensor) receives z if given."""
+        if out is None:
+            out = np.empty(self.n, dtype=out_dtype)
+        info = L.Info()
+        l1, l2 = (C.c_double * 1)(lam1), (C.c_double * 1)(lam2)
+        st = self._lib.genios_solve(self._ctx, l1, l2, _ptr(out), _dt(out), C.byref(info),
+                                    int(warm_start))
+        L.check(st, self._ctx)
+        d = info.as_dict()
+        d["status_name"] = L.STATUS_NAMES[d["status"]]
+        return out, d
+
+    def last_error(self) -> str:
+        return self._lib.genios_last_error(self._ctx).decode()
+
+    def close(self):
+        if self._ctx:
+            self._lib.genios_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------------------
+# kernel-level ops on torch CUDA tensors
+# ----------------------------------------------------------------------------------------
+def _vt(prec):
+    return torch.float64 if prec == L.FP64 else torch.float32
+
+
+def _chk(st):
+    if st != L.OK:
+        raise L.GeniosError(st, L.lib().genios_last_error(None).decode())
+
+
+def lda(prec: int, n: int) -> int:
+    return int(L.lib().genios_op_lda(prec, n))
+
+
+def pad(A, prec: int):
+    """Copy a 2-D tensor into a zero-padded device matrix with the kernels' leading dimension
+    (storage dtype float64 / float32; BF16 / FP8 copies come from ``quantize``)."""
+    m, n = A.shape
+    ld = lda(prec, n)
+    dt = torch.float64 if prec == L.FP64 else torch.float32
+    out = torch.zeros((m, ld), dtype=dt, device="cuda")
+    out[:, :n] = A.to(device="cuda", dtype=dt)
+    return out
+
+
+def _ws(prec, m, n):
+    nb = int(L.lib().genios_op_workspace_bytes(prec, m, n))
+    return torch.empty(nb, dtype=torch.uint8, device="cuda"), nb
+
+
+def hv(prec, A, n, d, nu, v, row_scale=None):
+    m = A.shape[0]
+    y = torch.empty(n, dtype=_vt(prec), device="cuda")
+    ws, nb = _ws(prec, m, n)
+    _chk(L.lib().genios_op_hv(prec, m, n, _ptr(A), A.shape[1], _ptr(row_scale), _ptr(d), nu, _ptr(v),
+                              _ptr(y), _ptr(ws), nb, _stream_ptr()))
+    return y
+
+
+def gradient(loss, prec, A, A_lo, n, b, x, lam2):
+    m = A.shape[0]
+    g = torch.empty(n, dtype=_vt(prec), device="cuda")
+    w = torch.empty(m, dtype=_vt(prec), device="cuda")
+    D = torch.empty(m, dtype=_vt(prec), device="cuda")
+    ls = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ws, nb = _ws(prec, m, n)
+    _chk(L.lib().genios_op_gradient(loss, prec, m, n, _ptr(A), _ptr(A_lo), A.shape[1], _ptr(b), _ptr(x),
+                                    lam2, _ptr(g), _ptr(w), _ptr(D), _ptr(ls), _ptr(ws), nb,
+                                    _stream_ptr()))
+    return g, w, D, ls
+
+
+def zu_update(prec, x, z, u, rho, lam1, alpha):
+    n = x.numel()
+    norms = torch.zeros(6, dtype=torch.float64, device="cuda")
+    ws, nb = _ws(prec, 1, n)
+    _chk(L.lib().genios_op_zu_update(prec, n, _ptr(x), _ptr(z), _ptr(u), rho, lam1, alpha, _ptr(norms),
+                                     _ptr(ws), nb, _stream_ptr()))
+    return norms
+
+
+def nystrom(prec, A, n, s, d, Omega, row_scale=None):
+    m = A.shape[0]
+    U = torch.empty((n, s), dtype=_vt(prec), device="cuda")
+    lam = torch.empty(s, dtype=torch.float64, device="cuda")
+    eta = torch.empty(1, dtype=torch.float64, device="cuda")
+    nb = int(L.lib().genios_op_nystrom_workspace_bytes(prec, m, n, s))
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    _chk(L.lib().genios_op_nystrom(prec, m, n, s, _ptr(A), A.shape[1], _ptr(row_scale), _ptr(d),
+                                   _ptr(Omega), _ptr(U), _ptr(lam), _ptr(eta), _ptr(ws), nb,
+                                   _stream_ptr()))
+    return U, lam, eta
+
+
+def precond(prec, U, lam, nu, v):
+    n, s = U.shape
+    y = torch.empty(n, dtype=_vt(prec), device="cuda")
+    ws, nb = _ws(prec, 1, n)
+    _chk(L.lib().genios_op_precond(prec, n, s, _ptr(U), _ptr(lam), nu, _ptr(v), _ptr(y), _ptr(ws), nb,
+                                   _stream_ptr()))
+    return y
+
+
+def omega(prec, n, s, seed, stream_id=0):
+    Om = torch.empty((n, s), dtype=_vt(prec), device="cuda")
+    _chk(L.lib().genios_op_omega(prec, n, s, seed, stream_id, _ptr(Om), _stream_ptr()))
+    return Om
+
+
+def philox(ctr, key, nblocks):
+    out = torch.empty(4 * nblocks, dtype=torch.int32, device="cuda")
+    _chk(L.lib().genios_op_philox(*[int(c) & 0xFFFFFFFF for c in ctr], *[int(k) & 0xFFFFFFFF for k in key],
+                                  nblocks, _ptr(out), _stream_ptr()))
+    return out.cpu().numpy().view(np.uint32).reshape(nblocks, 4)
+
+
+def quantize(prec, A32):
+    m, n = A32.shape
+    A32 = A32.contiguous()
+    ld = lda(prec, n)
+    if prec == L.BF16:
+        hi = torch.empty((m, ld), dtype=torch.bfloat16, device="cuda")
+        lo = torch.empty((m, ld), dtype=torch.bfloat16, device="cuda")
+        _chk(L.lib().genios_op_quantize(prec, m, n, _ptr(A32), A32.stride(0), _ptr(hi), _ptr(lo), None,
+                                        _stream_ptr()))
+        return hi, lo
+    codes = torch.empty((m, ld), dtype=torch.uint8, device="cuda")
+    sc = torch.empty(m, dtype=torch.float32, device="cuda")
+    _chk(L.lib().genios_op_quantize(prec, m, n, _ptr(A32), A32.stride(0), _ptr(codes), None, _ptr(sc),
+                                    _stream_ptr()))
+    return codes, sc
+
+
+def pcg(prec, A, n, d, nu, r, U=None, lam=None, rtol=1e-6, max_iter=100, row_scale=None):
+    m = A.shape[0]
+    s = 0 if U is None else U.shape[1]
+    delta = torch.empty(n, dtype=_vt(prec), device="cuda")
+    it = C.c_int()
+    rel = C.c_double()
+    _chk(L.lib().genios_op_pcg(prec, m, n, _ptr(A), A.shape[1], _ptr(row_scale), _ptr(d), nu, _ptr(r), s,
+                               _ptr(U), _ptr(lam), rtol, max_iter, _ptr(delta), C.byref(it), C.byref(rel),
+                               _stream_ptr()))
+    return delta, it.value, rel.value
+
+
+ops = SimpleNamespace(lda=lda, pad=pad, hv=hv, gradient=gradient, zu_update=zu_update, nystrom=nystrom,
+                      precond=precond, omega=omega, philox=philox, quantize=quantize, pcg=pcg)

@@ -1,0 +1,290 @@
+"""Kernel-level parity of the CUDA path (through the C ABI) against the CPU float64 oracle.
+
+Tolerances.  FP64 kernels: 1e-11 relative to the output scale.  FP32 / BF16 / FP8 kernels
+accumulate in float32 after multiplying float32 (or exactly dequantised) values; a dot product
+of length n carries an error of order sqrt(n) eps32 |a||v|, so for the sizes here (n <= 5000)
+we allow 2e-5 relative to max|y|.  Low-precision A is compared with the oracle applied to the
+SAME dequantised matrix (hi + lo, or scale x e4m3), so the tolerance measures the kernel, not
+the quantisation.  Integer work (Philox words, BF16 / E4M3 codes) must be bit-exact.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import problems  # noqa: E402
+from oracle import admm as oadmm, linalg as olin, philox as ophilox, quant as oquant  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-11, 1: 2e-5, 2: 2e-5, 3: 2e-5}
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2310_08333_gb300 import build as b
+    b.build()
+    import paper_2310_08333_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def rel_close(got, ref, tol):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = max(np.max(np.abs(ref)), 1e-300)
+    err = np.max(np.abs(got - ref)) / scale
+    assert err <= tol, f"max rel err {err:.3e} > {tol:.1e}"
+
+
+def dev(a, dt=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dt)
+
+
+# ---------------------------------------------------------------------------- Philox / Omega
+def test_philox_known_answers_bit_exact(G):
+    vecs = [((0, 0, 0, 0), (0, 0)), ((0xffffffff,) * 4, (0xffffffff,) * 2),
+            ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0))]
+    for ctr, key in vecs:
+        got = G.ops.philox(ctr, key, 1)[0]
+        ref = ophilox.philox4x32_10(np.array(ctr, np.uint32), np.array(key, np.uint32))
+        assert [int(v) for v in got] == [int(v) for v in ref]
+    got = G.ops.philox((5, 7, 0, 0), (11, 13), 1000)
+    ctr = np.zeros((1000, 4), np.uint32)
+    ctr[:, 0] = 5 + np.arange(1000)
+    ctr[:, 1] = 7
+    ref = ophilox.philox4x32_10(ctr, np.array([11, 13], np.uint32))
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_omega_matches_oracle(G, prec):
+    n, s, seed = 1003, 37, (1 << 40) + 12345
+    got = G.ops.omega(prec, n, s, seed, stream_id=3).cpu().numpy()
+    ref = ophilox.omega(n, s, seed, stream=3)
+    rel_close(got, ref, 1e-12 if prec == 0 else 1e-6)
+
+
+# ---------------------------------------------------------------------------- quantisation
+def test_quantize_bf16_hilo_bit_exact(G):
+    rng = np.random.default_rng(0)
+    A = (rng.standard_normal((77, 531)) * 10 ** rng.uniform(-3, 3, (77, 531))).astype(np.float32)
+    hi, lo = G.ops.quantize(2, dev(A))
+    hr, lr = oquant.split_hi_lo(A)
+    n = A.shape[1]
+    got_hi = hi.float().cpu().numpy()
+    got_lo = lo.float().cpu().numpy()
+    np.testing.assert_array_equal(got_hi[:, :n], hr)
+    np.testing.assert_array_equal(got_lo[:, :n], lr)
+    assert np.all(got_hi[:, n:] == 0) and np.all(got_lo[:, n:] == 0)
+
+
+def test_quantize_fp8_rows_bit_exact(G):
+    rng = np.random.default_rng(1)
+    A = (rng.standard_normal((64, 301)) * 10 ** rng.uniform(-2, 2, (64, 1))).astype(np.float32)
+    A[5] = 0.0
+    codes, sc = G.ops.quantize(3, dev(A))
+    cr, sr = oquant.quantize_fp8_rows(A)
+    np.testing.assert_array_equal(sc.cpu().numpy(), sr)
+    np.testing.assert_array_equal(codes.cpu().numpy()[:, :301], cr)
+    assert np.all(codes.cpu().numpy()[:, 301:] == 0)
+
+
+# ---------------------------------------------------------------------------- Hv
+def _matrices(prec, A):
+    """device storage for `prec` and the float64 matrix the kernel actually multiplies"""
+    if prec in (0, 1):
+        Ad = G_ops().pad(torch.from_numpy(A), prec)
+        Aeff = Ad[:, :A.shape[1]].double().cpu().numpy()
+        return Ad, Aeff, None
+    A32 = dev(A)
+    if prec == 2:
+        hi, lo = G_ops().quantize(2, A32)
+        return hi, hi.float().cpu().numpy()[:, :A.shape[1]].astype(np.float64), None
+    codes, sc = G_ops().quantize(3, A32)
+    deq = oquant.e4m3_decode(codes.cpu().numpy()[:, :A.shape[1]]) * sc.cpu().numpy()[:, None]
+    return codes, deq, sc
+
+
+def G_ops():
+    import paper_2310_08333_gb300 as pkg
+    return pkg.ops
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", [(1, 1), (37, 5), (1237, 3001), (500, 8000), (3, 20000)])
+def test_hv_matches_oracle(G, prec, shape):
+    m, n = shape
+    if prec == 0 and n > 8192:
+        pytest.skip("FP64 fused rowpass covers n <= 8192")
+    rng = np.random.default_rng(m * 7 + n)
+    A = rng.standard_normal((m, n))
+    d = rng.uniform(0.05, 0.3, m)
+    v = rng.standard_normal(n)
+    nu = 0.7
+    Ad, Aeff, sc = _matrices(prec, A)
+    vt = torch.float64 if prec == 0 else torch.float32
+    y = G.ops.hv(prec, Ad, n, dev(d, vt), nu, dev(v, vt), row_scale=sc).cpu().numpy()
+    dref = d if prec == 0 else d.astype(np.float32).astype(np.float64)
+    vref = v if prec == 0 else v.astype(np.float32).astype(np.float64)
+    ref = olin.hessian_vector(Aeff, dref, vref, nu)
+    rel_close(y, ref, TOL[prec])
+
+
+def test_hv_without_weights_is_gram(G):
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((300, 700))
+    v = rng.standard_normal(700)
+    Ad = G.ops.pad(torch.from_numpy(A), 0)
+    y = G.ops.hv(0, Ad, 700, None, 0.0, dev(v, torch.float64)).cpu().numpy()
+    rel_close(y, A.T @ (A @ v), 1e-11)
+
+
+# ---------------------------------------------------------------------------- gradient pass
+@pytest.mark.parametrize("loss", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(1, 3), (999, 1001), (2048, 4000)])
+def test_gradient_matches_oracle(G, loss, prec, shape):
+    m, n = shape
+    rng = np.random.default_rng(m + 3 * n + loss)
+    A = rng.standard_normal((m, n)) / np.sqrt(n)
+    b = rng.standard_normal(m) if loss == 0 else np.zeros(m)
+    x = rng.standard_normal(n)
+    mu = 0.25
+    vt = torch.float64 if prec == 0 else torch.float32
+    if prec in (0, 1):
+        Ad = G.ops.pad(torch.from_numpy(A), prec)
+        lo = None
+        Aeff = Ad[:, :n].double().cpu().numpy()
+    else:
+        Ad, lo = G.ops.quantize(2, dev(A))
+        Aeff = Ad.float().cpu().numpy()[:, :n].astype(np.float64) + lo.float().cpu().numpy()[:, :n]
+    g, w, D, ls = G.ops.gradient(loss, prec, Ad, lo, n, dev(b, vt), dev(x, vt), mu)
+    xr = x if prec == 0 else x.astype(np.float32).astype(np.float64)
+    br = b if prec == 0 else b.astype(np.float32).astype(np.float64)
+    ref = olin.gradient_pass(Aeff, br, xr, ["squared", "logistic"][loss], mu)
+    tol = TOL[prec] if prec == 0 else 5e-5
+    rel_close(g.cpu().numpy(), ref["grad"], tol)
+    rel_close(w.cpu().numpy(), ref["d1"], tol)
+    rel_close(D.cpu().numpy(), ref["D"], tol)
+    assert abs(ls.item() - ref["loss_sum"]) <= tol * max(1.0, abs(ref["loss_sum"])) * 10
+
+
+# ---------------------------------------------------------------------------- z/u update
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [1, 255, 257, 100003])
+def test_zu_update_matches_oracle(G, prec, n):
+    rng = np.random.default_rng(n)
+    x, z, u = rng.standard_normal((3, n))
+    z[: n // 3] = 0.0
+    vt = torch.float64 if prec == 0 else torch.float32
+    xd, zd, ud = dev(x, vt), dev(z, vt), dev(u, vt)
+    rho, lam, alpha = 1.7, 0.9, 1.6
+    norms = G.ops.zu_update(prec, xd, zd, ud, rho, lam, alpha).cpu().numpy()
+    if prec == 1:
+        x, z, u = (a.astype(np.float32).astype(np.float64) for a in (x, z, u))
+    zr, ur, nr = oadmm.zu_update(x, z, u, rho, lam, alpha)
+    tol = 1e-14 if prec == 0 else 1e-6
+    rel_close(zd.cpu().numpy(), zr, tol)
+    rel_close(ud.cpu().numpy(), ur, tol)
+    for k, key in enumerate(["rp2", "x2", "z2", "u2", "z1"]):
+        assert abs(norms[k] - nr[key]) <= tol * 10 * max(1.0, nr[key])
+    # nnz can differ only where |x_hat + u| is within rounding of the threshold
+    assert abs(norms[5] - nr["nnz"]) <= (0 if prec == 0 else 2)
+
+
+def test_zu_update_threshold_ties_map_to_zero(G):
+    # alpha = 1 (no relaxation) so x_hat = x; kappa = lambda / rho = 1.5
+    x = np.array([1.5, -1.5, 0.5, 2.0])
+    z = np.zeros(4)
+    u = np.zeros(4)
+    xd, zd, ud = dev(x, torch.float64), dev(z, torch.float64), dev(u, torch.float64)
+    G.ops.zu_update(0, xd, zd, ud, 1.0, 1.5, 1.0)
+    np.testing.assert_array_equal(zd.cpu().numpy(), [0.0, 0.0, 0.0, 0.5])
+    np.testing.assert_array_equal(ud.cpu().numpy(), [1.5, -1.5, 0.5, 1.5])
+
+
+# ---------------------------------------------------------------------------- Nystrom
+@pytest.mark.parametrize("prec", [0, 1])
+def test_nystrom_matches_oracle(G, prec):
+    rng = np.random.default_rng(4)
+    m, n, s = 900, 700, 40
+    # decaying spectrum: low rank (20) + noise
+    A = rng.standard_normal((m, 20)) @ rng.standard_normal((20, n)) / 5 + 0.05 * rng.standard_normal((m, n))
+    d = rng.uniform(0.1, 0.25, m)
+    vt = torch.float64 if prec == 0 else torch.float32
+    Ad = G.ops.pad(torch.from_numpy(A), prec)
+    Aeff = Ad[:, :n].double().cpu().numpy()
+    Om = G.ops.omega(prec, n, s, seed=99)
+    U, lam, eta = G.ops.nystrom(prec, Ad, n, s, dev(d, vt), Om)
+    # the library sketches with an orthonormal basis of range(Omega); so does the oracle
+    Omr = olin.orthonormal_test_matrix(Om.double().cpu().numpy())
+    dr = d if prec == 0 else d.astype(np.float32).astype(np.float64)
+    Y = olin.sketch(Aeff, dr, Omr)
+    eps = np.finfo(np.float64 if prec == 0 else np.float32).eps
+    Ur, lr, er = olin.nystrom_from_sketch(Y, Omr, eps=eps)
+    U = U.double().cpu().numpy()
+    lam = lam.cpu().numpy()
+    tol = 1e-9 if prec == 0 else 2e-3
+    top = lr > 1e-3 * lr[0]
+    np.testing.assert_allclose(lam[top], lr[top], rtol=tol)
+    Ahat = (U[:, top] * lam[top]) @ U[:, top].T
+    Aref = (Ur[:, top] * lr[top]) @ Ur[:, top].T
+    rel_close(Ahat, Aref, tol)
+    np.testing.assert_allclose(U[:, top].T @ U[:, top], np.eye(int(top.sum())), atol=10 * tol)
+    assert abs(eta.item() - er) <= 1e-6 * er
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_precond_matches_oracle(G, prec):
+    rng = np.random.default_rng(5)
+    n, s = 3001, 57
+    U, _ = np.linalg.qr(rng.standard_normal((n, s)))
+    lam = np.sort(rng.uniform(0.0, 50.0, s))[::-1]
+    v = rng.standard_normal(n)
+    nu = 1.3
+    vt = torch.float64 if prec == 0 else torch.float32
+    y = G.ops.precond(prec, dev(U, vt), dev(lam, torch.float64), nu, dev(v, vt)).cpu().numpy()
+    if prec == 1:
+        U = U.astype(np.float32).astype(np.float64)
+        v = v.astype(np.float32).astype(np.float64)
+    rel_close(y, olin.nystrom_precond_apply(U, lam, nu, v), 1e-12 if prec == 0 else 2e-5)
+
+
+# ---------------------------------------------------------------------------- PCG
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("use_pc", [False, True])
+def test_pcg_matches_oracle_and_direct_solve(G, prec, use_pc):
+    P = problems.logistic_lowrank(1500, 600, rank=20, nnz=10, seed=6)
+    A = P.A
+    rng = np.random.default_rng(7)
+    d = rng.uniform(0.05, 0.25, A.shape[0])
+    r = rng.standard_normal(600)
+    nu = 1.0
+    vt = torch.float64 if prec == 0 else torch.float32
+    Ad = G.ops.pad(torch.from_numpy(A), prec)
+    Aeff = Ad[:, :600].double().cpu().numpy()
+    U = lam = None
+    Pinv = None
+    if use_pc:
+        Om = G.ops.omega(prec, 600, 30, seed=8)
+        U, lam, _ = G.ops.nystrom(prec, Ad, 600, 30, dev(d, vt), Om)
+        Uh, lh = U.double().cpu().numpy(), lam.cpu().numpy()
+        Pinv = lambda x: olin.nystrom_precond_apply(Uh, lh, nu, x)  # noqa: E731
+    rtol = 1e-10 if prec == 0 else 1e-5
+    delta, it, rel = G.ops.pcg(prec, Ad, 600, dev(d, vt), nu, dev(r, vt), U, lam, rtol=rtol, max_iter=500)
+    dr = d if prec == 0 else d.astype(np.float32).astype(np.float64)
+    rr = r if prec == 0 else r.astype(np.float32).astype(np.float64)
+    Hop = lambda x: olin.hessian_vector(Aeff, dr, x, nu)  # noqa: E731
+    xo, ito, relo = olin.pcg(Hop, rr, Pinv, rtol=rtol, max_iter=500)
+    K = Aeff.T @ (dr[:, None] * Aeff) + nu * np.eye(600)
+    xs = np.linalg.solve(K, rr)
+    tol = 1e-8 if prec == 0 else 2e-4
+    rel_close(delta.cpu().numpy(), xs, tol)
+    assert rel <= rtol * (1.0 if prec == 0 else 2.0)
+    if prec == 0:
+        # same algorithm and inputs: the counts agree up to rounding-order effects
+        assert abs(it - ito) <= max(2, 0.05 * ito)
+    if use_pc:
+        _, it_nopc, _ = G.ops.pcg(prec, Ad, 600, dev(d, vt), nu, dev(r, vt), None, None, rtol=rtol, max_iter=500)
+        assert it < it_nopc            # the preconditioner must help on a low-rank + noise matrix
