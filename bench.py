@@ -241,14 +241,12 @@ def run_ours(args):
         Ah = torch.from_numpy(A32).pin_memory()
         bh = torch.from_numpy(b32).pin_memory()
         xh = torch.empty(P.n, dtype=torch.float64).pin_memory()
-        s2 = solver(prec)
-        s2.set_data(Ah, bh, P.loss)
-        s2.solve(lam, out=xh)
+        s2 = solver(prec)   # the kernels are already warm from the device-resident leg
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(args.e2e_steps):
             s2.set_data(Ah, bh, P.loss)
             s2.solve(lam, out=xh)
         torch.cuda.synchronize()
@@ -258,7 +256,7 @@ def run_ours(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             el = t.item()
         s2.close()
-        e2e = {"value": el / args.steps / ws, "unit": "s",
+        e2e = {"value": el / args.e2e_steps / ws, "unit": "s", "steps": args.e2e_steps,
                "h2d_bytes_per_step": int(A32.nbytes + b32.nbytes),
                "d2h_bytes_per_step": int(xh.numel() * 8)}
 
@@ -269,13 +267,17 @@ def run_ours(args):
         for name in args.variant_list.split(","):
             p = G._lib.PRECISIONS[name]
             sv = solver(p)
-            sv.set_data(Ad, bd, P.loss)
-            sv.solve(lam)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            zv, iv = sv.solve(lam)
-            el = time.perf_counter() - t0
-            sv.close()
+            try:
+                sv.set_data(Ad, bd, P.loss)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                zv, iv = sv.solve(lam)
+                el = time.perf_counter() - t0
+            except G.GeniosError as exc:
+                variants[name] = {"error": str(exc)}
+                continue
+            finally:
+                sv.close()
             es = {"fp64": 8, "fp32": 4, "bf16": 2, "fp8": 1}[name]
             hvb = P.m * P.n * es
             variants[name] = {
@@ -360,13 +362,14 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="logistic_20000x8000", choices=list(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16", "fp8"])
     ap.add_argument("--eps-kkt", type=float, default=1e-4)
-    ap.add_argument("--max-iter", type=int, default=5000)
+    ap.add_argument("--max-iter", type=int, default=20000)
     ap.add_argument("--variant-list", default="bf16,fp8")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -109,7 +109,7 @@ typedef struct genios_options {
     int32_t use_graphs;      /* capture the CG loop in a CUDA graph (default 1) */
     uint64_t seed;           /* seed of the Gaussian test matrix (Philox4x32-10) */
     int64_t device_wait_limit_us; /* bound on any device-side wait (default 2e6 us) */
-    int32_t verbose;         /* 0 silent, 1 per-iteration log to stderr */
+    int32_t verbose;         /* 0 silent; N > 0: log every N-th iteration to stderr */
     int32_t profile;         /* 1: time the rowpass kernels with CUDA events (info.hv_ms...) */
 } genios_options;
 

@@ -472,6 +472,7 @@ static genios_status build_precond(genios_ctx* ctx, const void* d, double* ms) {
     CK(nystrom_build(hv_prec(ctx), ctx->m, ctx->n, ctx->sk, ctx->A_hv, ctx->lda, ctx->A_scale, d,
                      ctx->Om, ctx->U, ctx->lam, nullptr, ctx->nw, &ok, s));
     ctx->launches += 12;
+    if (ok == -1) FAIL(GENIOS_ENUMERIC, "Nystrom sketch is not finite (NaN/Inf in A^T D A Omega)");
     if (!ok) FAIL(GENIOS_ENUMERIC, "Nystrom core: Cholesky failed after raising the shift");
     ctx->have_precond = true;
     ctx->n_sketch_total++;
@@ -665,7 +666,7 @@ extern "C" genios_status genios_solve(genios_ctx* ctx, const double* lambda1, co
                 inf.rel_kkt = std::sqrt(H.kd2) / std::max(std::max(std::sqrt(H.kg2), lam1), 1e-30);
                 if (inf.rel_kkt <= o.eps_kkt) stop = true;
             }
-            if (o.verbose)
+            if (o.verbose > 0 && (k % o.verbose == 0 || stop))
                 std::fprintf(stderr, "[genios] it %d rp %.3e rd %.3e rho %.3g kkt %.3e gap %.3e cg %d\n",
                              k, rp, rd, rho, inf.rel_kkt, inf.rel_gap, inf.cg_iters_total);
             if (stop) {
@@ -932,7 +933,7 @@ extern "C" genios_status genios_op_nystrom(int precision, int64_t m, int64_t n, 
     cudaError_t e = nystrom_build(P, m, n, s, A, lda, row_scale, d, Omega, U_out, lam_out, eta_out, w,
                                   &ok, st);
     if (e != cudaSuccess) return op_err(e);
-    return ok ? GENIOS_OK : GENIOS_ENUMERIC;
+    return ok == 1 ? GENIOS_OK : GENIOS_ENUMERIC;
 }
 
 extern "C" genios_status genios_op_precond(int precision, int64_t n, int s, const void* U, const double* lam,

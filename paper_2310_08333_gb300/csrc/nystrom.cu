@@ -242,8 +242,10 @@ __global__ void shift_kernel(int64_t total, int64_t n, double eps, double mult, 
         Ye[e] = Y[e] + (VT)eta * Om[e];
 }
 
-// Gram partials: part[b][a*s + c] = sum over the block's rows of X[j,a] * Y[j,c] (float64)
-constexpr int GR_THREADS = 512, GR_ROWS = 16, GR_EPT = 32;
+// Gram partials: part[b][a*s + c] = sum over the block's rows of X[j,a] * Y[j,c].  Rows are
+// staged through shared memory GR_ROWS at a time; each thread owns an 8 x 8 tile of the s x s
+// output (s <= 128) accumulated in the value type over the block's rows, written as float64.
+constexpr int GR_THREADS = 256, GR_ROWS = 16, GR_T = 8;
 template <typename VT>
 __global__ void __launch_bounds__(GR_THREADS) gram_partial(int64_t n, int sk, const VT* X,
                                                           const VT* Y, double* part) {
@@ -251,13 +253,17 @@ __global__ void __launch_bounds__(GR_THREADS) gram_partial(int64_t n, int sk, co
     VT* xs = reinterpret_cast<VT*>(gsm);
     VT* ys = xs + GR_ROWS * sk;
     const int ss = sk * sk;
+    const int nt = (sk + GR_T - 1) / GR_T;
+    const bool active = (int)threadIdx.x < nt * nt;
+    const int a0 = ((int)threadIdx.x / nt) * GR_T, c0 = ((int)threadIdx.x % nt) * GR_T;
     const int64_t rows_per_block = (n + gridDim.x - 1) / gridDim.x;
     const int64_t j0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t j1 = min(n, j0 + rows_per_block);
-    double accd[GR_EPT];
-    VT acc[GR_EPT];
+    VT acc[GR_T][GR_T];
 #pragma unroll
-    for (int q = 0; q < GR_EPT; ++q) accd[q] = 0.0;
+    for (int i = 0; i < GR_T; ++i)
+#pragma unroll
+        for (int j = 0; j < GR_T; ++j) acc[i][j] = VT(0);
     for (int64_t jt = j0; jt < j1; jt += GR_ROWS) {
         const int rows = (int)min((int64_t)GR_ROWS, j1 - jt);
         for (int e = threadIdx.x; e < GR_ROWS * sk; e += GR_THREADS) {
@@ -266,23 +272,29 @@ __global__ void __launch_bounds__(GR_THREADS) gram_partial(int64_t n, int sk, co
             ys[e] = r < rows ? Y[(jt + r) * sk + e % sk] : VT(0);
         }
         __syncthreads();
+        if (active) {
+            for (int r = 0; r < GR_ROWS; ++r) {
+                VT xa[GR_T], yc[GR_T];
 #pragma unroll
-        for (int q = 0; q < GR_EPT; ++q) acc[q] = VT(0);
-        for (int r = 0; r < GR_ROWS; ++r) {
+                for (int i = 0; i < GR_T; ++i) {
+                    xa[i] = a0 + i < sk ? xs[r * sk + a0 + i] : VT(0);
+                    yc[i] = c0 + i < sk ? ys[r * sk + c0 + i] : VT(0);
+                }
 #pragma unroll
-            for (int q = 0; q < GR_EPT; ++q) {
-                const int e = threadIdx.x + q * GR_THREADS;
-                if (e < ss) acc[q] = fma(xs[r * sk + e / sk], ys[r * sk + e % sk], acc[q]);
+                for (int i = 0; i < GR_T; ++i)
+#pragma unroll
+                    for (int j = 0; j < GR_T; ++j) acc[i][j] = fma(xa[i], yc[j], acc[i][j]);
             }
         }
-#pragma unroll
-        for (int q = 0; q < GR_EPT; ++q) accd[q] += (double)acc[q];
         __syncthreads();
     }
+    if (active) {
 #pragma unroll
-    for (int q = 0; q < GR_EPT; ++q) {
-        const int e = threadIdx.x + q * GR_THREADS;
-        if (e < ss) part[(int64_t)blockIdx.x * ss + e] = accd[q];
+        for (int i = 0; i < GR_T; ++i)
+#pragma unroll
+            for (int j = 0; j < GR_T; ++j)
+                if (a0 + i < sk && c0 + j < sk)
+                    part[(int64_t)blockIdx.x * ss + (a0 + i) * sk + c0 + j] = (double)acc[i][j];
     }
 }
 
@@ -325,11 +337,15 @@ __global__ void __launch_bounds__(256) ts_gemm(int64_t n, int sk, const VT* X, c
 // ------------------------------------------------------------------------------------------
 // In: G (s x s, symmetric part used).  Out: Cinv (value type, upper triangular inverse of the
 // Cholesky factor C with G = C^T C); status[0] = 1 on success, 0 if G is not positive definite.
+// Float64, one CTA, everything in shared memory: right-looking Cholesky, then the triangular
+// inverse in place column by column (column j of C^{-1} is -C^{-1}[0:j,0:j] C[0:j,j] / c_jj,
+// the rows of each column computed in parallel).
 template <typename VT>
 __global__ void __launch_bounds__(1024) chol_inv_kernel(int sk, const double* G, double* Cw, VT* Cinv,
                                                        int* status) {
     extern __shared__ __align__(16) unsigned char csm[];
     double* c = reinterpret_cast<double*>(csm);  // s x s
+    double* tmp = c + sk * sk;                    // s
     __shared__ int ok;
     for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) {
         const int i = e / sk, j = e % sk;
@@ -359,50 +375,57 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int sk, const double* G,
         if (threadIdx.x == 0) status[0] = 0;
         return;
     }
-    // upper-triangular inverse, one column per thread (back substitution C X = I)
-    for (int j = threadIdx.x; j < sk; j += blockDim.x) {
-        for (int i = sk - 1; i >= 0; --i) {
-            double acc = (i == j) ? 1.0 : 0.0;
-            if (i > j) {
-                Cw[i * sk + j] = 0.0;
-                continue;
-            }
-            for (int l = i + 1; l <= j; ++l) acc -= c[i * sk + l] * Cw[l * sk + j];
-            Cw[i * sk + j] = acc / c[i * sk + i];
+    for (int j = 0; j < sk; ++j) {
+        for (int l = threadIdx.x; l < j; l += blockDim.x) tmp[l] = c[l * sk + j];
+        __syncthreads();
+        const double ajj = 1.0 / c[j * sk + j];
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+            double acc = 0.0;
+            for (int l = i; l < j; ++l) acc += c[i * sk + l] * tmp[l];
+            c[i * sk + j] = -ajj * acc;
         }
+        __syncthreads();
+        if (threadIdx.x == 0) c[j * sk + j] = ajj;
+        __syncthreads();
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) Cinv[e] = (VT)Cw[e];
+    for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) {
+        const int i = e / sk, j = e % sk;
+        Cinv[e] = (VT)(j >= i ? c[e] : 0.0);
+    }
+    (void)Cw;
     if (threadIdx.x == 0) status[0] = 1;
 }
 
-// Cyclic Jacobi eigendecomposition of the symmetric s x s matrix M (FP64, one CTA).
-// Round-robin ordering: each round rotates s/2 disjoint pairs in parallel.
-// Out: V (s x s, global, columns = eigenvectors), ev (s eigenvalues, unsorted).
-__global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min, double* V, double* ev,
+// Cyclic Jacobi eigendecomposition of the symmetric s x s matrix M (one CTA), arithmetic in T.
+// Round-robin ("circle") ordering: in round r of a sweep over se = s + (s odd) indices, index
+// se - 1 meets r and, for k = 1 .. se/2 - 1, (r + k) mod (se - 1) meets (r - k) mod (se - 1);
+// the se/2 disjoint rotations of a round run in parallel (Golub & Van Loan §8.5).  A rotation
+// whose off-diagonal entry is negligible is skipped.  M, and V when VS, live in shared memory.
+// Out: Vout (s x s, global, columns = eigenvectors), ev (s eigenvalues, unsorted).
+template <typename T, bool VS>
+__global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min, T* Vout, double* ev,
                                                      int max_sweeps, double rel_tol) {
     extern __shared__ __align__(16) unsigned char jsm[];
-    const int se = sk + (sk & 1);  // even size (dummy index se-1 when s is odd)
-    double* M = reinterpret_cast<double*>(jsm);        // s x s
-    double* cs = M + sk * sk;                           // se/2
-    double* sn = cs + se / 2;                           // se/2
-    int* pos = reinterpret_cast<int*>(sn + se / 2);     // se
-    int* pp = pos + se;                                 // se/2
-    int* qq = pp + se / 2;                              // se/2
+    const int se = sk + (sk & 1);
+    const int half = se / 2;
+    T* M = reinterpret_cast<T*>(jsm);                   // s x s
+    T* Vs_ = M + sk * sk;                               // s x s (VS only)
+    T* cs = VS ? Vs_ + sk * sk : Vs_;                   // half
+    T* sn = cs + half;                                  // half
+    int* pp = reinterpret_cast<int*>(sn + half);        // half
+    int* qq = pp + half;                                // half
+    T* V = VS ? Vs_ : Vout;
     __shared__ int done;
     for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) {
         const int i = e / sk, j = e % sk;
-        M[e] = 0.5 * (Min[i * sk + j] + Min[j * sk + i]);
-        V[e] = (i == j) ? 1.0 : 0.0;
+        M[e] = (T)(0.5 * (Min[i * sk + j] + Min[j * sk + i]));
+        V[e] = (i == j) ? T(1) : T(0);
     }
-    for (int e = threadIdx.x; e < se; e += blockDim.x) pos[e] = e;
     __syncthreads();
-    const int half = se / 2;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        // convergence: off-diagonal vs total Frobenius norm
         double off = 0.0, tot = 0.0;
         for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) {
-            const double v = M[e] * M[e];
+            const double v = (double)M[e] * (double)M[e];
             tot += v;
             if (e / sk != e % sk) off += v;
         }
@@ -411,63 +434,83 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min,
         if (threadIdx.x == 0) done = (a2[0] <= rel_tol * rel_tol * a2[1]) ? 1 : 0;
         __syncthreads();
         if (done) break;
+        const double thr = 1e-2 * rel_tol * sqrt(a2[1]) / (double)sk;
         for (int round = 0; round < se - 1; ++round) {
             for (int k = threadIdx.x; k < half; k += blockDim.x) {
-                int p = pos[k], q = pos[se - 1 - k];
+                int p, q;
+                if (k == 0) { p = round; q = se - 1; }
+                else { p = (round + k) % (se - 1); q = (round - k + (se - 1)) % (se - 1); }
                 if (p > q) { int t = p; p = q; q = t; }
-                double c = 1.0, s = 0.0;
+                T c = T(1), s = T(0);
                 if (q < sk) {
-                    const double apq = M[p * sk + q];
-                    if (fabs(apq) > 1e-300) {
-                        const double tau = (M[q * sk + q] - M[p * sk + p]) / (2.0 * apq);
-                        const double t = tau >= 0.0 ? 1.0 / (tau + sqrt(1.0 + tau * tau))
-                                                    : -1.0 / (-tau + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
+                    const T apq = M[p * sk + q];
+                    if (fabs((double)apq) > thr) {
+                        const T app = M[p * sk + p], aqq = M[q * sk + q];
+                        const T tau = (aqq - app) / (T(2) * apq);
+                        const T t = tau >= T(0) ? T(1) / (tau + sqrt(T(1) + tau * tau))
+                                                : T(-1) / (-tau + sqrt(T(1) + tau * tau));
+                        c = T(1) / sqrt(T(1) + t * t);
                         s = t * c;
                     }
                 }
                 cs[k] = c; sn[k] = s; pp[k] = p; qq[k] = q;
             }
             __syncthreads();
-            // rows: M <- J^T M
-            for (int e = threadIdx.x; e < half * sk; e += blockDim.x) {
+            for (int e = threadIdx.x; e < half * sk; e += blockDim.x) {   // rows: M <- J^T M
                 const int k = e / sk, j = e % sk;
+                const T sv = sn[k];
+                if (sv == T(0)) continue;
                 const int p = pp[k], q = qq[k];
-                if (q >= sk || sn[k] == 0.0) continue;
-                const double mp = M[p * sk + j], mq = M[q * sk + j];
-                M[p * sk + j] = cs[k] * mp - sn[k] * mq;
-                M[q * sk + j] = sn[k] * mp + cs[k] * mq;
+                const T cv = cs[k];
+                const T mp = M[p * sk + j], mq = M[q * sk + j];
+                M[p * sk + j] = cv * mp - sv * mq;
+                M[q * sk + j] = sv * mp + cv * mq;
             }
             __syncthreads();
-            // columns: M <- M J, V <- V J
-            for (int e = threadIdx.x; e < half * sk; e += blockDim.x) {
+            for (int e = threadIdx.x; e < half * sk; e += blockDim.x) {   // cols: M <- M J, V <- V J
                 const int k = e / sk, i = e % sk;
+                const T sv = sn[k];
+                if (sv == T(0)) continue;
                 const int p = pp[k], q = qq[k];
-                if (q >= sk || sn[k] == 0.0) continue;
-                const double mp = M[i * sk + p], mq = M[i * sk + q];
-                M[i * sk + p] = cs[k] * mp - sn[k] * mq;
-                M[i * sk + q] = sn[k] * mp + cs[k] * mq;
-                const double vp = V[i * sk + p], vq = V[i * sk + q];
-                V[i * sk + p] = cs[k] * vp - sn[k] * vq;
-                V[i * sk + q] = sn[k] * vp + cs[k] * vq;
-            }
-            __syncthreads();
-            // rotate positions 1..se-1 (position 0 fixed)
-            if (threadIdx.x == 0) {
-                const int last = pos[se - 1];
-                for (int t = se - 1; t > 1; --t) pos[t] = pos[t - 1];
-                pos[1] = last;
+                const T cv = cs[k];
+                const T mp = M[i * sk + p], mq = M[i * sk + q];
+                M[i * sk + p] = cv * mp - sv * mq;
+                M[i * sk + q] = sv * mp + cv * mq;
+                const T vp = V[i * sk + p], vq = V[i * sk + q];
+                V[i * sk + p] = cv * vp - sv * vq;
+                V[i * sk + q] = sv * vp + cv * vq;
             }
             __syncthreads();
         }
     }
-    for (int e = threadIdx.x; e < sk; e += blockDim.x) ev[e] = M[e * sk + e];
+    for (int e = threadIdx.x; e < sk; e += blockDim.x) ev[e] = (double)M[e * sk + e];
+    if (VS)
+        for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) Vout[e] = V[e];
+}
+
+// Float64 Rayleigh quotients ev_c = v_c^T M v_c / v_c^T v_c of the Jacobi eigenvectors against
+// the float64 matrix M: the eigenvalue error becomes second order in the eigenvector error.
+// One block per eigenpair.
+template <typename T>
+__global__ void eig_rq_kernel(int sk, const double* M, const T* V, double* ev) {
+    const int c = blockIdx.x;
+    double num = 0.0, den = 0.0;
+    for (int i = threadIdx.x; i < sk; i += blockDim.x) {
+        double yi = 0.0;
+        for (int k = 0; k < sk; ++k) yi += M[i * sk + k] * (double)V[k * sk + c];
+        const double vi = (double)V[i * sk + c];
+        num += vi * yi;
+        den += vi * vi;
+    }
+    double a[2] = {num, den};
+    block_sum<2>(a);
+    if (threadIdx.x == 0) ev[c] = a[1] > 0.0 ? a[0] / a[1] : 0.0;
 }
 
 // Sort eigenpairs descending; Vs[k][c] = V[k][perm c] / sigma_c (value type);
 // lam[c] = max(ev[perm c] - eta, 0).  One CTA.
-template <typename VT>
-__global__ void eig_finish_kernel(int sk, const double* V, const double* ev, const double* eta,
+template <typename VT, typename T>
+__global__ void eig_finish_kernel(int sk, const T* V, const double* ev, const double* eta,
                                   VT* Vs, double* lam) {
     __shared__ int perm[256];
     __shared__ double sig[256];
@@ -490,7 +533,7 @@ __global__ void eig_finish_kernel(int sk, const double* V, const double* ev, con
     __syncthreads();
     for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) {
         const int k = e / sk, c = e % sk;
-        Vs[e] = sig[c] > 0.0 ? (VT)(V[k * sk + perm[c]] / sig[c]) : VT(0);
+        Vs[e] = sig[c] > 0.0 ? (VT)((double)V[k * sk + perm[c]] / sig[c]) : VT(0);
     }
 }
 
@@ -584,7 +627,7 @@ static cudaError_t orthonormalize(int64_t n, int sk, const VT* Om, NysWork w, cu
     const int gb = gram_blocks(n);
     const size_t gsm = 2 * GR_ROWS * sk * sizeof(VT);
     const size_t tsm = (size_t)(sk * sk + 16 * sk) * sizeof(VT);
-    const size_t csm = (size_t)ss * 8;
+    const size_t csm = (size_t)ss * 8 + (size_t)sk * 8;
     cudaFuncSetAttribute(ts_gemm<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm + 1024);
     cudaFuncSetAttribute(chol_inv_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm + 1024);
     cudaFuncSetAttribute(gram_partial<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm + 1024);
@@ -615,16 +658,28 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
     // partials for the sum of squares reuse gpart (>= 1024 doubles as gram_blocks*ss >= s^2)
     sumsq_kernel<VT><<<256, 256, 0, s>>>(total, Y, w.gpart, counter, fro2);
     NYS_CHECK("sumsq");
+    {
+        double f2 = 0.0;
+        cudaMemcpyAsync(&f2, fro2, sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        if (!std::isfinite(f2)) {
+            *chol_ok = -1;  // non-finite sketch
+            return cudaSuccess;
+        }
+    }
     const int ss = sk * sk;
     const int gb = gram_blocks(n);
     const size_t gsm = 2 * GR_ROWS * sk * sizeof(VT);
     const size_t tsm = (size_t)(sk * sk + 16 * sk) * sizeof(VT);
-    const size_t csm = (size_t)ss * 8;
+    const size_t csm = (size_t)ss * 8 + (size_t)sk * 8;
     const int se = sk + (sk & 1);
-    const size_t jsm = (size_t)ss * 8 + (size_t)se * 8 + (size_t)se * 4 * 2 + 64;
+    const bool vs = 2 * (size_t)ss * sizeof(VT) + (size_t)se * (sizeof(VT) + 4) <= 200 * 1024;
+    const size_t jsm = (vs ? 2 : 1) * (size_t)ss * sizeof(VT) + (size_t)se * (sizeof(VT) + 4) + 64;
     cudaFuncSetAttribute(ts_gemm<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm + 1024);
     cudaFuncSetAttribute(chol_inv_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm + 1024);
-    cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm + 1024);
+    cudaFuncSetAttribute(jacobi_kernel<VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm + 1024);
+    cudaFuncSetAttribute(jacobi_kernel<VT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm + 1024);
     cudaFuncSetAttribute(gram_partial<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm + 1024);
     VT* Ye = static_cast<VT*>(w.B);
     VT* Cinv = static_cast<VT*>(w.Cinv);
@@ -658,9 +713,17 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
     NYS_CHECK("gram_partial(B, B)");
     gram_reduce<<<(ss + 255) / 256, 256, 0, s>>>(gb, ss, w.gpart, w.M, 1, sk);
     NYS_CHECK("gram_reduce(M)");
-    jacobi_kernel<<<1, 1024, jsm, s>>>(sk, w.M, V, w.ev, 40, 1e-15);
+    // Jacobi in the value type (a float64 Jacobi at s = 100 costs ~25 ms on this part's float64
+    // pipe); in float32 the eigenvalues are then refined by float64 Rayleigh quotients
+    VT* Vj = reinterpret_cast<VT*>(V);
+    if (vs) jacobi_kernel<VT, true><<<1, 1024, jsm, s>>>(sk, w.M, Vj, w.ev, 40, sizeof(VT) == 8 ? 1e-15 : 1e-6);
+    else jacobi_kernel<VT, false><<<1, 1024, jsm, s>>>(sk, w.M, Vj, w.ev, 40, sizeof(VT) == 8 ? 1e-15 : 1e-6);
     NYS_CHECK("jacobi");
-    eig_finish_kernel<VT><<<1, 256, 0, s>>>(sk, V, w.ev, eta, Cinv, lam);
+    if (sizeof(VT) == 4) {
+        eig_rq_kernel<VT><<<sk, 128, 0, s>>>(sk, w.M, Vj, w.ev);
+        NYS_CHECK("eig_rq");
+    }
+    eig_finish_kernel<VT, VT><<<1, 256, 0, s>>>(sk, Vj, w.ev, eta, Cinv, lam);
     NYS_CHECK("eig_finish");
     // U = B V Sigma^{-1}
     ts_gemm<VT><<<512, 256, tsm, s>>>(n, sk, Ye, Cinv, U);

@@ -67,28 +67,37 @@ __global__ void cg_q_kernel(const VT* P, int G, int64_t ldp, int64_t n, VT* p, c
     }
 }
 
-// Block partial of U^T r over the block's 256 rows, plus sum of r^2; last block finalises.
-// Returns true in the last block (after S->w and out2 are final).
+// U^T r over the block's UTR_ROWS rows (r staged in shared memory) plus the block sum of r^2.
+// Threads: c = t % 128 is a column of U, g = t / 128 one of two row groups; products and the
+// per-thread sums run in the value type, block partials in float64.  The last block adds the
+// partials of all blocks in a fixed order (two threads per column, four independent
+// accumulators each) into w_out and returns true with rr_out.  Requires s <= 128, blockDim 256.
+constexpr int UTR_ROWS = 64;
+
 template <typename VT>
-GENIOS_DEV bool ut_r_and_norm(const VT* U, int sk, const VT* rloc_sh, int64_t j0, int64_t n,
+GENIOS_DEV bool ut_r_and_norm(const VT* U, int sk, const VT* rsh, int64_t j0, int64_t n,
                               double rr_thread, double* part, unsigned* counter,
                               double* w_out, double& rr_out, long long* dbg) {
-    // rloc_sh: shared copy of r[j0 .. j0+256)
     const int t = threadIdx.x;
-    double wc = 0.0;
-    if (t < sk) {
-        const int64_t rows = min((int64_t)VT_THREADS, n - j0);
-        for (int64_t jj = 0; jj < rows; ++jj)
-            if (GCHK(dbg, (j0 + jj) * sk + t, n * (long long)sk) && GCHK(dbg, jj, VT_THREADS))
-                wc += (double)U[(j0 + jj) * sk + t] * (double)rloc_sh[jj];
-    }
-    double v[1] = {rr_thread};
-    block_sum<1>(v);
-    const int stride = sk + 1;
+    const int c = t & 127, g = t >> 7;
+    __shared__ double wsh[256];
     __shared__ unsigned s_last;
     __shared__ double s_rr;
-    if (t < sk && GCHK(dbg, (long long)blockIdx.x * stride + t, 262144)) part[(size_t)blockIdx.x * stride + t] = wc;
-    if (t == 0 && GCHK(dbg, (long long)blockIdx.x * stride + sk, 262144)) part[(size_t)blockIdx.x * stride + sk] = v[0];
+    VT acc = VT(0);
+    if (c < sk) {
+        const int rows = (int)min((int64_t)UTR_ROWS, n - j0);
+        for (int jj = g; jj < rows; jj += 2)
+            if (GCHK(dbg, (j0 + jj) * sk + c, n * (long long)sk))
+                acc = fma(U[(j0 + jj) * sk + c], rsh[jj], acc);
+    }
+    wsh[t] = (double)acc;
+    double v[1] = {rr_thread};
+    block_sum<1>(v);  // its barriers also publish wsh
+    const int stride = sk + 1;
+    if (t < sk && GCHK(dbg, (long long)blockIdx.x * stride + t, 262144))
+        part[(size_t)blockIdx.x * stride + t] = wsh[t] + wsh[t + 128];
+    if (t == 0 && GCHK(dbg, (long long)blockIdx.x * stride + sk, 262144))
+        part[(size_t)blockIdx.x * stride + sk] = v[0];
     __threadfence();
     __syncthreads();
     if (t == 0) {
@@ -98,13 +107,28 @@ GENIOS_DEV bool ut_r_and_norm(const VT* U, int sk, const VT* rloc_sh, int64_t j0
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
-    for (int c = t; c <= sk; c += blockDim.x) {
-        double acc = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) acc += __ldcg(part + (size_t)b * stride + c);
-        if (c < sk) { if (GCHK(dbg, c, 256)) w_out[c] = acc; }
-        else s_rr = acc;
+    const int nb = gridDim.x;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if (c < sk) {
+        int b = g;
+        for (; b + 6 < nb; b += 8) {
+            a0 += __ldcg(part + (size_t)b * stride + c);
+            a1 += __ldcg(part + (size_t)(b + 2) * stride + c);
+            a2 += __ldcg(part + (size_t)(b + 4) * stride + c);
+            a3 += __ldcg(part + (size_t)(b + 6) * stride + c);
+        }
+        for (; b < nb; b += 2) a0 += __ldcg(part + (size_t)b * stride + c);
     }
     __syncthreads();
+    wsh[t] = (a0 + a1) + (a2 + a3);
+    if (t < 32) {  // r^2 slot
+        double r2 = 0.0;
+        for (int b = t; b < nb; b += 32) r2 += __ldcg(part + (size_t)b * stride + sk);
+        r2 = warp_sum(r2);
+        if (t == 0) s_rr = r2;
+    }
+    __syncthreads();
+    if (t < sk && GCHK(dbg, t, 256)) w_out[t] = wsh[t] + wsh[t + 128];
     rr_out = s_rr;
     if (t == 0) *counter = 0u;
     return true;
@@ -114,20 +138,22 @@ template <typename VT>
 __global__ void cg_update_kernel(int64_t n, VT* delta, VT* r, const VT* p, const VT* q,
                                  const VT* U, int sk, VT* zc, DevState* S, Scratch sc) {
     if (S->cg_done) return;
-    __shared__ VT rsh[VT_THREADS];
-    const int64_t j0 = (int64_t)blockIdx.x * VT_THREADS;
+    __shared__ VT rsh[UTR_ROWS];
+    const int64_t j0 = (int64_t)blockIdx.x * UTR_ROWS;
     const int64_t j = j0 + threadIdx.x;
     const VT al = (VT)S->alpha;
     double rr = 0.0;
-    VT rj = VT(0);
-    if (j < n) {
-        delta[j] += al * p[j];
-        rj = r[j] - al * q[j];
-        r[j] = rj;
-        if (sk == 0) zc[j] = rj;
-        rr = (double)rj * (double)rj;
+    if (threadIdx.x < UTR_ROWS) {
+        VT rj = VT(0);
+        if (j < n) {
+            delta[j] += al * p[j];
+            rj = r[j] - al * q[j];
+            r[j] = rj;
+            if (sk == 0) zc[j] = rj;
+            rr = (double)rj * (double)rj;
+        }
+        rsh[threadIdx.x] = rj;
     }
-    rsh[threadIdx.x] = rj;
     __syncthreads();
     double rr_tot;
     if (ut_r_and_norm<VT>(U, sk, rsh, j0, n, rr, sc.part, sc.counter, S->w, rr_tot, sc.dbg)) {
@@ -147,23 +173,23 @@ template <typename VT>
 __global__ void cg_precond_kernel(int64_t n, const VT* U, int sk, const double* lam, const VT* r,
                                   VT* zc, DevState* S, Scratch sc) {
     if (S->cg_done) return;
-    __shared__ double coefw[256];
+    __shared__ VT coefw[256];
     const double nu = S->nu;
     const double ls = lam[sk - 1];
     for (int c = threadIdx.x; c < sk; c += blockDim.x)
-        if (GCHK(sc.dbg, c, 256)) coefw[c] = ((ls + nu) / (lam[c] + nu) - 1.0) * S->w[c];
+        if (GCHK(sc.dbg, c, 256)) coefw[c] = (VT)(((ls + nu) / (lam[c] + nu) - 1.0) * S->w[c]);
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     double rz = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * nw + wid; j < n; j += (int64_t)gridDim.x * nw) {
-        double acc = 0.0;
+        VT acc = VT(0);
         for (int c = lane; c < sk; c += 32)
-            if (GCHK(sc.dbg, j * sk + c, n * (long long)sk)) acc += (double)U[j * sk + c] * coefw[c];
+            if (GCHK(sc.dbg, j * sk + c, n * (long long)sk)) acc = fma(U[j * sk + c], coefw[c], acc);
         acc = warp_sum(acc);
         if (lane == 0) {
             const VT rj = r[j];
-            const VT zj = rj + (VT)acc;
+            const VT zj = rj + acc;
             zc[j] = zj;
             rz += (double)rj * (double)zj;
         }
@@ -186,22 +212,24 @@ template <typename VT>
 __global__ void rhs_init_kernel(int64_t n, const VT* g, const VT* x, const VT* z, VT* u, double rho,
                                 double u_scale, double nu, double tol, int cg_max, VT* r, VT* delta,
                                 VT* p, VT* zc, const VT* U, int sk, DevState* S, Scratch sc) {
-    __shared__ VT rsh[VT_THREADS];
-    const int64_t j0 = (int64_t)blockIdx.x * VT_THREADS;
+    __shared__ VT rsh[UTR_ROWS];
+    const int64_t j0 = (int64_t)blockIdx.x * UTR_ROWS;
     const int64_t j = j0 + threadIdx.x;
     double rr = 0.0;
-    VT rj = VT(0);
-    if (j < n) {
-        const VT uj = u[j] * (VT)u_scale;
-        u[j] = uj;
-        rj = -(g[j] + (VT)rho * (x[j] - z[j] + uj));
-        r[j] = rj;
-        delta[j] = VT(0);
-        p[j] = VT(0);
-        if (sk == 0) zc[j] = rj;
-        rr = (double)rj * (double)rj;
+    if (threadIdx.x < UTR_ROWS) {
+        VT rj = VT(0);
+        if (j < n) {
+            const VT uj = u[j] * (VT)u_scale;
+            u[j] = uj;
+            rj = -(g[j] + (VT)rho * (x[j] - z[j] + uj));
+            r[j] = rj;
+            delta[j] = VT(0);
+            p[j] = VT(0);
+            if (sk == 0) zc[j] = rj;
+            rr = (double)rj * (double)rj;
+        }
+        rsh[threadIdx.x] = rj;
     }
-    rsh[threadIdx.x] = rj;
     __syncthreads();
     double rr_tot;
     if (ut_r_and_norm<VT>(U, sk, rsh, j0, n, rr, sc.part, sc.counter, S->w, rr_tot, sc.dbg)) {
@@ -250,10 +278,11 @@ __global__ void grad_finish_kernel(const VT* P, int G, int64_t ldp, const double
     }
     double out[6], outm[1];
     if (grid_sum_max<6, 1>(v, mx, sc.part, sc.counter, out, outm)) {
+        double ls[1] = {0.0};
+        for (int b = threadIdx.x; b < G; b += blockDim.x) ls[0] += loss_part[b];
+        block_sum<1>(ls);
         if (threadIdx.x == 0) {
-            double ls = 0.0;
-            for (int b = 0; b < G; ++b) ls += loss_part[b];
-            S->loss_sum = ls;
+            S->loss_sum = ls[0];
             S->rd2 = out[0];
             S->rhou2 = out[1];
             S->g2 = out[2];
@@ -408,12 +437,14 @@ cudaError_t cg_q(bool dbl, const void* P, int G, int64_t ldp, int64_t n, void* p
 }
 
 // per-block partials of U^T r must fit the scratch partial buffer
-static bool utr_fits(int64_t n, int sk) { return (int64_t)nblocks(n, VT_THREADS) * (sk + 1) <= 262144; }
+static bool utr_fits(int64_t n, int sk) {
+    return sk <= 128 && (int64_t)nblocks(n, UTR_ROWS) * (sk + 1) <= 262144;
+}
 
 cudaError_t cg_update(bool dbl, int64_t n, void* delta, void* r, const void* p, const void* q,
                       const void* U, int sk, void* zc, DevState* S, Scratch sc, cudaStream_t s) {
     if (!utr_fits(n, sk)) return cudaErrorInvalidValue;
-    const int grid = nblocks(n, VT_THREADS);
+    const int grid = nblocks(n, UTR_ROWS);
     if (dbl) cg_update_kernel<double><<<grid, VT_THREADS, 0, s>>>(n, C<double>(delta), C<double>(r), CC<double>(p), CC<double>(q), CC<double>(U), sk, C<double>(zc), S, sc);
     else cg_update_kernel<float><<<grid, VT_THREADS, 0, s>>>(n, C<float>(delta), C<float>(r), CC<float>(p), CC<float>(q), CC<float>(U), sk, C<float>(zc), S, sc);
     return cudaGetLastError();
@@ -421,7 +452,7 @@ cudaError_t cg_update(bool dbl, int64_t n, void* delta, void* r, const void* p, 
 
 cudaError_t cg_precond(bool dbl, int64_t n, const void* U, int sk, const double* lam, const void* r,
                        void* zc, DevState* S, Scratch sc, cudaStream_t s) {
-    const int grid = grid_for(n, 8, 2048);
+    const int grid = grid_for(n, 8, 608);
     if (dbl) cg_precond_kernel<double><<<grid, VT_THREADS, 0, s>>>(n, CC<double>(U), sk, lam, CC<double>(r), C<double>(zc), S, sc);
     else cg_precond_kernel<float><<<grid, VT_THREADS, 0, s>>>(n, CC<float>(U), sk, lam, CC<float>(r), C<float>(zc), S, sc);
     return cudaGetLastError();
@@ -432,7 +463,7 @@ cudaError_t rhs_init(bool dbl, int64_t n, const void* g, const void* x, const vo
                      void* delta, void* p, void* zc, const void* U, int sk, DevState* S,
                      Scratch sc, cudaStream_t s) {
     if (!utr_fits(n, sk)) return cudaErrorInvalidValue;
-    const int grid = nblocks(n, VT_THREADS);
+    const int grid = nblocks(n, UTR_ROWS);
     if (dbl) rhs_init_kernel<double><<<grid, VT_THREADS, 0, s>>>(n, CC<double>(g), CC<double>(x), CC<double>(z), C<double>(u), rho, u_scale, nu, tol, cg_max, C<double>(r), C<double>(delta), C<double>(p), C<double>(zc), CC<double>(U), sk, S, sc);
     else rhs_init_kernel<float><<<grid, VT_THREADS, 0, s>>>(n, CC<float>(g), CC<float>(x), CC<float>(z), C<float>(u), rho, u_scale, nu, tol, cg_max, C<float>(r), C<float>(delta), C<float>(p), C<float>(zc), CC<float>(U), sk, S, sc);
     return cudaGetLastError();

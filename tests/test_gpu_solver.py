@@ -119,7 +119,8 @@ def test_config3_logistic_reduced_parity(G, prec):
     lam = P.lam_frac * checks.lambda_max(A, b, "logistic")
     ref = oadmm.solve(A, b, "logistic", lam, rho=30.0, tol=1e-13, check_every=5)
     assert ref["converged"]
-    z, info, _ = gpu_solve(G, P, prec, lam, rho=30.0)
+    # float32 evaluation of a_i^T x floors the reachable relative KKT near 2e-6 here
+    z, info, _ = gpu_solve(G, P, prec, lam, rho=30.0, eps_kkt=1e-10 if prec == 0 else 5e-6)
     assert info["status"] == 0, info
     if prec == 0:
         assert_parity(P, z, ref["z"], lam, 0.0, "logistic")
@@ -135,7 +136,7 @@ def test_elastic_net_logistic_parity(G):
     lam = 0.01 * checks.lambda_max(A, b, "logistic")
     ref = oadmm.solve(A, b, "logistic", lam, 1e-3, rho=20.0, tol=1e-13, check_every=5)
     assert ref["converged"]
-    z, info, _ = gpu_solve(G, P, 1, lam, 1e-3, rho=20.0)
+    z, info, _ = gpu_solve(G, P, 1, lam, 1e-3, rho=20.0, eps_kkt=5e-6)
     assert info["status"] == 0, info
     tol = max(1e-5, derived_tol(A, b, ref["z"], "logistic", lam, 1e-3, info["rel_kkt"]))
     print(f"FP32 elastic-net logistic: rel KKT {info['rel_kkt']:.2e}, derived tol {tol:.2e}")
@@ -215,7 +216,7 @@ def test_config3_full_size_kkt_property(G):
     P = problems.logistic_lowrank()
     A32 = P.A.astype(np.float32)
     z, info, lmax = gpu_solve(G, P, 1, P.lam_frac * checks.lambda_max(A32.astype(np.float64), P.b, "logistic"),
-                              rho=BENCH_RHO, eps_kkt=1e-4, max_iter=5000)
+                              rho=BENCH_RHO, eps_kkt=1e-4, max_iter=12000)
     A = A32.astype(np.float64)
     lam = info["lambda1"]
     kkt = checks.rel_kkt(A, P.b, z, "logistic", lam)
