@@ -282,6 +282,28 @@ genios_status genios_op_pcg(int precision, int64_t m, int64_t n, const void* A, 
                             int s, const void* U, const double* lam, double rtol, int max_iter,
                             void* delta_out, int* iters_out, double* relres_out, void* stream);
 
+/* Size of the fixed device scratch used by genios_op_hv_noalloc (8 MiB). */
+#define GENIOS_HV_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* genios_op_hv without a workspace: the same product y = A^T (d .* (A v)) + nu v with the same
+ * arguments as genios_op_hv minus the workspace, for callers that cannot allocate device memory
+ * at all, e.g. code inside a host application that owns every byte of device memory and hands
+ * out no scratch, or a path where an allocation could fail or stall.  The paper has no
+ * counterpart: this is a deployment convenience.
+ *   - It calls no cudaMalloc / cudaFree and no allocating library routine.  Its scratch (the
+ *     per-CTA partial sums) is a fixed GENIOS_HV_NOALLOC_SCRATCH_BYTES array in the library
+ *     image, present on every GPU that loads the library and held until the process exits.
+ *   - Limit: (number of CTAs of the rowpass, at most the SM count) x lda x value size must fit
+ *     the scratch, e.g. n <= 13,797 (float32) or n <= 6,898 (float64) on a 152-SM GPU; larger
+ *     requests return GENIOS_EINVAL with the reason in genios_last_error(NULL).
+ *   - The first call on a device looks up the array's device address on that device (once);
+ *     make that first call before any stream capture.
+ *   - All calls share the scratch.  Calls whose kernels may overlap on the GPU (different
+ *     streams, or unordered host threads on one device) race on it; order them. */
+genios_status genios_op_hv_noalloc(int precision, int64_t m, int64_t n, const void* A, int64_t lda,
+                                   const float* row_scale, const void* d, double nu, const void* v,
+                                   void* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,7 @@ SIGNATURES = {
     "genios_op_quantize": (_i32, [_i32, _i64, _i64, _vp, _i64, _vp, _vp, _vp, _vp]),
     "genios_op_pcg": (_i32, [_i32, _i64, _i64, _vp, _i64, _vp, _vp, _d, _vp, _i32, _vp, _vp, _d, _i32,
                              _vp, C.POINTER(_i32), C.POINTER(_d), _vp]),
+    "genios_op_hv_noalloc": (_i32, [_i32, _i64, _i64, _vp, _i64, _vp, _vp, _d, _vp, _vp, _vp]),
 }
 
 _lib = None

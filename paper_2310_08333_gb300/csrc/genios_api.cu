@@ -62,6 +62,8 @@ bool is_device_ptr(const void* p) {
 
 }  // namespace
 
+void genios::set_last_error(const std::string& msg) { g_create_error = msg; }
+
 struct genios_ctx {
     genios_options opt;
     int device = 0;

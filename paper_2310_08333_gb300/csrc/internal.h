@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <string>
 
 namespace genios {
 
@@ -84,6 +85,8 @@ struct RowpassPlan {
 };
 
 int device_sm_count();
+// Message returned by genios_last_error(NULL) on this thread.
+void set_last_error(const std::string& msg);
 RowpassPlan rowpass_plan(int prec, int64_t m, int64_t n, int64_t lda);
 cudaError_t rowpass_launch(const RowpassArgs& a, const RowpassPlan& p, cudaStream_t s);
 

@@ -151,6 +151,15 @@ def hv(prec, A, n, d, nu, v, row_scale=None):
     return y
 
 
+def hv_noalloc(prec, A, n, d, nu, v, row_scale=None):
+    """Same product as ``hv`` through the entry point that allocates nothing (fixed scratch)."""
+    m = A.shape[0]
+    y = torch.empty(n, dtype=_vt(prec), device="cuda")
+    _chk(L.lib().genios_op_hv_noalloc(prec, m, n, _ptr(A), A.shape[1], _ptr(row_scale), _ptr(d), nu,
+                                      _ptr(v), _ptr(y), _stream_ptr()))
+    return y
+
+
 def gradient(loss, prec, A, A_lo, n, b, x, lam2):
     m = A.shape[0]
     g = torch.empty(n, dtype=_vt(prec), device="cuda")
@@ -237,5 +246,5 @@ def pcg(prec, A, n, d, nu, r, U=None, lam=None, rtol=1e-6, max_iter=100, row_sca
     return delta, it.value, rel.value
 
 
-ops = SimpleNamespace(lda=lda, pad=pad, hv=hv, gradient=gradient, zu_update=zu_update, nystrom=nystrom,
+ops = SimpleNamespace(lda=lda, pad=pad, hv=hv, hv_noalloc=hv_noalloc, gradient=gradient, zu_update=zu_update, nystrom=nystrom,
                       precond=precond, omega=omega, philox=philox, quantize=quantize, pcg=pcg)
