@@ -43,7 +43,11 @@ struct DevState {
     double conj_sum;  // sum_i loss*(nu_i)
     double btnu;      // b^T nu
     double gap_scale; // scale applied to loss'(Ax - b)
-    double pad[4];
+    int32_t cg_guard; // condition-kernel counter: bounds the device-side CG loop
+    int32_t hv_count; // rowpass (Hv) launches timed on the device
+    unsigned long long hv_t0, hv_t1;  // first-CTA start / last-CTA end of the current Hv launch (ns)
+    double hv_ns;     // accumulated device time of the timed Hv launches
+    double pad[1];
     double w[256];    // U^T r (Nystrom preconditioner), s <= 256
 };
 
@@ -74,6 +78,7 @@ struct RowpassArgs {
     int* err;
     long long wait_limit;       // clock cycles
     long long* dbg;             // bounds-check record (checked builds only)
+    unsigned long long* timer;  // if non-null: [0] min CTA start, [1] max CTA end (globaltimer ns)
     long long smem_bytes;       // dynamic shared memory of the launch (checked builds)
     long long partial_len;      // elements of `partial` (checked builds)
 };
@@ -111,6 +116,10 @@ cudaError_t cg_update(bool dbl, int64_t n, void* delta, void* r, const void* p, 
 // CG: zc = P^{-1} r (Eq. (10)) from S->w; rz, beta
 cudaError_t cg_precond(bool dbl, int64_t n, const void* U, int sk, const double* lam,
                        const void* r, void* zc, DevState* S, Scratch sc, cudaStream_t s);
+// Device-side CG loop condition (CUDA graph conditional WHILE node): continue while the CG is
+// not done and the guard counter has not passed cg_max + 2; also folds the device timer of the
+// last Hv launch into S->hv_ns / hv_count when `timed`.
+cudaError_t cg_condition(unsigned long long handle, DevState* S, int timed, cudaStream_t s);
 // x-step right-hand side and CG initialisation:
 //   u *= u_scale; r = -(g + rho (x - z + u)); delta = 0; p = 0; rhs2; U^T r
 cudaError_t rhs_init(bool dbl, int64_t n, const void* g, const void* x, const void* z, void* u,

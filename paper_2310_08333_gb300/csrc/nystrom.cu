@@ -667,6 +667,15 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
             *chol_ok = -1;  // non-finite sketch
             return cudaSuccess;
         }
+        if (f2 == 0.0) {
+            // A^T D A Omega = 0 (e.g. D = 0): the approximation is 0, lam = 0 and any orthonormal
+            // U; Eq. (10) then reduces to the identity
+            cudaMemcpyAsync(U, Om, (size_t)total * sizeof(VT), cudaMemcpyDeviceToDevice, s);
+            cudaMemsetAsync(lam, 0, (size_t)sk * sizeof(double), s);
+            if (eta_out) cudaMemsetAsync(eta_out, 0, sizeof(double), s);
+            *chol_ok = 1;
+            return cudaGetLastError();
+        }
     }
     const int ss = sk * sk;
     const int gb = gram_blocks(n);
@@ -716,8 +725,12 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
     // Jacobi in the value type (a float64 Jacobi at s = 100 costs ~25 ms on this part's float64
     // pipe); in float32 the eigenvalues are then refined by float64 Rayleigh quotients
     VT* Vj = reinterpret_cast<VT*>(V);
-    if (vs) jacobi_kernel<VT, true><<<1, 1024, jsm, s>>>(sk, w.M, Vj, w.ev, 40, sizeof(VT) == 8 ? 1e-15 : 1e-6);
-    else jacobi_kernel<VT, false><<<1, 1024, jsm, s>>>(sk, w.M, Vj, w.ev, 40, sizeof(VT) == 8 ? 1e-15 : 1e-6);
+    // stop when the off-diagonal part is below the arithmetic's noise (float32: 1e-5 of ||M||_F;
+    // a float32 Jacobi cannot push it much lower and would spin to the sweep cap)
+    const int sweeps = sizeof(VT) == 8 ? 40 : 15;
+    const double jtol = sizeof(VT) == 8 ? 1e-15 : 1e-5;
+    if (vs) jacobi_kernel<VT, true><<<1, 1024, jsm, s>>>(sk, w.M, Vj, w.ev, sweeps, jtol);
+    else jacobi_kernel<VT, false><<<1, 1024, jsm, s>>>(sk, w.M, Vj, w.ev, sweeps, jtol);
     NYS_CHECK("jacobi");
     if (sizeof(VT) == 4) {
         eig_rq_kernel<VT><<<sk, 128, 0, s>>>(sk, w.M, Vj, w.ev);

@@ -60,6 +60,11 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
     VT* red = reinterpret_cast<VT*>(empty + nst_cap);  // [2][RB][RP_CWARPS]
 
     if (a.skip != nullptr && *a.skip != 0) return;  // uniform across the block
+    if (a.timer != nullptr && threadIdx.x == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        atomicMin(a.timer, t);
+    }
 
     const int64_t G = gridDim.x;
     const int64_t r0 = (a.m * (int64_t)blockIdx.x) / G;
@@ -265,6 +270,15 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
         }
     }
     if (MODE == RP_GRAD && tid == 0 && a.loss_part != nullptr) a.loss_part[blockIdx.x] = lsum;
+    if (a.timer != nullptr) {
+        __syncwarp();
+        named_bar_sync(1, RP_CTHREADS);
+        if (tid == 0) {
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            atomicMax(a.timer + 1, t);
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------

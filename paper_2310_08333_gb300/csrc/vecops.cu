@@ -242,6 +242,9 @@ __global__ void rhs_init_kernel(int64_t n, const VT* g, const VT* x, const VT* z
             S->cg_max = cg_max;
             S->cg_done = rr_tot > 0.0 ? 0 : 1;
             S->cg_first = 1;
+            S->cg_guard = 0;
+            S->hv_t0 = ~0ull;
+            S->hv_t1 = 0ull;
             S->beta = 0.0;
             if (sk == 0) {
                 S->rz = rr_tot;
@@ -403,6 +406,19 @@ __global__ void convert_kernel(int64_t rows, int64_t cols, const S* src, int64_t
     }
 }
 
+__global__ void cg_cond_kernel(cudaGraphConditionalHandle h, DevState* S, int timed) {
+    if (timed && S->hv_t1 > S->hv_t0) {   // fold the last Hv launch's device time
+        S->hv_ns += (double)(S->hv_t1 - S->hv_t0);
+        S->hv_count += 1;
+    }
+    S->hv_t0 = ~0ull;
+    S->hv_t1 = 0ull;
+    const int guard = ++S->cg_guard;
+    const int cap = S->cg_max < 10000 ? S->cg_max : 10000;   // hard bound on the device loop
+    const bool more = S->cg_done == 0 && guard < cap + 2;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 // ------------------------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------------------------
@@ -517,4 +533,11 @@ cudaError_t convert_copy(int src_dt, int dst_dt, int64_t rows, int64_t cols, con
 
 cudaError_t fill_zero(void* p, size_t bytes, cudaStream_t s) { return cudaMemsetAsync(p, 0, bytes, s); }
 
+}  // namespace genios
+
+namespace genios {
+cudaError_t cg_condition(unsigned long long handle, DevState* S, int timed, cudaStream_t s) {
+    cg_cond_kernel<<<1, 1, 0, s>>>((cudaGraphConditionalHandle)handle, S, timed);
+    return cudaGetLastError();
+}
 }  // namespace genios
