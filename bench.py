@@ -197,7 +197,8 @@ def run_ours(args):
     def solver(p, profile=0):
         return G.Solver(precision=p, stop_rule=G.STOP_KKT, eps_kkt=args.eps_kkt,
                         sketch_rank=P.sketch_rank, rho=rho, max_iter=args.max_iter,
-                        profile=profile, use_graphs=0 if args.no_graphs else 1)
+                        profile=1 if args.no_graphs else profile,
+                        use_graphs=0 if args.no_graphs else 1)
 
     s = solver(prec)
     s.set_data(Ad, bd, P.loss)
@@ -237,7 +238,7 @@ def run_ours(args):
     hv_bytes = infos[0]["hv_bytes"]
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    achieved = hv_bytes / (hv_avg_ms * 1e-3) / 1e9 if hv_n else None
+    achieved = hv_bytes / (hv_avg_ms * 1e-3) / 1e9 if hv_n and hv_ms > 0 else None
     ev_achieved = ev_avg_us = None
     if not args.no_event_leg:
         sp = solver(prec, profile=1)

@@ -241,12 +241,20 @@ genios_status genios_op_zu_update(int precision, int64_t n, const void* x, void*
  *   Omega: n x s value-type row-major (input).  U_out: n x s value-type row-major (output).
  *   lam_out: s doubles (device).  eta_out: device double or NULL.
  *   A, row_scale, d as in genios_op_hv (the sketch streams A in `precision`).
- * workspace: genios_op_nystrom_workspace_bytes(precision, m, n, s). */
+ * workspace: genios_op_nystrom_workspace_bytes(precision, m, n, s).
+ * flags: 0, or a sum of GENIOS_NYS_REUSE_BASIS (the workspace holds the orthonormal basis of this
+ *   same Omega from an earlier call: skip the orthonormalisation) and GENIOS_NYS_WARM (the
+ *   workspace holds the eigenvectors of an earlier successful call with the same Omega and s:
+ *   start the s x s eigensolver from them; meaningful when d has changed little).  The caller
+ *   guarantees the workspace contents; the result is the same approximation either way, up to
+ *   the eigensolver's tolerance. */
+#define GENIOS_NYS_REUSE_BASIS 1
+#define GENIOS_NYS_WARM 2
 size_t genios_op_nystrom_workspace_bytes(int precision, int64_t m, int64_t n, int s);
 genios_status genios_op_nystrom(int precision, int64_t m, int64_t n, int s, const void* A, int64_t lda,
                                 const float* row_scale, const void* d, const void* Omega,
                                 void* U_out, double* lam_out, double* eta_out, void* workspace,
-                                size_t workspace_bytes, void* stream);
+                                size_t workspace_bytes, int flags, void* stream);
 
 /* Nystrom preconditioner, Eq. (10): y = (lam_s + nu) U (Lam + nu I)^{-1} U^T v + v - U U^T v.
  * U: n x s value-type row-major; lam: s doubles (descending, lam_s = lam[s-1]). */

@@ -19,6 +19,7 @@ LOSS_SQUARED, LOSS_LOGISTIC = 0, 1
 FP64, FP32, BF16, FP8_E4M3 = 0, 1, 2, 3
 DT_F64, DT_F32, DT_BF16, DT_U8 = 0, 1, 2, 3
 STOP_RESID, STOP_GAP, STOP_KKT = 1, 2, 4
+NYS_REUSE_BASIS, NYS_WARM = 1, 2   # genios_op_nystrom flags
 
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp8": FP8_E4M3}
 
@@ -82,7 +83,7 @@ SIGNATURES = {
     "genios_op_zu_update": (_i32, [_i32, _i64, _vp, _vp, _vp, _d, _d, _d, _vp, _vp, _sz, _vp]),
     "genios_op_nystrom_workspace_bytes": (_sz, [_i32, _i64, _i64, _i32]),
     "genios_op_nystrom": (_i32, [_i32, _i64, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
-                                 _sz, _vp]),
+                                 _sz, _i32, _vp]),
     "genios_op_precond": (_i32, [_i32, _i64, _i32, _vp, _vp, _d, _vp, _vp, _vp, _sz, _vp]),
     "genios_op_omega": (_i32, [_i32, _i64, _i32, C.c_uint64, _u32, _vp, _vp]),
     "genios_op_philox": (_i32, [_u32, _u32, _u32, _u32, _u32, _u32, _i64, _vp, _vp]),

@@ -98,6 +98,8 @@ struct genios_ctx {
     void* nyswork = nullptr;
     NysWork nw{};
     bool have_precond = false;
+    bool omega_ready = false;   // Om drawn and its orthonormal basis in nw.Oq
+    bool eig_warm = false;      // nw holds the eigenvectors of the last successful core
     int n_sketch_total = 0;
     // device scalars
     DevState* S = nullptr;
@@ -302,6 +304,8 @@ extern "C" genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const
     ctx->has_data = false;
     ctx->solved = false;
     ctx->have_precond = false;
+    ctx->omega_ready = false;
+    ctx->eig_warm = false;
     ctx->loss = loss;
     ctx->m = m[0];
     ctx->n = n[0];
@@ -483,13 +487,24 @@ static genios_status read_state(genios_ctx* ctx) {
 static genios_status build_precond(genios_ctx* ctx, const void* d, double* ms) {
     const double t0 = now_ms();
     cudaStream_t s = ctx->stream;
-    CK(omega_fill(ctx->dbl, ctx->n, ctx->sk, ctx->opt.seed, (uint32_t)ctx->n_sketch_total, ctx->Om, s));
+    // One Gaussian test matrix per data set: re-sketches reuse it (and its orthonormal basis),
+    // and each eigendecomposition starts from the eigenvectors of the previous one.
+    int flags = 0;
+    if (!ctx->omega_ready) {
+        CK(omega_fill(ctx->dbl, ctx->n, ctx->sk, ctx->opt.seed, 0u, ctx->Om, s));
+    } else {
+        flags |= NYS_REUSE_BASIS;
+        if (ctx->eig_warm) flags |= NYS_WARM_EIG;
+    }
     int ok = 0;
     CK(nystrom_build(hv_prec(ctx), ctx->m, ctx->n, ctx->sk, ctx->A_hv, ctx->lda, ctx->A_scale, d,
-                     ctx->Om, ctx->U, ctx->lam, nullptr, ctx->nw, &ok, s));
-    ctx->launches += 12;
+                     ctx->Om, ctx->U, ctx->lam, nullptr, ctx->nw, &ok, flags, s));
+    ctx->launches += (flags & NYS_REUSE_BASIS) ? 14 : 21;
+    ctx->omega_ready = true;
+    ctx->eig_warm = false;
     if (ok == -1) FAIL(GENIOS_ENUMERIC, "Nystrom sketch is not finite (NaN/Inf in A^T D A Omega)");
     if (!ok) FAIL(GENIOS_ENUMERIC, "Nystrom core: Cholesky failed after raising the shift");
+    ctx->eig_warm = ok == 1;
     ctx->have_precond = true;
     ctx->n_sketch_total++;
     CK(cudaStreamSynchronize(s));
@@ -1007,6 +1022,9 @@ extern "C" genios_status genios_op_zu_update(int precision, int64_t n, const voi
                             nullptr, norms_out, w.sc, s));
 }
 
+static_assert(genios::NYS_REUSE_BASIS == GENIOS_NYS_REUSE_BASIS && genios::NYS_WARM_EIG == GENIOS_NYS_WARM,
+              "Nystrom flag values");
+
 extern "C" size_t genios_op_nystrom_workspace_bytes(int precision, int64_t m, int64_t n, int s) {
     if (!prec_valid(precision) || m < 1 || n < 1 || s < 1 || s > 128) return 0;
     return nystrom_work_bytes(hvp_of(precision), m, n, s) + 1024;
@@ -1016,9 +1034,9 @@ extern "C" genios_status genios_op_nystrom(int precision, int64_t m, int64_t n, 
                                            int64_t lda, const float* row_scale, const void* d,
                                            const void* Omega, void* U_out, double* lam_out,
                                            double* eta_out, void* workspace, size_t workspace_bytes,
-                                           void* stream) {
+                                           int flags, void* stream) {
     if (!prec_valid(precision) || m < 1 || n < 1 || s < 1 || s > 128 || s > n || !A || !Omega ||
-        !U_out || !lam_out)
+        !U_out || !lam_out || (flags & ~(GENIOS_NYS_REUSE_BASIS | GENIOS_NYS_WARM)) != 0)
         return GENIOS_EINVAL;
     if (!workspace || workspace_bytes < genios_op_nystrom_workspace_bytes(precision, m, n, s))
         return GENIOS_EINVAL;
@@ -1027,9 +1045,9 @@ extern "C" genios_status genios_op_nystrom(int precision, int64_t m, int64_t n, 
     NysWork w = nystrom_carve(workspace, P, m, n, s);
     int ok = 0;
     cudaError_t e = nystrom_build(P, m, n, s, A, lda, row_scale, d, Omega, U_out, lam_out, eta_out, w,
-                                  &ok, st);
+                                  &ok, flags, st);
     if (e != cudaSuccess) return op_err(e);
-    return ok == 1 ? GENIOS_OK : GENIOS_ENUMERIC;
+    return ok >= 1 ? GENIOS_OK : GENIOS_ENUMERIC;
 }
 
 extern "C" genios_status genios_op_precond(int precision, int64_t n, int s, const void* U, const double* lam,

@@ -174,9 +174,16 @@ struct NysWork {
 size_t nystrom_work_bytes(int prec, int64_t m, int64_t n, int sk);
 NysWork nystrom_carve(void* base, int prec, int64_t m, int64_t n, int sk);
 // Builds U (n x s) and lam (s, descending) for H = A^T diag(d) A; returns cudaSuccess and
-// *chol_ok = 1 on success (the shift is raised up to 6 times if the Cholesky fails).
+// *chol_ok = 1 on success (the shift is raised up to 6 times if the Cholesky fails), 2 when the
+// sketch is exactly zero (U = the orthonormal test matrix, lam = 0), 0 when the Cholesky failed
+// and -1 when the sketch is not finite.
+// flags: NYS_REUSE_BASIS = w.Oq already holds the orthonormal basis of this Om (an earlier build
+// on the same workspace); NYS_WARM_EIG = the eigenvectors of that earlier build, still in the
+// workspace, start the Jacobi iteration.
+enum { NYS_REUSE_BASIS = 1, NYS_WARM_EIG = 2 };   // = GENIOS_NYS_REUSE_BASIS, GENIOS_NYS_WARM
 cudaError_t nystrom_build(int prec, int64_t m, int64_t n, int sk, const void* A, int64_t lda,
                           const float* row_scale, const void* d, const void* Om, void* U,
-                          double* lam, double* eta_out, NysWork w, int* chol_ok, cudaStream_t s);
+                          double* lam, double* eta_out, NysWork w, int* chol_ok, int flags,
+                          cudaStream_t s);
 
 }  // namespace genios

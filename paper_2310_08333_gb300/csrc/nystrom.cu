@@ -399,42 +399,53 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int sk, const double* G,
 // Cyclic Jacobi eigendecomposition of the symmetric s x s matrix M (one CTA), arithmetic in T.
 // Round-robin ("circle") ordering: in round r of a sweep over se = s + (s odd) indices, index
 // se - 1 meets r and, for k = 1 .. se/2 - 1, (r + k) mod (se - 1) meets (r - k) mod (se - 1);
-// the se/2 disjoint rotations of a round run in parallel (Golub & Van Loan §8.5).  A rotation
-// whose off-diagonal entry is negligible is skipped.  M, and V when VS, live in shared memory.
-// Out: Vout (s x s, global, columns = eigenvectors), ev (s eigenvalues, unsorted).
+// the se/2 disjoint rotations of a round run in parallel (Golub & Van Loan §8.5).  A pair is
+// rotated while |m_pq| > rot_tol sqrt(|m_pp m_qq|) (the relative test of Demmel & Veselic).  The
+// iteration stops after a sweep in which no pair exceeded conv_tol = sqrt(rot_tol) at its turn:
+// Jacobi converges quadratically, so that sweep already brought every pair to the rot_tol level
+// (rotations at the arithmetic's noise never stop on their own).  V starts from Vinit (a warm start
+// from a nearby problem, Min then being Vinit^T M Vinit) and from I otherwise, and accumulates
+// the rotations.  Rows of M and V are stored with an odd stride so that the column updates
+// are free of bank conflicts.  Out: Vout (s x s, columns = eigenvectors), ev (unsorted).
+constexpr int JAC_MAX_PER_THREAD = 8;   // ceil((s/2) * s / 1024) for s <= 128
 template <typename T, bool VS>
-__global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min, T* Vout, double* ev,
-                                                     int max_sweeps, double rel_tol) {
+__global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min, const T* Vinit, T* Vout,
+                                                     double* ev, int max_sweeps, double rot_tol,
+                                                     int* sweeps_out) {
     extern __shared__ __align__(16) unsigned char jsm[];
     const int se = sk + (sk & 1);
     const int half = se / 2;
-    T* M = reinterpret_cast<T*>(jsm);                   // s x s
-    T* Vs_ = M + sk * sk;                               // s x s (VS only)
-    T* cs = VS ? Vs_ + sk * sk : Vs_;                   // half
+    const int ld = sk | 1;
+    T* M = reinterpret_cast<T*>(jsm);                   // s x ld
+    T* Vs_ = M + sk * ld;                               // s x ld (VS only)
+    T* cs = VS ? Vs_ + sk * ld : Vs_;                   // half
     T* sn = cs + half;                                  // half
     int* pp = reinterpret_cast<int*>(sn + half);        // half
     int* qq = pp + half;                                // half
+    const int vld = VS ? ld : sk;
     T* V = VS ? Vs_ : Vout;
-    __shared__ int done;
+    __shared__ int nrot;
     for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) {
         const int i = e / sk, j = e % sk;
-        M[e] = (T)(0.5 * (Min[i * sk + j] + Min[j * sk + i]));
-        V[e] = (i == j) ? T(1) : T(0);
+        M[i * ld + j] = (T)(0.5 * (Min[i * sk + j] + Min[j * sk + i]));
+        V[i * vld + j] = Vinit ? Vinit[e] : ((i == j) ? T(1) : T(0));
     }
+    // this thread's (pair, index) work items, fixed for the whole iteration
+    int wk[JAC_MAX_PER_THREAD], wj[JAC_MAX_PER_THREAD];
+    int nw = 0;
+#pragma unroll
+    for (int r = 0; r < JAC_MAX_PER_THREAD; ++r) {
+        const int e = threadIdx.x + r * blockDim.x;
+        wk[r] = 0; wj[r] = 0;
+        if (e < half * sk) { wk[r] = e / sk; wj[r] = e % sk; nw = r + 1; }
+    }
+    const T tol = (T)rot_tol;
+    const T ctol = (T)sqrt(rot_tol);
+    int sweep = 0;
     __syncthreads();
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) {
-            const double v = (double)M[e] * (double)M[e];
-            tot += v;
-            if (e / sk != e % sk) off += v;
-        }
-        double a2[2] = {off, tot};
-        block_sum<2>(a2);
-        if (threadIdx.x == 0) done = (a2[0] <= rel_tol * rel_tol * a2[1]) ? 1 : 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) nrot = 0;
         __syncthreads();
-        if (done) break;
-        const double thr = 1e-2 * rel_tol * sqrt(a2[1]) / (double)sk;
         for (int round = 0; round < se - 1; ++round) {
             for (int k = threadIdx.x; k < half; k += blockDim.x) {
                 int p, q;
@@ -443,9 +454,11 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min,
                 if (p > q) { int t = p; p = q; q = t; }
                 T c = T(1), s = T(0);
                 if (q < sk) {
-                    const T apq = M[p * sk + q];
-                    if (fabs((double)apq) > thr) {
-                        const T app = M[p * sk + p], aqq = M[q * sk + q];
+                    const T apq = M[p * ld + q];
+                    const T app = M[p * ld + p], aqq = M[q * ld + q];
+                    const T scale = sqrt(fabs(app * aqq));
+                    if (apq != T(0) && fabs(apq) > tol * scale) {
+                        if (fabs(apq) > ctol * scale) nrot = 1;   // benign race: writers store 1
                         const T tau = (aqq - app) / (T(2) * apq);
                         const T t = tau >= T(0) ? T(1) / (tau + sqrt(T(1) + tau * tau))
                                                 : T(-1) / (-tau + sqrt(T(1) + tau * tau));
@@ -456,36 +469,82 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min,
                 cs[k] = c; sn[k] = s; pp[k] = p; qq[k] = q;
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < half * sk; e += blockDim.x) {   // rows: M <- J^T M
-                const int k = e / sk, j = e % sk;
+#pragma unroll
+            for (int r = 0; r < JAC_MAX_PER_THREAD; ++r) {            // rows: M <- J^T M
+                if (r >= nw) break;
+                const int k = wk[r], j = wj[r];
                 const T sv = sn[k];
                 if (sv == T(0)) continue;
                 const int p = pp[k], q = qq[k];
                 const T cv = cs[k];
-                const T mp = M[p * sk + j], mq = M[q * sk + j];
-                M[p * sk + j] = cv * mp - sv * mq;
-                M[q * sk + j] = sv * mp + cv * mq;
+                const T mp = M[p * ld + j], mq = M[q * ld + j];
+                M[p * ld + j] = cv * mp - sv * mq;
+                M[q * ld + j] = sv * mp + cv * mq;
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < half * sk; e += blockDim.x) {   // cols: M <- M J, V <- V J
-                const int k = e / sk, i = e % sk;
+#pragma unroll
+            for (int r = 0; r < JAC_MAX_PER_THREAD; ++r) {            // cols: M <- M J, V <- V J
+                if (r >= nw) break;
+                const int k = wk[r], i = wj[r];
                 const T sv = sn[k];
                 if (sv == T(0)) continue;
                 const int p = pp[k], q = qq[k];
                 const T cv = cs[k];
-                const T mp = M[i * sk + p], mq = M[i * sk + q];
-                M[i * sk + p] = cv * mp - sv * mq;
-                M[i * sk + q] = sv * mp + cv * mq;
-                const T vp = V[i * sk + p], vq = V[i * sk + q];
-                V[i * sk + p] = cv * vp - sv * vq;
-                V[i * sk + q] = sv * vp + cv * vq;
+                const T mp = M[i * ld + p], mq = M[i * ld + q];
+                M[i * ld + p] = cv * mp - sv * mq;
+                M[i * ld + q] = sv * mp + cv * mq;
+                const T vp = V[i * vld + p], vq = V[i * vld + q];
+                V[i * vld + p] = cv * vp - sv * vq;
+                V[i * vld + q] = sv * vp + cv * vq;
             }
             __syncthreads();
         }
+        const int any = nrot;
+        __syncthreads();   // every thread has read nrot before thread 0 resets it
+        if (any == 0) { ++sweep; break; }
     }
-    for (int e = threadIdx.x; e < sk; e += blockDim.x) ev[e] = (double)M[e * sk + e];
+    if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
+    for (int e = threadIdx.x; e < sk; e += blockDim.x) ev[e] = (double)M[e * ld + e];
     if (VS)
-        for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) Vout[e] = V[e];
+        for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) Vout[e] = V[(e / sk) * vld + e % sk];
+}
+
+// Warm start of the Jacobi iteration: Mout = V0^T M V0 for the s x s symmetric M and the
+// eigenvector matrix V0 of a nearby matrix, in two passes (T1 = M V0, then V0^T T1).  One block
+// per output row, value-type arithmetic.
+template <typename T>
+__global__ void congruence_kernel(int sk, int pass, const double* M, const T* V0, T* T1, double* Mout) {
+    const int i = blockIdx.x;
+    for (int c = threadIdx.x; c < sk; c += blockDim.x) {
+        T acc = T(0);
+        if (pass == 0) {
+            for (int k = 0; k < sk; ++k) acc += (T)M[i * sk + k] * V0[k * sk + c];
+            T1[i * sk + c] = acc;
+        } else {
+            for (int k = 0; k < sk; ++k) acc += V0[k * sk + i] * T1[k * sk + c];
+            Mout[i * sk + c] = (double)acc;
+        }
+    }
+}
+
+// One Newton-Schulz step towards the nearest orthogonal matrix, V <- V (3I - V^T V) / 2, which
+// squares the orthogonality error of a V that is orthogonal up to rounding (the Jacobi rotations
+// are applied in the value type, and warm starts would otherwise let that error accumulate from
+// one sketch to the next).  pass 0: G = V^T V (float64 sums); pass 1: Vout = V (1.5 I - 0.5 G).
+// One block per output row.
+template <typename T>
+__global__ void polar_step_kernel(int sk, int pass, const T* V, double* G, T* Vout) {
+    const int i = blockIdx.x;
+    for (int c = threadIdx.x; c < sk; c += blockDim.x) {
+        double acc = 0.0;
+        if (pass == 0) {
+            for (int k = 0; k < sk; ++k) acc += (double)V[k * sk + i] * (double)V[k * sk + c];
+            G[i * sk + c] = acc;
+        } else {
+            for (int k = 0; k < sk; ++k) acc += (double)V[i * sk + k] * G[k * sk + c];
+            Vout[i * sk + c] = (T)(1.5 * (double)V[i * sk + c] - 0.5 * acc);
+        }
+    }
 }
 
 // Float64 Rayleigh quotients ev_c = v_c^T M v_c / v_c^T v_c of the Jacobi eigenvectors against
@@ -514,14 +573,17 @@ __global__ void eig_finish_kernel(int sk, const T* V, const double* ev, const do
                                   VT* Vs, double* lam) {
     __shared__ int perm[256];
     __shared__ double sig[256];
-    if (threadIdx.x == 0) {
-        for (int c = 0; c < sk; ++c) perm[c] = c;
-        for (int a = 0; a < sk; ++a) {  // selection sort, descending
-            int best = a;
-            for (int b = a + 1; b < sk; ++b)
-                if (ev[perm[b]] > ev[perm[best]]) best = b;
-            const int t = perm[a]; perm[a] = perm[best]; perm[best] = t;
-        }
+    __shared__ double key[256];
+    for (int c = threadIdx.x; c < sk; c += blockDim.x) {
+        const double e = ev[c];
+        key[c] = e == e ? e : -INFINITY;   // NaN sorts last
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < sk; c += blockDim.x) {   // rank sort, descending, stable
+        const double kc = key[c];
+        int rank = 0;
+        for (int b = 0; b < sk; ++b) rank += (key[b] > kc || (key[b] == kc && b < c)) ? 1 : 0;
+        perm[rank] = c;
     }
     __syncthreads();
     const double e0 = fmax(ev[perm[0]], 0.0);
@@ -648,7 +710,7 @@ static cudaError_t orthonormalize(int64_t n, int sk, const VT* Om, NysWork w, cu
 
 template <typename VT>
 static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U, double* lam,
-                        double* eta_out, int* chol_ok, cudaStream_t s) {
+                        double* eta_out, int* chol_ok, bool warm, cudaStream_t s) {
     const int64_t total = n * sk;
     const double eps = sizeof(VT) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
     double* fro2 = w.scal;
@@ -673,7 +735,7 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
             cudaMemcpyAsync(U, Om, (size_t)total * sizeof(VT), cudaMemcpyDeviceToDevice, s);
             cudaMemsetAsync(lam, 0, (size_t)sk * sizeof(double), s);
             if (eta_out) cudaMemsetAsync(eta_out, 0, sizeof(double), s);
-            *chol_ok = 1;
+            *chol_ok = 2;   // success without eigenvectors (nothing to warm-start from)
             return cudaGetLastError();
         }
     }
@@ -683,8 +745,9 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
     const size_t tsm = (size_t)(sk * sk + 16 * sk) * sizeof(VT);
     const size_t csm = (size_t)ss * 8 + (size_t)sk * 8;
     const int se = sk + (sk & 1);
-    const bool vs = 2 * (size_t)ss * sizeof(VT) + (size_t)se * (sizeof(VT) + 4) <= 200 * 1024;
-    const size_t jsm = (vs ? 2 : 1) * (size_t)ss * sizeof(VT) + (size_t)se * (sizeof(VT) + 4) + 64;
+    const size_t sld = (size_t)sk * (size_t)(sk | 1);
+    const bool vs = 2 * sld * sizeof(VT) + (size_t)se * (sizeof(VT) + 4) <= 200 * 1024;
+    const size_t jsm = (vs ? 2 : 1) * sld * sizeof(VT) + (size_t)se * (sizeof(VT) + 4) + 64;
     cudaFuncSetAttribute(ts_gemm<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm + 1024);
     cudaFuncSetAttribute(chol_inv_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm + 1024);
     cudaFuncSetAttribute(jacobi_kernel<VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm + 1024);
@@ -725,13 +788,30 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
     // Jacobi in the value type (a float64 Jacobi at s = 100 costs ~25 ms on this part's float64
     // pipe); in float32 the eigenvalues are then refined by float64 Rayleigh quotients
     VT* Vj = reinterpret_cast<VT*>(V);
-    // stop when the off-diagonal part is below the arithmetic's noise (float32: 1e-5 of ||M||_F;
-    // a float32 Jacobi cannot push it much lower and would spin to the sweep cap)
-    const int sweeps = sizeof(VT) == 8 ? 40 : 15;
-    const double jtol = sizeof(VT) == 8 ? 1e-15 : 1e-5;
-    if (vs) jacobi_kernel<VT, true><<<1, 1024, jsm, s>>>(sk, w.M, Vj, w.ev, sweeps, jtol);
-    else jacobi_kernel<VT, false><<<1, 1024, jsm, s>>>(sk, w.M, Vj, w.ev, sweeps, jtol);
+    // relative pair tolerance near the arithmetic's resolution; a warm start (V of the previous
+    // sketch of the same test matrix, which the slowly varying D leaves nearly diagonalising)
+    // needs a few sweeps where a cold start needs about ten
+    const int sweeps = sizeof(VT) == 8 ? 30 : 20;
+    const double jtol = sizeof(VT) == 8 ? 1e-15 : 1e-7;
+    const double* Mj = w.M;
+    const VT* Vinit = nullptr;
+    if (warm) {
+        // Vj holds the previous eigenvectors; Cinv is free between ts_gemm(B) and eig_finish
+        VT* T1 = Cinv;
+        congruence_kernel<VT><<<sk, 128, 0, s>>>(sk, 0, w.M, Vj, T1, nullptr);
+        congruence_kernel<VT><<<sk, 128, 0, s>>>(sk, 1, w.M, Vj, T1, w.G);
+        NYS_CHECK("congruence");
+        Mj = w.G;
+        Vinit = Vj;
+    }
+    int* jsweeps = w.status + 1;
+    if (vs) jacobi_kernel<VT, true><<<1, 1024, jsm, s>>>(sk, Mj, Vinit, Vj, w.ev, sweeps, jtol, jsweeps);
+    else jacobi_kernel<VT, false><<<1, 1024, jsm, s>>>(sk, Mj, Vinit, Vj, w.ev, sweeps, jtol, jsweeps);
     NYS_CHECK("jacobi");
+    polar_step_kernel<VT><<<sk, 128, 0, s>>>(sk, 0, Vj, w.G, nullptr);
+    polar_step_kernel<VT><<<sk, 128, 0, s>>>(sk, 1, Vj, w.G, Cinv);
+    cudaMemcpyAsync(Vj, Cinv, (size_t)ss * sizeof(VT), cudaMemcpyDeviceToDevice, s);
+    NYS_CHECK("polar");
     if (sizeof(VT) == 4) {
         eig_rq_kernel<VT><<<sk, 128, 0, s>>>(sk, w.M, Vj, w.ev);
         NYS_CHECK("eig_rq");
@@ -747,20 +827,26 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
 
 cudaError_t nystrom_build(int prec, int64_t m, int64_t n, int sk, const void* A, int64_t lda,
                           const float* rs, const void* d, const void* Om, void* U, double* lam,
-                          double* eta_out, NysWork w, int* chol_ok, cudaStream_t s) {
+                          double* eta_out, NysWork w, int* chol_ok, int flags, cudaStream_t s) {
     if (sk < 1 || sk > 128) return cudaErrorInvalidValue;
+    const bool reuse = (flags & NYS_REUSE_BASIS) != 0;
+    const bool warm = (flags & NYS_WARM_EIG) != 0;
     if (prec == P_FP64) {
-        cudaError_t e = orthonormalize<double>(n, sk, static_cast<const double*>(Om), w, s);
-        if (e != cudaSuccess) return e;
+        if (!reuse) {
+            cudaError_t e = orthonormalize<double>(n, sk, static_cast<const double*>(Om), w, s);
+            if (e != cudaSuccess) return e;
+        }
         const double* Oq = static_cast<const double*>(w.Oq);
         launch_sketch<P_FP64, double>(m, n, sk, A, lda, rs, static_cast<const double*>(d), Oq,
                                       static_cast<double*>(w.W), static_cast<double*>(w.Y), s);
         return core<double>(n, sk, Oq, static_cast<double*>(w.Y), w, static_cast<double*>(U), lam,
-                            eta_out, chol_ok, s);
+                            eta_out, chol_ok, warm, s);
     }
     const float* df = static_cast<const float*>(d);
-    cudaError_t e = orthonormalize<float>(n, sk, static_cast<const float*>(Om), w, s);
-    if (e != cudaSuccess) return e;
+    if (!reuse) {
+        cudaError_t e = orthonormalize<float>(n, sk, static_cast<const float*>(Om), w, s);
+        if (e != cudaSuccess) return e;
+    }
     const float* Of = static_cast<const float*>(w.Oq);
     float* Wf = static_cast<float*>(w.W);
     float* Yf = static_cast<float*>(w.Y);
@@ -768,7 +854,7 @@ cudaError_t nystrom_build(int prec, int64_t m, int64_t n, int sk, const void* A,
     else if (prec == P_BF16) launch_sketch<P_BF16, float>(m, n, sk, A, lda, rs, df, Of, Wf, Yf, s);
     else if (prec == P_FP8) launch_sketch<P_FP8, float>(m, n, sk, A, lda, rs, df, Of, Wf, Yf, s);
     else return cudaErrorInvalidValue;
-    return core<float>(n, sk, Of, Yf, w, static_cast<float*>(U), lam, eta_out, chol_ok, s);
+    return core<float>(n, sk, Of, Yf, w, static_cast<float*>(U), lam, eta_out, chol_ok, warm, s);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -182,16 +182,22 @@ def zu_update(prec, x, z, u, rho, lam1, alpha):
     return norms
 
 
-def nystrom(prec, A, n, s, d, Omega, row_scale=None):
+def nystrom_workspace(prec, m, n, s):
+    nb = int(L.lib().genios_op_nystrom_workspace_bytes(prec, m, n, s))
+    return torch.empty(nb, dtype=torch.uint8, device="cuda")
+
+
+def nystrom(prec, A, n, s, d, Omega, row_scale=None, workspace=None, flags=0):
+    """``workspace`` (from ``nystrom_workspace``) may be passed back in with ``flags`` =
+    L.NYS_REUSE_BASIS | L.NYS_WARM to reuse the basis / eigenvectors of the previous call."""
     m = A.shape[0]
     U = torch.empty((n, s), dtype=_vt(prec), device="cuda")
     lam = torch.empty(s, dtype=torch.float64, device="cuda")
     eta = torch.empty(1, dtype=torch.float64, device="cuda")
-    nb = int(L.lib().genios_op_nystrom_workspace_bytes(prec, m, n, s))
-    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    ws = nystrom_workspace(prec, m, n, s) if workspace is None else workspace
     _chk(L.lib().genios_op_nystrom(prec, m, n, s, _ptr(A), A.shape[1], _ptr(row_scale), _ptr(d),
-                                   _ptr(Omega), _ptr(U), _ptr(lam), _ptr(eta), _ptr(ws), nb,
-                                   _stream_ptr()))
+                                   _ptr(Omega), _ptr(U), _ptr(lam), _ptr(eta), _ptr(ws), ws.numel(),
+                                   int(flags), _stream_ptr()))
     return U, lam, eta
 
 
@@ -247,4 +253,5 @@ def pcg(prec, A, n, d, nu, r, U=None, lam=None, rtol=1e-6, max_iter=100, row_sca
 
 
 ops = SimpleNamespace(lda=lda, pad=pad, hv=hv, hv_noalloc=hv_noalloc, gradient=gradient, zu_update=zu_update, nystrom=nystrom,
+                      nystrom_workspace=nystrom_workspace,
                       precond=precond, omega=omega, philox=philox, quantize=quantize, pcg=pcg)

@@ -235,6 +235,60 @@ def test_nystrom_matches_oracle(G, prec, shape):
     rel_close(Ahat, Aref, tol)
     np.testing.assert_allclose(U[:, top].T @ U[:, top], np.eye(int(top.sum())), atol=10 * tol)
     assert abs(eta.item() - er) <= 1e-6 * er
+    # Eq. (10) weights the direction of u_c by (lam_s + nu) / (lam_c + nu): the top columns must
+    # be orthonormal to well below lam_s / lam_1 for the operator to stay positive definite
+    # (columns with lam_c near lam_s have weight ~1 and tolerate the float32 error of B / sigma_c)
+    assert np.abs(U[:, top].T @ U[:, top] - np.eye(int(top.sum()))).max() <= (1e-10 if prec == 0 else 2e-5)
+    assert _precond_min_eig(U, lam, 1e-4 * lam[0]) > 0.0
+
+
+def _precond_min_eig(U, lam, nu):
+    """Smallest eigenvalue of the dense Eq. (10) operator built from U, lam (float64)."""
+    n = U.shape[0]
+    P = (lam[-1] + nu) * (U / (lam + nu)) @ U.T + np.eye(n) - U @ U.T
+    return np.linalg.eigvalsh(0.5 * (P + P.T))[0]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_nystrom_warm_start_and_basis_reuse_match_cold(G, prec):
+    """A re-sketch with a slightly changed D that reuses the orthonormal basis and starts the
+    eigensolver from the previous eigenvectors gives the cold result, an orthonormal U, and a
+    positive definite Eq. (10) preconditioner even for a small nu (where a U that is not
+    orthonormal to about lam_s / lam_1 makes the operator indefinite)."""
+    from paper_2310_08333_gb300 import _lib as L
+    rng = np.random.default_rng(14)
+    m, n, s = 3000, 1500, 100
+    A = rng.standard_normal((m, 20)) @ rng.standard_normal((20, n)) / 5 + 0.05 * rng.standard_normal((m, n))
+    d1 = rng.uniform(0.1, 0.25, m)
+    d2 = d1 * (1.0 + 0.1 * rng.uniform(-1.0, 1.0, m))
+    vt = torch.float64 if prec == 0 else torch.float32
+    Ad, _, sc = _matrices(prec, A)
+    Om = G.ops.omega(prec, n, s, seed=7)
+    ws = G.ops.nystrom_workspace(prec, m, n, s)
+    G.ops.nystrom(prec, Ad, n, s, dev(d1, vt), Om, row_scale=sc, workspace=ws)
+    Uw, lw, ew = G.ops.nystrom(prec, Ad, n, s, dev(d2, vt), Om, row_scale=sc, workspace=ws,
+                               flags=L.NYS_REUSE_BASIS | L.NYS_WARM)
+    Uc, lc, ec = G.ops.nystrom(prec, Ad, n, s, dev(d2, vt), Om, row_scale=sc)
+    Uw, Uc = Uw.double().cpu().numpy(), Uc.double().cpu().numpy()
+    lw, lc = lw.cpu().numpy(), lc.cpu().numpy()
+    tol = 1e-9 if prec == 0 else 2e-3
+    top = lc > 1e-3 * lc[0]
+    np.testing.assert_allclose(lw[top], lc[top], rtol=tol)
+    rel_close((Uw[:, top] * lw[top]) @ Uw[:, top].T, (Uc[:, top] * lc[top]) @ Uc[:, top].T, tol)
+    assert abs(ew.item() - ec.item()) <= 1e-6 * ec.item()
+    orth_tol = 1e-10 if prec == 0 else 2e-5
+    for U, lam in ((Uw, lw), (Uc, lc)):
+        assert np.abs(U[:, top].T @ U[:, top] - np.eye(int(top.sum()))).max() <= orth_tol
+        assert _precond_min_eig(U, lam, 1e-4 * lam[0]) > 0.0
+    # repeated warm starts do not let the eigenvectors drift from orthogonality
+    for k in range(8):
+        dk = d1 * (1.0 + 0.1 * rng.uniform(-1.0, 1.0, m))
+        Uk, lk, _ = G.ops.nystrom(prec, Ad, n, s, dev(dk, vt), Om, row_scale=sc, workspace=ws,
+                                  flags=L.NYS_REUSE_BASIS | L.NYS_WARM)
+    Uk, lk = Uk.double().cpu().numpy(), lk.cpu().numpy()
+    topk = lk > 1e-3 * lk[0]
+    assert np.abs(Uk[:, topk].T @ Uk[:, topk] - np.eye(int(topk.sum()))).max() <= orth_tol
+    assert _precond_min_eig(Uk, lk, 1e-4 * lk[0]) > 0.0
 
 
 @pytest.mark.parametrize("prec", [0, 1])

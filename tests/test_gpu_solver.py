@@ -225,3 +225,6 @@ def test_config3_full_size_kkt_property(G):
     S = checks.support(z)
     g = checks.grad_f(A, P.b, z, "logistic")
     assert np.max(np.abs(np.delete(g, S))) <= lam * (1 + 1e-3)
+    # the rank-100 Nystrom preconditioner keeps the CG solves short (about 7 iterations per
+    # x-update here); a broken preconditioner runs into the 50-iteration cap instead
+    assert info["cg_iters_total"] <= 12 * info["iters"], (info["cg_iters_total"], info["iters"])
