@@ -113,6 +113,9 @@ typedef struct genios_options {
     int64_t device_wait_limit_us; /* bound on any device-side wait (default 2e6 us) */
     int32_t verbose;         /* 0 silent; N > 0: log every N-th iteration to stderr */
     int32_t profile;         /* 1: time the rowpass kernels with CUDA events (info.hv_ms...) */
+    int32_t tensor_sketch;   /* 1 (default): float value types sketch A^T D A Omega on the tensor
+                                cores (bf16 operands, genios_op_sketch); 0: CUDA-core sketch in
+                                the streaming precision */
 } genios_options;
 
 typedef struct genios_info {
@@ -255,6 +258,22 @@ genios_status genios_op_nystrom(int precision, int64_t m, int64_t n, int s, cons
                                 const float* row_scale, const void* d, const void* Omega,
                                 void* U_out, double* lam_out, double* eta_out, void* workspace,
                                 size_t workspace_bytes, int flags, void* stream);
+
+/* Sketch Y = A^T diag(d) A Omega (§2.2 with the sketch target of §3.3) on the tensor cores, the
+ * product the solver uses for float value types: A (stored in `precision`, FP32 / BF16 / FP8 with
+ * row_scale, m x n, row stride lda >= n) and Omega are rounded to bfloat16, W = A Omega is
+ * accumulated in float32, D W is split into bfloat16 hi + lo and Y = A^T (D W) is accumulated in
+ * float32 (tcgen05.mma, accumulators in tensor memory).
+ *   d: m floats (device) or NULL for the identity.
+ *   Omega: n x s float32 row-major (device); OVERWRITTEN with its bfloat16-rounded values, i.e.
+ *     the test matrix actually multiplied.  Y_out: n x s float32 row-major (device).
+ *   s <= 128.  FP64 is not supported (EINVAL): its sketch stays on the CUDA cores.
+ *   workspace: genios_op_sketch_workspace_bytes(precision, m, n, s) device bytes.
+ * Returns GENIOS_ETIMEOUT if a bounded device wait ran out (the output is then invalid). */
+size_t genios_op_sketch_workspace_bytes(int precision, int64_t m, int64_t n, int s);
+genios_status genios_op_sketch(int precision, int64_t m, int64_t n, int s, const void* A, int64_t lda,
+                               const float* row_scale, const float* d, float* Omega, float* Y_out,
+                               void* workspace, size_t workspace_bytes, void* stream);
 
 /* Nystrom preconditioner, Eq. (10): y = (lam_s + nu) U (Lam + nu I)^{-1} U^T v + v - U U^T v.
  * U: n x s value-type row-major; lam: s doubles (descending, lam_s = lam[s-1]). */

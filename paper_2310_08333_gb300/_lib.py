@@ -37,7 +37,7 @@ class Options(C.Structure):
         ("max_iter", C.c_int32), ("max_cg_iter", C.c_int32), ("stop_rule", C.c_int32),
         ("precision", C.c_int32), ("kkt_check_every", C.c_int32), ("use_graphs", C.c_int32),
         ("seed", C.c_uint64), ("device_wait_limit_us", C.c_int64),
-        ("verbose", C.c_int32), ("profile", C.c_int32),
+        ("verbose", C.c_int32), ("profile", C.c_int32), ("tensor_sketch", C.c_int32),
     ]
 
 
@@ -84,6 +84,8 @@ SIGNATURES = {
     "genios_op_nystrom_workspace_bytes": (_sz, [_i32, _i64, _i64, _i32]),
     "genios_op_nystrom": (_i32, [_i32, _i64, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                  _sz, _i32, _vp]),
+    "genios_op_sketch_workspace_bytes": (_sz, [_i32, _i64, _i64, _i32]),
+    "genios_op_sketch": (_i32, [_i32, _i64, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "genios_op_precond": (_i32, [_i32, _i64, _i32, _vp, _vp, _d, _vp, _vp, _vp, _sz, _vp]),
     "genios_op_omega": (_i32, [_i32, _i64, _i32, C.c_uint64, _u32, _vp, _vp]),
     "genios_op_philox": (_i32, [_u32, _u32, _u32, _u32, _u32, _u32, _i64, _vp, _vp]),

@@ -96,6 +96,9 @@ struct genios_ctx {
     void* U = nullptr;
     double* lam = nullptr;
     void* nyswork = nullptr;
+    void* tcbuf = nullptr;      // tensor-core sketch operands (value type float only)
+    TcSketch tc{};
+    bool use_tc = false;
     NysWork nw{};
     bool have_precond = false;
     bool omega_ready = false;   // Om drawn and its orthonormal basis in nw.Oq
@@ -168,6 +171,7 @@ extern "C" void genios_default_options(genios_options* o) {
     o->device_wait_limit_us = 2000000;
     o->verbose = 0;
     o->profile = 0;
+    o->tensor_sketch = 1;
 }
 
 extern "C" genios_status genios_create(const genios_options* opts, int device, void* stream,
@@ -281,6 +285,28 @@ static genios_status load_matrix_f32(genios_ctx* ctx, const void* A, int dt, int
     return GENIOS_OK;
 }
 
+// Tensor-core sketch operands: the blocked bf16 copies of A and A^T, packed once per data set
+// from the float32 (or stored) matrix.  Only for float value types with a sketch.
+static cudaError_t tc_setup(genios_ctx* ctx, int src_prec, const void* A, int64_t lda,
+                            const float* row_scale, int64_t M, int64_t N) {
+    ctx->use_tc = false;
+    int sk = ctx->opt.sketch_rank;
+    if (sk < 0) sk = (int)std::min<int64_t>(50, N / 20);
+    sk = (int)std::min<int64_t>(sk, N);
+    if (sk < 1 || ctx->prec == GENIOS_FP64 || !ctx->opt.tensor_sketch) return cudaSuccess;
+    TcPlan p = tc_plan(M, N, sk);
+    if (!p.ok) return cudaSuccess;
+    cudaError_t e = ctx->mem.get(&ctx->tcbuf, tc_bytes(p));
+    if (e != cudaSuccess) return e;
+    ctx->tc.plan = p;
+    ctx->tc.work = tc_carve(ctx->tcbuf, p);
+    ctx->tc.wait_limit = (long long)ctx->opt.device_wait_limit_us * 2100LL;
+    e = tc_pack_a(p, ctx->tc.work, src_prec, A, lda, row_scale, ctx->stream);
+    if (e != cudaSuccess) return e;
+    ctx->use_tc = true;
+    return cudaSuccess;
+}
+
 extern "C" genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const int64_t* m,
                                          const int64_t* n, const void* const* A, int A_dtype,
                                          const int64_t* lda, const void* const* b, int shared_A) {
@@ -342,6 +368,7 @@ extern "C" genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const
             ctx->lda = ld32;
             ctx->A_g = A32;
             ctx->lda_g = ld32;
+            CK(tc_setup(ctx, P_FP32, A32, ld32, nullptr, M, N));
         } else {
             ctx->lda_g = padded_lda(P_BF16, N);
             CK(ctx->mem.get(&ctx->A_g, (size_t)M * ctx->lda_g * 2));
@@ -357,6 +384,7 @@ extern "C" genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const
                 CK(quantize_fp8_rows(M, N, A32, ld32, static_cast<uint8_t*>(ctx->A_hv), ctx->A_scale,
                                      ctx->lda, s));
             }
+            CK(tc_setup(ctx, P_FP32, A32, ld32, nullptr, M, N));
             CK(cudaStreamSynchronize(s));
             ctx->mem.release(A32);
         }
@@ -498,8 +526,9 @@ static genios_status build_precond(genios_ctx* ctx, const void* d, double* ms) {
     }
     int ok = 0;
     CK(nystrom_build(hv_prec(ctx), ctx->m, ctx->n, ctx->sk, ctx->A_hv, ctx->lda, ctx->A_scale, d,
-                     ctx->Om, ctx->U, ctx->lam, nullptr, ctx->nw, &ok, flags, s));
-    ctx->launches += (flags & NYS_REUSE_BASIS) ? 14 : 21;
+                     ctx->Om, ctx->U, ctx->lam, nullptr, ctx->nw, &ok, flags,
+                     ctx->use_tc ? &ctx->tc : nullptr, s));
+    ctx->launches += ((flags & NYS_REUSE_BASIS) ? 14 : 21) + (ctx->use_tc ? 2 : 0);
     ctx->omega_ready = true;
     ctx->eig_warm = false;
     if (ok == -1) FAIL(GENIOS_ENUMERIC, "Nystrom sketch is not finite (NaN/Inf in A^T D A Omega)");
@@ -1027,7 +1056,20 @@ static_assert(genios::NYS_REUSE_BASIS == GENIOS_NYS_REUSE_BASIS && genios::NYS_W
 
 extern "C" size_t genios_op_nystrom_workspace_bytes(int precision, int64_t m, int64_t n, int s) {
     if (!prec_valid(precision) || m < 1 || n < 1 || s < 1 || s > 128) return 0;
-    return nystrom_work_bytes(hvp_of(precision), m, n, s) + 1024;
+    size_t b = nystrom_work_bytes(hvp_of(precision), m, n, s) + 1024;
+    if (precision != GENIOS_FP64) b += tc_bytes(tc_plan(m, n, s)) + 1024;
+    return b;
+}
+
+static TcSketch op_tc(void* base, int precision, int64_t m, int64_t n, int s) {
+    TcSketch t{};
+    t.plan = tc_plan(m, n, s);
+    t.work = tc_carve(base, t.plan);
+    t.wait_limit = 2000000LL * 2100LL;
+    return t;
+}
+static int src_prec_of(int precision) {
+    return precision == GENIOS_FP32 ? P_FP32 : precision == GENIOS_BF16 ? P_BF16 : P_FP8;
 }
 
 extern "C" genios_status genios_op_nystrom(int precision, int64_t m, int64_t n, int s, const void* A,
@@ -1043,11 +1085,50 @@ extern "C" genios_status genios_op_nystrom(int precision, int64_t m, int64_t n, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int P = hvp_of(precision);
     NysWork w = nystrom_carve(workspace, P, m, n, s);
+    TcSketch t{};
+    const TcSketch* tp = nullptr;
+    if (precision != GENIOS_FP64) {
+        const size_t nb = (nystrom_work_bytes(P, m, n, s) + 1023) & ~size_t(1023);
+        t = op_tc(static_cast<unsigned char*>(workspace) + nb, precision, m, n, s);
+        cudaError_t e = tc_pack_a(t.plan, t.work, src_prec_of(precision), A, lda, row_scale, st);
+        if (e != cudaSuccess) return op_err(e);
+        tp = &t;
+    }
     int ok = 0;
     cudaError_t e = nystrom_build(P, m, n, s, A, lda, row_scale, d, Omega, U_out, lam_out, eta_out, w,
-                                  &ok, flags, st);
+                                  &ok, flags, tp, st);
     if (e != cudaSuccess) return op_err(e);
     return ok >= 1 ? GENIOS_OK : GENIOS_ENUMERIC;
+}
+
+extern "C" size_t genios_op_sketch_workspace_bytes(int precision, int64_t m, int64_t n, int s) {
+    if (!prec_valid(precision) || precision == GENIOS_FP64 || m < 1 || n < 1 || s < 1 || s > 128) return 0;
+    return tc_bytes(tc_plan(m, n, s)) + 1024;
+}
+
+extern "C" genios_status genios_op_sketch(int precision, int64_t m, int64_t n, int s, const void* A,
+                                          int64_t lda, const float* row_scale, const float* d, float* Omega,
+                                          float* Y_out, void* workspace, size_t workspace_bytes, void* stream) {
+    if (!prec_valid(precision) || precision == GENIOS_FP64 || m < 1 || n < 1 || s < 1 || s > 128 || !A ||
+        !Omega || !Y_out || lda < n)
+        return GENIOS_EINVAL;
+    if (precision == GENIOS_FP8_E4M3 && !row_scale) return GENIOS_EINVAL;
+    if (!workspace || workspace_bytes < genios_op_sketch_workspace_bytes(precision, m, n, s)) return GENIOS_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    TcSketch t = op_tc(workspace, precision, m, n, s);
+    cudaError_t e = tc_pack_a(t.plan, t.work, src_prec_of(precision), A, lda, row_scale, st);
+    if (e == cudaSuccess) e = tc_pack_omega(t.plan, t.work, Omega, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t.work.err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = tc_sketch(t.plan, t.work, d, Y_out, t.wait_limit, st);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, t.work.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return op_err(e);
+    if (err != 0) {
+        set_last_error("genios_op_sketch: a bounded wait in the tensor-core GEMM ran out");
+        return GENIOS_ETIMEOUT;
+    }
+    return GENIOS_OK;
 }
 
 extern "C" genios_status genios_op_precond(int precision, int64_t n, int s, const void* U, const double* lam,

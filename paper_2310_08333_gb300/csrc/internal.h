@@ -180,10 +180,43 @@ NysWork nystrom_carve(void* base, int prec, int64_t m, int64_t n, int sk);
 // flags: NYS_REUSE_BASIS = w.Oq already holds the orthonormal basis of this Om (an earlier build
 // on the same workspace); NYS_WARM_EIG = the eigenvectors of that earlier build, still in the
 // workspace, start the Jacobi iteration.
-enum { NYS_REUSE_BASIS = 1, NYS_WARM_EIG = 2 };   // = GENIOS_NYS_REUSE_BASIS, GENIOS_NYS_WARM
+enum { NYS_REUSE_BASIS = 1, NYS_WARM_EIG = 2 };
+
+// Tensor-core sketch (umma.cu): operands in the blocked bf16 layout, products on tcgen05.
+struct TcPlan {
+    int64_t m, n;
+    int sk, np;                      // np = s rounded up to 16 (MMA N)
+    int64_t rpad_m, kpad_n, rpad_n, kpad_m;
+    int splits1, splits2;            // K splits of W = A Omega and Y = A^T W'
+    bool ok;
+};
+struct TcWork {
+    unsigned char *A_rows, *A_cols, *Om, *W;
+    float* part;
+    int* err;
+};
+struct TcSketch {
+    TcPlan plan;
+    TcWork work;
+    long long wait_limit;
+};
+TcPlan tc_plan(int64_t m, int64_t n, int sk);
+size_t tc_bytes(const TcPlan& p, size_t* off = nullptr);
+TcWork tc_carve(void* base, const TcPlan& p);
+// Packs A (m x n, row stride lda, stored as src_prec: P_FP32, P_BF16, or P_FP8 with row scales)
+// into the two blocked bf16 operands.
+cudaError_t tc_pack_a(const TcPlan& p, TcWork w, int src_prec, const void* A, int64_t lda,
+                      const float* row_scale, cudaStream_t s);
+// Rounds Om (n x s float) to bf16 values in place and packs it.
+cudaError_t tc_pack_omega(const TcPlan& p, TcWork w, float* Om, cudaStream_t s);
+// Y (n x s float) = A^T diag(d) A Om with the packed operands (d may be NULL: identity).
+cudaError_t tc_sketch(const TcPlan& p, TcWork w, const float* d, float* Y, long long wait_limit,
+                      cudaStream_t s);   // = GENIOS_NYS_REUSE_BASIS, GENIOS_NYS_WARM
+// tc: when non-NULL (value type float), the sketch runs on the tensor cores with the packed
+// operands of tc (A already packed); otherwise on the CUDA cores in `prec`.
 cudaError_t nystrom_build(int prec, int64_t m, int64_t n, int sk, const void* A, int64_t lda,
                           const float* row_scale, const void* d, const void* Om, void* U,
                           double* lam, double* eta_out, NysWork w, int* chol_ok, int flags,
-                          cudaStream_t s);
+                          const TcSketch* tc, cudaStream_t s);
 
 }  // namespace genios

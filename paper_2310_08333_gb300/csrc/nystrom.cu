@@ -827,7 +827,8 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
 
 cudaError_t nystrom_build(int prec, int64_t m, int64_t n, int sk, const void* A, int64_t lda,
                           const float* rs, const void* d, const void* Om, void* U, double* lam,
-                          double* eta_out, NysWork w, int* chol_ok, int flags, cudaStream_t s) {
+                          double* eta_out, NysWork w, int* chol_ok, int flags, const TcSketch* tc,
+                          cudaStream_t s) {
     if (sk < 1 || sk > 128) return cudaErrorInvalidValue;
     const bool reuse = (flags & NYS_REUSE_BASIS) != 0;
     const bool warm = (flags & NYS_WARM_EIG) != 0;
@@ -846,10 +847,27 @@ cudaError_t nystrom_build(int prec, int64_t m, int64_t n, int sk, const void* A,
     if (!reuse) {
         cudaError_t e = orthonormalize<float>(n, sk, static_cast<const float*>(Om), w, s);
         if (e != cudaSuccess) return e;
+        if (tc) {   // the basis is rounded to the bf16 values the tensor cores multiply
+            e = tc_pack_omega(tc->plan, tc->work, static_cast<float*>(w.Oq), s);
+            if (e != cudaSuccess) return e;
+        }
     }
     const float* Of = static_cast<const float*>(w.Oq);
     float* Wf = static_cast<float*>(w.W);
     float* Yf = static_cast<float*>(w.Y);
+    if (tc) {
+        cudaError_t e = cudaMemsetAsync(tc->work.err, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = tc_sketch(tc->plan, tc->work, df, Yf, tc->wait_limit, s);
+        int err = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&err, tc->work.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        if (err != 0) {
+            std::fprintf(stderr, "[genios] tensor-core sketch: a bounded wait ran out (code %d)\n", err);
+            return cudaErrorLaunchTimeout;
+        }
+        return core<float>(n, sk, Of, Yf, w, static_cast<float*>(U), lam, eta_out, chol_ok, warm, s);
+    }
     if (prec == P_FP32) launch_sketch<P_FP32, float>(m, n, sk, A, lda, rs, df, Of, Wf, Yf, s);
     else if (prec == P_BF16) launch_sketch<P_BF16, float>(m, n, sk, A, lda, rs, df, Of, Wf, Yf, s);
     else if (prec == P_FP8) launch_sketch<P_FP8, float>(m, n, sk, A, lda, rs, df, Of, Wf, Yf, s);

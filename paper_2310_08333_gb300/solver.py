@@ -201,6 +201,18 @@ def nystrom(prec, A, n, s, d, Omega, row_scale=None, workspace=None, flags=0):
     return U, lam, eta
 
 
+def sketch(prec, A, n, s, d, Omega, row_scale=None):
+    """Tensor-core sketch Y = A^T diag(d) A Omega; Omega (float32, n x s) is rounded to bf16 in
+    place.  Returns Y (n x s float32)."""
+    m = A.shape[0]
+    Y = torch.empty((n, s), dtype=torch.float32, device="cuda")
+    nb = int(L.lib().genios_op_sketch_workspace_bytes(prec, m, n, s))
+    ws = torch.empty(max(nb, 1), dtype=torch.uint8, device="cuda")
+    _chk(L.lib().genios_op_sketch(prec, m, n, s, _ptr(A), A.shape[1], _ptr(row_scale), _ptr(d), _ptr(Omega),
+                                  _ptr(Y), _ptr(ws), nb, _stream_ptr()))
+    return Y
+
+
 def precond(prec, U, lam, nu, v):
     n, s = U.shape
     y = torch.empty(n, dtype=_vt(prec), device="cuda")
@@ -253,5 +265,5 @@ def pcg(prec, A, n, d, nu, r, U=None, lam=None, rtol=1e-6, max_iter=100, row_sca
 
 
 ops = SimpleNamespace(lda=lda, pad=pad, hv=hv, hv_noalloc=hv_noalloc, gradient=gradient, zu_update=zu_update, nystrom=nystrom,
-                      nystrom_workspace=nystrom_workspace,
+                      nystrom_workspace=nystrom_workspace, sketch=sketch,
                       precond=precond, omega=omega, philox=philox, quantize=quantize, pcg=pcg)

@@ -206,6 +206,49 @@ def test_zu_update_threshold_ties_map_to_zero(G):
     np.testing.assert_array_equal(ud.cpu().numpy(), [1.5, -1.5, 0.5, 1.5])
 
 
+# ---------------------------------------------------------------------------- tensor-core sketch
+def _sketch_operand(prec, Aeff):
+    """The matrix the tensor-core sketch multiplies: A rounded to bfloat16 (FP8: the float32
+    dequantised value, rounded)."""
+    return oquant.bf16_rne(np.asarray(Aeff, dtype=np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+@pytest.mark.parametrize("shape", [(37, 5, 3), (300, 200, 20), (1000, 700, 100), (2100, 1500, 128),
+                                   (130, 4100, 16)])
+@pytest.mark.parametrize("with_d", [True, False])
+def test_tensor_sketch_matches_oracle(G, prec, shape, with_d):
+    """Y = A^T diag(d) A Omega on tcgen05 against the float64 product of the same bf16-rounded
+    operands.  The only approximation left is the hi + lo split of D W (2^-17 relative) and
+    float32 accumulation, so the tolerance is 2e-5 of max |Y|."""
+    rng = np.random.default_rng(21)
+    m, n, s = shape
+    A = rng.standard_normal((m, n))
+    d = rng.uniform(0.05, 0.25, m)
+    Ad, Aeff, sc = _matrices(prec, A)
+    Om = torch.as_tensor(rng.standard_normal((n, s)), dtype=torch.float32, device="cuda").contiguous()
+    Y = G.ops.sketch(prec, Ad, n, s, dev(d) if with_d else None, Om, row_scale=sc)
+    Omr = Om.double().cpu().numpy()
+    np.testing.assert_array_equal(Omr, oquant.bf16_rne(Omr))          # rounded in place
+    Ab = _sketch_operand(prec, Aeff)
+    dr = d.astype(np.float32).astype(np.float64) if with_d else np.ones(m)
+    rel_close(Y.cpu().numpy(), olin.sketch(Ab, dr, Omr), 2e-5)
+
+
+def test_tensor_sketch_full_size(G):
+    """The 20000 x 8000, s = 100 sketch of the bench workload (two CTAs per SM, split K)."""
+    rng = np.random.default_rng(22)
+    P = problems.logistic_lowrank()
+    m, n, s = P.m, P.n, 100
+    d = rng.uniform(0.0, 0.25, m)
+    Ad, Aeff, _ = _matrices(1, P.A)
+    Om = torch.as_tensor(rng.standard_normal((n, s)), dtype=torch.float32, device="cuda").contiguous()
+    Y = G.ops.sketch(1, Ad, n, s, dev(d), Om)
+    Ab = _sketch_operand(1, Aeff)
+    ref = Ab.T @ (d.astype(np.float32).astype(np.float64)[:, None] * (Ab @ Om.double().cpu().numpy()))
+    rel_close(Y.cpu().numpy(), ref, 2e-5)
+
+
 # ---------------------------------------------------------------------------- Nystrom
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("shape", [(900, 700, 40), (3000, 1500, 100)])
@@ -219,9 +262,13 @@ def test_nystrom_matches_oracle(G, prec, shape):
     Ad, Aeff, sc = _matrices(prec, A)
     Om = G.ops.omega(prec, n, s, seed=99)
     U, lam, eta = G.ops.nystrom(prec, Ad, n, s, dev(d, vt), Om, row_scale=sc)
-    # the library sketches with an orthonormal basis of range(Omega); so does the oracle
+    # the library sketches with an orthonormal basis of range(Omega); so does the oracle.  Float
+    # value types sketch on the tensor cores: bf16-rounded A and basis.
     Omr = olin.orthonormal_test_matrix(Om.double().cpu().numpy())
     dr = d if prec == 0 else d.astype(np.float32).astype(np.float64)
+    if prec != 0:
+        Omr = oquant.bf16_rne(Omr)
+        Aeff = _sketch_operand(prec, Aeff)
     Y = olin.sketch(Aeff, dr, Omr)
     eps = np.finfo(np.float64 if prec == 0 else np.float32).eps
     Ur, lr, er = olin.nystrom_from_sketch(Y, Omr, eps=eps)
