@@ -96,6 +96,7 @@ struct genios_ctx {
     void* U = nullptr;
     double* lam = nullptr;
     void* nyswork = nullptr;
+    CgvPlan cgv{};              // cluster CG vector kernel
     void* tcbuf = nullptr;      // tensor-core sketch operands (value type float only)
     TcSketch tc{};
     bool use_tc = false;
@@ -424,6 +425,8 @@ extern "C" genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const
     if (sk < 0) sk = (int)std::min<int64_t>(50, N / 20);
     sk = (int)std::min<int64_t>(sk, N);
     ctx->sk = std::max(0, sk);
+    ctx->cgv = cgv_plan(ctx->dbl, N, ctx->sk);
+    if (!ctx->cgv.ok) FAIL(GENIOS_EUNSUPPORTED, "no thread-block cluster configuration for the CG vector kernel");
     if (ctx->sk > 0) {
         CK(ctx->mem.get(&ctx->Om, (size_t)N * ctx->sk * vt));
         CK(ctx->mem.get(&ctx->U, (size_t)N * ctx->sk * vt));
@@ -568,17 +571,13 @@ static genios_status build_cg_graph(genios_ctx* ctx, const void* d, bool pc) {
     const int sk = pc ? ctx->sk : 0;
     cudaError_t e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = hv_pass(ctx, ctx->p, ctx->zc, d, &ctx->S->cg_done, true);
+    if (e == cudaSuccess) e = hv_pass(ctx, ctx->p, nullptr, d, &ctx->S->cg_done, true);
     if (e == cudaSuccess)
-        e = cg_q(ctx->dbl, ctx->Pbuf, ctx->plan_hv.grid, ctx->ldp, ctx->n, ctx->p, ctx->zc, ctx->q,
-                 ctx->S, ctx->sc, ctx->cap_stream);
+        e = cgv_q(ctx->dbl, ctx->Pbuf, ctx->plan_hv.grid, ctx->ldp, ctx->n, ctx->p, ctx->q, ctx->U, sk,
+                  ctx->sc.part, ctx->S, ctx->cap_stream);
     if (e == cudaSuccess)
-        e = cg_update(ctx->dbl, ctx->n, ctx->delta, ctx->r, ctx->p, ctx->q, ctx->U, sk, ctx->zc,
-                      ctx->S, ctx->sc, ctx->cap_stream);
-    if (e == cudaSuccess && pc)
-        e = cg_precond(ctx->dbl, ctx->n, ctx->U, sk, ctx->lam, ctx->r, ctx->zc, ctx->S, ctx->sc,
-                       ctx->cap_stream);
-    if (e == cudaSuccess) e = cg_condition((unsigned long long)h, ctx->S, 1, ctx->cap_stream);
+        e = cgv_iter(ctx->dbl, ctx->cgv, ctx->n, ctx->q, ctx->r, ctx->delta, ctx->p, ctx->U, sk, ctx->lam,
+                     ctx->S, ctx->sc.part, (unsigned long long)h, 1, 1, ctx->cap_stream);
     cudaGraph_t captured = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &captured);
     ctx->stream = saved;
@@ -602,14 +601,10 @@ static genios_status build_cg_graph(genios_ctx* ctx, const void* d, bool pc) {
 // Hv launches.
 static genios_status cg_loop(genios_ctx* ctx, const void* d, int* iters, std::vector<float>* hv_ms) {
     cudaStream_t s = ctx->stream;
-    if (!ctx->delta || !ctx->r || !ctx->p || !ctx->q || !ctx->zc || !ctx->S || !ctx->Pbuf)
+    if (!ctx->delta || !ctx->r || !ctx->p || !ctx->q || !ctx->S || !ctx->Pbuf)
         FAIL(GENIOS_EINVAL, "cg_loop: work vector not allocated");
     const bool pc = ctx->sk > 0 && ctx->have_precond;
     const int sk = pc ? ctx->sk : 0;
-    if (pc) {
-        CK(cg_precond(ctx->dbl, ctx->n, ctx->U, sk, ctx->lam, ctx->r, ctx->zc, ctx->S, ctx->sc, s));
-        ctx->launches++;
-    }
     if (ctx->opt.use_graphs && !ctx->opt.profile) {
         if (!ctx->cg_exec || ctx->cg_graph_pc != pc || ctx->cg_graph_d != d) {
             genios_status st = build_cg_graph(ctx, d, pc);
@@ -618,8 +613,9 @@ static genios_status cg_loop(genios_ctx* ctx, const void* d, int* iters, std::ve
         CK(cudaGraphLaunch(ctx->cg_exec, s));
         genios_status st = read_state(ctx);
         if (st != GENIOS_OK) return st;
+        if (ctx->Sh->cg_fault) FAIL(GENIOS_ETIMEOUT, "CG vector kernel: a bounded device wait ran out");
         *iters = ctx->Sh->cg_it;
-        ctx->launches += (int64_t)(ctx->Sh->cg_guard) * (pc ? 5 : 4);
+        ctx->launches += (int64_t)(ctx->Sh->cg_guard) * 4;
         return GENIOS_OK;
     }
     const int G = ctx->plan_hv.grid;
@@ -634,14 +630,15 @@ static genios_status cg_loop(genios_ctx* ctx, const void* d, int* iters, std::ve
             }
             CK(cudaEventRecord(ctx->evs[0], s));
         }
-        CK(hv_pass(ctx, ctx->p, ctx->zc, d, &ctx->S->cg_done));
+        CK(hv_pass(ctx, ctx->p, nullptr, d, &ctx->S->cg_done));
         if (prof) CK(cudaEventRecord(ctx->evs[1], s));
-        CK(cg_q(ctx->dbl, ctx->Pbuf, G, ctx->ldp, ctx->n, ctx->p, ctx->zc, ctx->q, ctx->S, ctx->sc, s));
-        CK(cg_update(ctx->dbl, ctx->n, ctx->delta, ctx->r, ctx->p, ctx->q, ctx->U, sk, ctx->zc,
-                     ctx->S, ctx->sc, s));
-        ctx->launches += 2;
+        CK(cgv_q(ctx->dbl, ctx->Pbuf, G, ctx->ldp, ctx->n, ctx->p, ctx->q, ctx->U, sk, ctx->sc.part, ctx->S, s));
+        CK(cgv_iter(ctx->dbl, ctx->cgv, ctx->n, ctx->q, ctx->r, ctx->delta, ctx->p, ctx->U, sk, ctx->lam,
+                    ctx->S, ctx->sc.part, 0ull, 0, 0, s));
+        ctx->launches += 3;
         genios_status st = read_state(ctx);
         if (st != GENIOS_OK) return st;
+        if (ctx->Sh->cg_fault) FAIL(GENIOS_ETIMEOUT, "CG vector kernel: a bounded device wait ran out");
         if (prof) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, ctx->evs[0], ctx->evs[1]));
@@ -649,10 +646,6 @@ static genios_status cg_loop(genios_ctx* ctx, const void* d, int* iters, std::ve
         }
         it = ctx->Sh->cg_it;
         if (ctx->Sh->cg_done) break;
-        if (pc) {
-            CK(cg_precond(ctx->dbl, ctx->n, ctx->U, sk, ctx->lam, ctx->r, ctx->zc, ctx->S, ctx->sc, s));
-            ctx->launches++;
-        }
     }
     *iters = it;
     return GENIOS_OK;
@@ -840,8 +833,9 @@ extern "C" genios_status genios_solve(genios_ctx* ctx, const double* lambda1, co
                             : std::min(std::sqrt(last_rp * last_rd), 1.0) / std::pow((double)k, o.gamma);
         tol = std::max(tol, floor);
         // ---- x-step rhs, CG
-        CK(rhs_init(ctx->dbl, n, ctx->g, ctx->x, ctx->z, ctx->u, rho, u_scale, nu, tol, o.max_cg_iter,
-                    ctx->r, ctx->delta, ctx->p, ctx->zc, ctx->U, use_pc ? ctx->sk : 0, ctx->S, ctx->sc, s));
+        CK(cgv_start(ctx->dbl, ctx->cgv, n, ctx->g, ctx->x, ctx->z, ctx->u, rho, u_scale, nu, tol,
+                     o.max_cg_iter, ctx->r, ctx->delta, ctx->p, ctx->U,
+                     use_pc && ctx->have_precond ? ctx->sk : 0, ctx->lam, ctx->S, ctx->sc.part, s));
         ctx->launches++;
         int cgit = 0;
         st = cg_loop(ctx, dvec, &cgit, &hv_ms);
@@ -1205,6 +1199,8 @@ extern "C" genios_status genios_op_pcg(int precision, int64_t m, int64_t n, cons
     ctx->U = const_cast<void*>(U);
     ctx->lam = const_cast<double*>(lam);
     ctx->delta = delta_out;
+    genios_default_options(&ctx->opt);
+    ctx->opt.use_graphs = 0;   // host-driven loop: the transient context owns no graph
     ctx->opt.device_wait_limit_us = 2000000;
     ctx->opt.profile = 0;
     const size_t vb = (size_t)lda * ctx->vt;
@@ -1228,8 +1224,13 @@ extern "C" genios_status genios_op_pcg(int precision, int64_t m, int64_t n, cons
         cudaMemsetAsync(ctx->S, 0, sizeof(DevState), st);
         cudaMemsetAsync(ctx->g, 0, vb, st);
         // rhs: r = -(0 + (-1)(r_in - 0 + 0)) = r_in   (g doubles as the zero z and u)
-        cudaError_t e = rhs_init(ctx->dbl, n, ctx->g, r, ctx->g, ctx->g, -1.0, 1.0, nu, rtol, max_iter,
-                                 ctx->r, delta_out, ctx->p, ctx->zc, U, s, ctx->S, ctx->sc, st);
+        ctx->cgv = cgv_plan(ctx->dbl, n, s);
+        if (!ctx->cgv.ok) {
+            result = GENIOS_EUNSUPPORTED;
+            break;
+        }
+        cudaError_t e = cgv_start(ctx->dbl, ctx->cgv, n, ctx->g, r, ctx->g, ctx->g, -1.0, 1.0, nu, rtol,
+                                  max_iter, ctx->r, delta_out, ctx->p, U, s, lam, ctx->S, ctx->sc.part, st);
         if (e != cudaSuccess) {
             result = op_err(e);
             break;

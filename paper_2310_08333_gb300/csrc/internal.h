@@ -24,6 +24,7 @@ struct DevState {
     int32_t cg_done;  // 1 once ||r|| <= tol ||rhs|| or cg_it == cg_max
     int32_t cg_max;
     int32_t cg_first; // 1 before the first preconditioner application of a solve
+    int32_t cg_fault; // non-zero if a bounded device wait of the CG vector kernel ran out
     // gradient pass at x (§3.3) and residual norms (Eqs. (11)-(12))
     double loss_sum;  // sum_i loss(a_i^T x - b_i)
     double g2;        // ||grad f(x)||^2
@@ -48,7 +49,9 @@ struct DevState {
     unsigned long long hv_t0, hv_t1;  // first-CTA start / last-CTA end of the current Hv launch (ns)
     double hv_ns;     // accumulated device time of the timed Hv launches
     double pad[1];
-    double w[256];    // U^T r (Nystrom preconditioner), s <= 256
+    double w[256];    // U^T r (Nystrom preconditioner), s <= 256 (op-level preconditioner)
+    double cgw[128];  // U^T r of the current CG residual (cluster CG path, s <= 128)
+    double cgc[128];  // preconditioner coefficients c_i w_i for the next direction
 };
 
 // ------------------------------------------------------------------------------------------
@@ -107,19 +110,32 @@ struct Scratch {
 // y = sum_b P[b] + nu v  (plain Hv finish, op level)
 cudaError_t hv_finish(bool dbl, const void* P, int G, int64_t ldp, int64_t n, double nu,
                       const void* v, void* y, cudaStream_t s);
-// CG: p = zc + beta p; q = sum_b P[b] + nu p; pq, alpha
-cudaError_t cg_q(bool dbl, const void* P, int G, int64_t ldp, int64_t n, void* p, const void* zc,
-                 void* q, DevState* S, Scratch sc, cudaStream_t s);
-// CG: delta += alpha p; r -= alpha q; rr; U^T r (s > 0); done flag; (s == 0: zc = r, beta)
-cudaError_t cg_update(bool dbl, int64_t n, void* delta, void* r, const void* p, const void* q,
-                      const void* U, int sk, void* zc, DevState* S, Scratch sc, cudaStream_t s);
-// CG: zc = P^{-1} r (Eq. (10)) from S->w; rz, beta
+// zc = P^{-1} r (Eq. (10)) from S->w (after rhs_init); rz, beta  (op-level preconditioner)
 cudaError_t cg_precond(bool dbl, int64_t n, const void* U, int sk, const double* lam,
                        const void* r, void* zc, DevState* S, Scratch sc, cudaStream_t s);
-// Device-side CG loop condition (CUDA graph conditional WHILE node): continue while the CG is
-// not done and the guard counter has not passed cg_max + 2; also folds the device timer of the
-// last Hv launch into S->hv_ns / hv_count when `timed`.
-cudaError_t cg_condition(unsigned long long handle, DevState* S, int timed, cudaStream_t s);
+
+// CG vector work as one thread-block cluster (cgvec.cu)
+struct CgvPlan {
+    int cl;          // CTAs in the cluster (16, else 8)
+    bool ok;
+};
+CgvPlan cgv_plan(bool dbl, int64_t n, int sk);
+// Per-block partials (cgv_blocks(n) blocks of 32 rows, 129 doubles each) live in `part`.
+int cgv_blocks(int64_t n);
+// q = sum_b P[b] + nu p; per-block partials of p^T q and U^T q.
+cudaError_t cgv_q(bool dbl, const void* P, int G, int64_t ldp, int64_t n, const void* p, void* q,
+                  const void* U, int sk, double* part, const DevState* S, cudaStream_t s);
+// Start of a CG solve on the step-form right-hand side r = -(g + rho (x - z + u_scale u))
+// (u <- u_scale u, delta = 0, p = P^{-1} r, DevState scalars set): three launches.
+cudaError_t cgv_start(bool dbl, const CgvPlan& pl, int64_t n, const void* g, const void* x, const void* z,
+                      void* u, double rho, double u_scale, double nu, double tol, int cg_max, void* r,
+                      void* delta, void* p, const void* U, int sk, const double* lam, DevState* S,
+                      double* part, cudaStream_t s);
+// One CG iteration after cgv_q: the cluster step (scalars, stop test, graph condition when
+// use_cond) and the new direction (two launches).
+cudaError_t cgv_iter(bool dbl, const CgvPlan& pl, int64_t n, const void* q, void* r, void* delta, void* p,
+                     const void* U, int sk, const double* lam, DevState* S, double* part,
+                     unsigned long long cond, int use_cond, int timed, cudaStream_t s);
 // x-step right-hand side and CG initialisation:
 //   u *= u_scale; r = -(g + rho (x - z + u)); delta = 0; p = 0; rhs2; U^T r
 cudaError_t rhs_init(bool dbl, int64_t n, const void* g, const void* x, const void* z, void* u,

@@ -86,6 +86,7 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
         if (tid == RP_CTHREADS) {
             const char* Ab = static_cast<const char*>(a.A);
             const char* Al = static_cast<const char*>(a.A_lo);
+            const uint64_t pol = l2_evict_first_policy();
             for (int st = 0; st < nstage_work; ++st) {
                 const int s = st % nst_cap;
                 const int use = st / nst_cap;
@@ -102,8 +103,8 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
                     !GCHK(a.dbg, r0 + (long long)st * rps + rows - 1, a.m)) break;
 #endif
                 mbar_arrive_expect_tx(&full[s], bytes * SPLIT);
-                bulk_g2s(dst, Ab + off, bytes, &full[s]);
-                if (HILO) bulk_g2s(dst + (size_t)rps * row_bytes, Al + off, bytes, &full[s]);
+                bulk_g2s_hint(dst, Ab + off, bytes, &full[s], pol);
+                if (HILO) bulk_g2s_hint(dst + (size_t)rps * row_bytes, Al + off, bytes, &full[s], pol);
             }
         }
         return;

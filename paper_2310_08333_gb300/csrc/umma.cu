@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) umma_gemm_kernel(UmmaArgs a) {
 
     if (warp == 0) {
         if (lane == 0) {   // producer: one A tile + the matching B tile per stage
+            const uint64_t pol = l2_evict_first_policy();   // A tiles are read once per product
             int f = 0;
             for (; f < nk; ++f) {
                 const int s = f % a.stages, use = f / a.stages;
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) umma_gemm_kernel(UmmaArgs a) {
                 unsigned char* dst = smem + (size_t)s * stage_bytes;
                 const int64_t kt = kt0 + f;
                 mbar_arrive_expect_tx(&full[s], stage_bytes);
-                bulk_g2s(dst, a.A + (size_t)(tile * a.ktiles + kt) * UM_TILE_A, UM_TILE_A, &full[s]);
+                bulk_g2s_hint(dst, a.A + (size_t)(tile * a.ktiles + kt) * UM_TILE_A, UM_TILE_A, &full[s], pol);
                 bulk_g2s(dst + UM_TILE_A, a.B + (size_t)kt * bytes_b, bytes_b, &full[s]);
             }
             issued = f;

@@ -42,31 +42,6 @@ __global__ void hv_finish_kernel(const VT* P, int G, int64_t ldp, int64_t n, dou
     if ((threadIdx.x >> 5) == 0 && j < n) y[j] = sum + (VT)nu * v[j];
 }
 
-template <typename VT>
-__global__ void cg_q_kernel(const VT* P, int G, int64_t ldp, int64_t n, VT* p, const VT* zc, VT* q,
-                            DevState* S, Scratch sc) {
-    if (S->cg_done) return;
-    __shared__ VT sh[8 * 33];
-    const int64_t j = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
-    VT sum = column_sum<VT, VT>(P, G, ldp, j, n, sh);
-    double v[1] = {0.0};
-    if ((threadIdx.x >> 5) == 0 && j < n) {
-        const VT pj = zc[j] + (VT)S->beta * p[j];
-        const VT qj = sum + (VT)S->nu * pj;
-        p[j] = pj;
-        q[j] = qj;
-        v[0] = (double)pj * (double)qj;
-    }
-    double out[1];
-    if (grid_sum<1>(v, sc.part, sc.counter, out)) {
-        if (threadIdx.x == 0) {
-            S->pq = out[0];
-            S->alpha = out[0] > 0.0 ? S->rz / out[0] : 0.0;
-            if (!(out[0] > 0.0)) S->cg_done = 1;  // breakdown / exact solution
-        }
-    }
-}
-
 // U^T r over the block's UTR_ROWS rows (r staged in shared memory) plus the block sum of r^2.
 // Threads: c = t % 128 is a column of U, g = t / 128 one of two row groups; products and the
 // per-thread sums run in the value type, block partials in float64.  The last block adds the
@@ -132,41 +107,6 @@ GENIOS_DEV bool ut_r_and_norm(const VT* U, int sk, const VT* rsh, int64_t j0, in
     rr_out = s_rr;
     if (t == 0) *counter = 0u;
     return true;
-}
-
-template <typename VT>
-__global__ void cg_update_kernel(int64_t n, VT* delta, VT* r, const VT* p, const VT* q,
-                                 const VT* U, int sk, VT* zc, DevState* S, Scratch sc) {
-    if (S->cg_done) return;
-    __shared__ VT rsh[UTR_ROWS];
-    const int64_t j0 = (int64_t)blockIdx.x * UTR_ROWS;
-    const int64_t j = j0 + threadIdx.x;
-    const VT al = (VT)S->alpha;
-    double rr = 0.0;
-    if (threadIdx.x < UTR_ROWS) {
-        VT rj = VT(0);
-        if (j < n) {
-            delta[j] += al * p[j];
-            rj = r[j] - al * q[j];
-            r[j] = rj;
-            if (sk == 0) zc[j] = rj;
-            rr = (double)rj * (double)rj;
-        }
-        rsh[threadIdx.x] = rj;
-    }
-    __syncthreads();
-    double rr_tot;
-    if (ut_r_and_norm<VT>(U, sk, rsh, j0, n, rr, sc.part, sc.counter, S->w, rr_tot, sc.dbg)) {
-        if (threadIdx.x == 0) {
-            S->rr = rr_tot;
-            S->cg_it += 1;
-            if (rr_tot <= S->tol * S->tol * S->rhs2 || S->cg_it >= S->cg_max) S->cg_done = 1;
-            if (sk == 0) {  // no preconditioner: z = r, so r^T z = ||r||^2
-                S->beta = S->rz > 0.0 ? rr_tot / S->rz : 0.0;
-                S->rz = rr_tot;
-            }
-        }
-    }
 }
 
 template <typename VT>
@@ -406,19 +346,6 @@ __global__ void convert_kernel(int64_t rows, int64_t cols, const S* src, int64_t
     }
 }
 
-__global__ void cg_cond_kernel(cudaGraphConditionalHandle h, DevState* S, int timed) {
-    if (timed && S->hv_t1 > S->hv_t0) {   // fold the last Hv launch's device time
-        S->hv_ns += (double)(S->hv_t1 - S->hv_t0);
-        S->hv_count += 1;
-    }
-    S->hv_t0 = ~0ull;
-    S->hv_t1 = 0ull;
-    const int guard = ++S->cg_guard;
-    const int cap = S->cg_max < 10000 ? S->cg_max : 10000;   // hard bound on the device loop
-    const bool more = S->cg_done == 0 && guard < cap + 2;
-    cudaGraphSetConditional(h, more ? 1u : 0u);
-}
-
 // ------------------------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------------------------
@@ -444,26 +371,9 @@ cudaError_t hv_finish(bool dbl, const void* P, int G, int64_t ldp, int64_t n, do
     return cudaGetLastError();
 }
 
-cudaError_t cg_q(bool dbl, const void* P, int G, int64_t ldp, int64_t n, void* p, const void* zc,
-                 void* q, DevState* S, Scratch sc, cudaStream_t s) {
-    const int grid = nblocks(n, 32);
-    if (dbl) cg_q_kernel<double><<<grid, VT_THREADS, 0, s>>>(CC<double>(P), G, ldp, n, C<double>(p), CC<double>(zc), C<double>(q), S, sc);
-    else cg_q_kernel<float><<<grid, VT_THREADS, 0, s>>>(CC<float>(P), G, ldp, n, C<float>(p), CC<float>(zc), C<float>(q), S, sc);
-    return cudaGetLastError();
-}
-
 // per-block partials of U^T r must fit the scratch partial buffer
 static bool utr_fits(int64_t n, int sk) {
     return sk <= 128 && (int64_t)nblocks(n, UTR_ROWS) * (sk + 1) <= 262144;
-}
-
-cudaError_t cg_update(bool dbl, int64_t n, void* delta, void* r, const void* p, const void* q,
-                      const void* U, int sk, void* zc, DevState* S, Scratch sc, cudaStream_t s) {
-    if (!utr_fits(n, sk)) return cudaErrorInvalidValue;
-    const int grid = nblocks(n, UTR_ROWS);
-    if (dbl) cg_update_kernel<double><<<grid, VT_THREADS, 0, s>>>(n, C<double>(delta), C<double>(r), CC<double>(p), CC<double>(q), CC<double>(U), sk, C<double>(zc), S, sc);
-    else cg_update_kernel<float><<<grid, VT_THREADS, 0, s>>>(n, C<float>(delta), C<float>(r), CC<float>(p), CC<float>(q), CC<float>(U), sk, C<float>(zc), S, sc);
-    return cudaGetLastError();
 }
 
 cudaError_t cg_precond(bool dbl, int64_t n, const void* U, int sk, const double* lam, const void* r,
@@ -536,8 +446,4 @@ cudaError_t fill_zero(void* p, size_t bytes, cudaStream_t s) { return cudaMemset
 }  // namespace genios
 
 namespace genios {
-cudaError_t cg_condition(unsigned long long handle, DevState* S, int timed, cudaStream_t s) {
-    cg_cond_kernel<<<1, 1, 0, s>>>((cudaGraphConditionalHandle)handle, S, timed);
-    return cudaGetLastError();
-}
 }  // namespace genios
