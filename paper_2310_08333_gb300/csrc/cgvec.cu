@@ -27,6 +27,8 @@ constexpr int CGV_THREADS = 512;
 constexpr int CGV_ROWS = 32;          // rows of an n-vector per block of the all-SM kernels
 constexpr int CGV_BT = 256;           // threads of the all-SM kernels
 constexpr int CGV_STRIDE = 129;       // doubles per block partial: [0] scalar, [1 + c] s-vector
+constexpr int RPT = 3;                // vector rows per thread of the cluster step (n <= 3 * 512 * CL)
+constexpr int UNR = 12;               // block partials per thread of the cluster step (nb <= 48 CL)
 
 int cgv_blocks(int64_t n) { return (int)((n + CGV_ROWS - 1) / CGV_ROWS); }
 // the U^T r partials of cgv_p follow the cgv_q / cgv_r0 partials in the same buffer
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(CGV_BT) cgv_r0_kernel(int64_t n, const VT* g, 
 template <typename VT>
 __global__ void __launch_bounds__(CGV_BT) cgv_q_kernel(const VT* P, int G, int64_t ldp, int64_t n, const VT* p,
                                                        VT* q, const VT* U, int sk, double* part,
-                                                       const DevState* S) {
+                                                       const DevState* S, const VT* mask) {
     if (S->cg_done) return;
     __shared__ VT sh[8][33];
     __shared__ VT qsh[CGV_ROWS];
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(CGV_BT) cgv_q_kernel(const VT* P, int G, int64
             for (int k = 0; k < 8; ++k) s += sh[k][tx];
             const VT pj = p[j];
             qj = s + (VT)S->nu * pj;
+            if (mask != nullptr && mask[j] == VT(0)) qj = VT(0);   // operator restricted to the mask
             q[j] = qj;
             pq = (double)pj * (double)qj;
         }
@@ -171,51 +174,69 @@ __global__ void __launch_bounds__(CGV_THREADS, 1) cgv_kernel(CgvArgs<VT> a) {
     const double tol = a.mode == 1 ? tol_s : a.tol;
     const int cg_max = a.mode == 1 ? cgmax_s : a.cg_max;
 
+    // Every global load of this step is issued here, before any reduction, so that the step
+    // costs one memory round trip: the block partials of p^T q, this CTA's rows of the vectors,
+    // and this CTA's share of the U^T q / U^T r block partials.
+    const int64_t j0 = a.n * rank / CL, j1 = a.n * (rank + 1) / CL;
+    VT pv[RPT], qv[RPT], rv[RPT], dv[RPT];
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) {
+        const int64_t j = j0 + tid + (int64_t)t * CGV_THREADS;
+        pv[t] = qv[t] = rv[t] = dv[t] = VT(0);
+        if (j < j1) {
+            rv[t] = a.r[j];
+            if (a.mode == 1) {
+                pv[t] = a.p[j];
+                qv[t] = a.q[j];
+                dv[t] = a.delta[j];
+            }
+        }
+    }
+    double pqv = 0.0;
+    if (a.mode == 1)
+        for (int b = tid; b < a.nb; b += CGV_THREADS) pqv += a.part[(size_t)b * CGV_STRIDE];
+    const int c = tid & 127, g4 = tid >> 7;
+    const int b0 = (int)((int64_t)a.nb * rank / CL), b1 = (int)((int64_t)a.nb * (rank + 1) / CL);
+    double vq[UNR], vr[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+        const int bb = b0 + g4 + 4 * u;
+        const bool ok = c < sk && bb < b1;
+        vq[u] = ok ? a.part[(size_t)bb * CGV_STRIDE + 1 + c] : 0.0;
+        vr[u] = (ok && a.mode == 1) ? a.part_r[(size_t)bb * CGV_STRIDE + 1 + c] : 0.0;
+    }
+
     // alpha from the block partials of p^T q (same order in every CTA)
     double pq = 0.0, alpha = 0.0;
     if (a.mode == 1) {
-        double v[1] = {0.0};
-        for (int b = tid; b < a.nb; b += CGV_THREADS) v[0] += a.part[(size_t)b * CGV_STRIDE];
+        double v[1] = {pqv};
         block_sum<1>(v);
         pq = v[0];
         alpha = pq > 0.0 ? rz_old / pq : 0.0;
     }
 
     // this CTA's rows: delta += alpha p, r -= alpha q, ||r||^2
-    const int64_t j0 = a.n * rank / CL, j1 = a.n * (rank + 1) / CL;
     double rr_loc = 0.0;
-    for (int64_t j = j0 + tid; j < j1; j += CGV_THREADS) {
-        VT rj;
-        if (a.mode == 1) {
-            a.delta[j] += (VT)alpha * a.p[j];
-            rj = a.r[j] - (VT)alpha * a.q[j];
-            a.r[j] = rj;
-        } else {
-            rj = a.r[j];
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) {
+        const int64_t j = j0 + tid + (int64_t)t * CGV_THREADS;
+        if (j < j1) {
+            VT rj = rv[t];
+            if (a.mode == 1) {
+                a.delta[j] = dv[t] + (VT)alpha * pv[t];
+                rj = rv[t] - (VT)alpha * qv[t];
+                a.r[j] = rj;
+            }
+            rr_loc += (double)rj * (double)rj;
         }
-        rr_loc += (double)rj * (double)rj;
     }
     // this CTA's share of the block partials: start: U^T r; iteration: U^T r_old - alpha U^T q
     // (the direct U^T r of the previous residual comes from cgv_p, so the recurrence spans one step)
     {
-        const int c = tid & 127, g4 = tid >> 7;
-        const int b0 = (int)((int64_t)a.nb * rank / CL), b1 = (int)((int64_t)a.nb * (rank + 1) / CL);
-        double s = 0.0;
-        if (c < sk) {
-            constexpr int UNR = 8;
-            for (int b = b0 + g4; b < b1; b += 4 * UNR) {
-                double vq[UNR], vr[UNR];
+        double sacc = 0.0;
 #pragma unroll
-                for (int u = 0; u < UNR; ++u) {
-                    const int bb = b + 4 * u;
-                    vq[u] = bb < b1 ? a.part[(size_t)bb * CGV_STRIDE + 1 + c] : 0.0;
-                    vr[u] = (a.mode == 1 && bb < b1) ? a.part_r[(size_t)bb * CGV_STRIDE + 1 + c] : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < UNR; ++u) s += a.mode == 1 ? vr[u] - alpha * vq[u] : vq[u];
-            }
-        }
-        grp[g4][c] = s;
+        for (int u = 0; u < UNR; ++u) sacc += a.mode == 1 ? vr[u] - alpha * vq[u] : vq[u];
+        grp[g4][c] = sacc;
     }
     {
         double v[1] = {rr_loc};
@@ -295,7 +316,7 @@ __global__ void __launch_bounds__(CGV_THREADS, 1) cgv_kernel(CgvArgs<VT> a) {
 // iteration's w.  One warp per row, four columns per lane.
 template <typename VT>
 __global__ void __launch_bounds__(CGV_BT) cgv_p_kernel(int64_t n, const VT* r, VT* p, const VT* U, int sk,
-                                                       double* part_r, const DevState* S) {
+                                                       double* part_r, const DevState* S, const VT* mask) {
     if (S->cg_done) return;
     __shared__ VT csh[128];
     __shared__ VT ush[CGV_BT / 32][128];
@@ -342,7 +363,8 @@ __global__ void __launch_bounds__(CGV_BT) cgv_p_kernel(int64_t n, const VT* r, V
             for (int t = 1; t < RPW; ++t)
                 if (lane == t) rj = rv[t];
             const VT zj = rj + mine;
-            p[j] = beta != 0.0 ? zj + (VT)beta * p[j] : zj;
+            if (mask != nullptr && mask[j] == VT(0)) p[j] = VT(0);   // preconditioner restricted too
+            else p[j] = beta != 0.0 ? zj + (VT)beta * p[j] : zj;
         }
     }
     if (sk > 0) {
@@ -369,6 +391,7 @@ static CgvPlan plan_vt(int64_t n, int sk) {
     if (sk < 0 || sk > 128 || n < 1) return p;
     cudaFuncSetAttribute(cgv_kernel<VT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     for (int cl : {16, 8}) {
+        if ((n + cl - 1) / cl > (int64_t)RPT * CGV_THREADS || (cgv_blocks(n) + cl - 1) / cl > 4 * UNR) continue;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(cl);
         cfg.blockDim = dim3(CGV_THREADS);
@@ -415,7 +438,7 @@ template <typename VT>
 static cudaError_t start_vt(const CgvPlan& pl, int64_t n, const void* g, const void* x, const void* z, void* u,
                             double rho, double u_scale, double nu, double tol, int cg_max, void* r, void* delta,
                             void* p, const void* U, int sk, const double* lam, DevState* S, double* part,
-                            cudaStream_t s) {
+                            const void* mask, cudaStream_t s) {
     const int nb = cgv_blocks(n);
     cgv_r0_kernel<VT><<<nb, CGV_BT, 0, s>>>(n, static_cast<const VT*>(g), static_cast<const VT*>(x),
                                             static_cast<const VT*>(z), static_cast<VT*>(u), rho, u_scale,
@@ -441,39 +464,42 @@ static cudaError_t start_vt(const CgvPlan& pl, int64_t n, const void* g, const v
     e = launch_cluster(pl, a, s);
     if (e != cudaSuccess) return e;
     cgv_p_kernel<VT><<<nb, CGV_BT, 0, s>>>(n, static_cast<const VT*>(r), static_cast<VT*>(p),
-                                           static_cast<const VT*>(U), sk, part + part_r_offset(nb), S);
+                                           static_cast<const VT*>(U), sk, part + part_r_offset(nb), S,
+                                           static_cast<const VT*>(mask));
     return cudaGetLastError();
 }
 
 cudaError_t cgv_start(bool dbl, const CgvPlan& pl, int64_t n, const void* g, const void* x, const void* z,
                       void* u, double rho, double u_scale, double nu, double tol, int cg_max, void* r,
                       void* delta, void* p, const void* U, int sk, const double* lam, DevState* S,
-                      double* part, cudaStream_t s) {
+                      double* part, const void* mask, cudaStream_t s) {
     if (!pl.ok || sk > 128) return cudaErrorInvalidValue;
     return dbl ? start_vt<double>(pl, n, g, x, z, u, rho, u_scale, nu, tol, cg_max, r, delta, p, U, sk, lam, S,
-                                  part, s)
+                                  part, mask, s)
                : start_vt<float>(pl, n, g, x, z, u, rho, u_scale, nu, tol, cg_max, r, delta, p, U, sk, lam, S,
-                                 part, s);
+                                 part, mask, s);
 }
 
 cudaError_t cgv_q(bool dbl, const void* P, int G, int64_t ldp, int64_t n, const void* p, void* q, const void* U,
-                  int sk, double* part, const DevState* S, cudaStream_t s) {
+                  int sk, double* part, const DevState* S, const void* mask, cudaStream_t s) {
     const int nb = cgv_blocks(n);
     if (dbl)
         cgv_q_kernel<double><<<nb, CGV_BT, 0, s>>>(static_cast<const double*>(P), G, ldp, n,
                                                    static_cast<const double*>(p), static_cast<double*>(q),
-                                                   static_cast<const double*>(U), sk, part, S);
+                                                   static_cast<const double*>(U), sk, part, S,
+                                                   static_cast<const double*>(mask));
     else
         cgv_q_kernel<float><<<nb, CGV_BT, 0, s>>>(static_cast<const float*>(P), G, ldp, n,
                                                   static_cast<const float*>(p), static_cast<float*>(q),
-                                                  static_cast<const float*>(U), sk, part, S);
+                                                  static_cast<const float*>(U), sk, part, S,
+                                                  static_cast<const float*>(mask));
     return cudaGetLastError();
 }
 
 template <typename VT>
 static cudaError_t iter_vt(const CgvPlan& pl, int64_t n, const void* q, void* r, void* delta, void* p,
                            const void* U, int sk, const double* lam, DevState* S, double* part,
-                           unsigned long long cond, int use_cond, int timed, cudaStream_t s) {
+                           unsigned long long cond, int use_cond, int timed, const void* mask, cudaStream_t s) {
     const int nb = cgv_blocks(n);
     CgvArgs<VT> a{};
     a.mode = 1;
@@ -494,16 +520,17 @@ static cudaError_t iter_vt(const CgvPlan& pl, int64_t n, const void* q, void* r,
     cudaError_t e = launch_cluster(pl, a, s);
     if (e != cudaSuccess) return e;
     cgv_p_kernel<VT><<<nb, CGV_BT, 0, s>>>(n, static_cast<const VT*>(r), static_cast<VT*>(p),
-                                           static_cast<const VT*>(U), sk, part + part_r_offset(nb), S);
+                                           static_cast<const VT*>(U), sk, part + part_r_offset(nb), S,
+                                           static_cast<const VT*>(mask));
     return cudaGetLastError();
 }
 
 cudaError_t cgv_iter(bool dbl, const CgvPlan& pl, int64_t n, const void* q, void* r, void* delta, void* p,
                      const void* U, int sk, const double* lam, DevState* S, double* part,
-                     unsigned long long cond, int use_cond, int timed, cudaStream_t s) {
+                     unsigned long long cond, int use_cond, int timed, const void* mask, cudaStream_t s) {
     if (!pl.ok || sk > 128) return cudaErrorInvalidValue;
-    return dbl ? iter_vt<double>(pl, n, q, r, delta, p, U, sk, lam, S, part, cond, use_cond, timed, s)
-               : iter_vt<float>(pl, n, q, r, delta, p, U, sk, lam, S, part, cond, use_cond, timed, s);
+    return dbl ? iter_vt<double>(pl, n, q, r, delta, p, U, sk, lam, S, part, cond, use_cond, timed, mask, s)
+               : iter_vt<float>(pl, n, q, r, delta, p, U, sk, lam, S, part, cond, use_cond, timed, mask, s);
 }
 
 }  // namespace genios

@@ -105,6 +105,7 @@ struct genios_ctx {
     bool omega_ready = false;   // Om drawn and its orthonormal basis in nw.Oq
     bool eig_warm = false;      // nw holds the eigenvectors of the last successful core
     int n_sketch_total = 0;
+    int grad_cg_iters = 0;      // adjoint CG iterations of the last genios_grad
     // device scalars
     DevState* S = nullptr;
     DevState* Sh = nullptr;  // pinned host mirror
@@ -574,10 +575,10 @@ static genios_status build_cg_graph(genios_ctx* ctx, const void* d, bool pc) {
     if (e == cudaSuccess) e = hv_pass(ctx, ctx->p, nullptr, d, &ctx->S->cg_done, true);
     if (e == cudaSuccess)
         e = cgv_q(ctx->dbl, ctx->Pbuf, ctx->plan_hv.grid, ctx->ldp, ctx->n, ctx->p, ctx->q, ctx->U, sk,
-                  ctx->sc.part, ctx->S, ctx->cap_stream);
+                  ctx->sc.part, ctx->S, nullptr, ctx->cap_stream);
     if (e == cudaSuccess)
         e = cgv_iter(ctx->dbl, ctx->cgv, ctx->n, ctx->q, ctx->r, ctx->delta, ctx->p, ctx->U, sk, ctx->lam,
-                     ctx->S, ctx->sc.part, (unsigned long long)h, 1, 1, ctx->cap_stream);
+                     ctx->S, ctx->sc.part, (unsigned long long)h, 1, 1, nullptr, ctx->cap_stream);
     cudaGraph_t captured = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &captured);
     ctx->stream = saved;
@@ -632,9 +633,10 @@ static genios_status cg_loop(genios_ctx* ctx, const void* d, int* iters, std::ve
         }
         CK(hv_pass(ctx, ctx->p, nullptr, d, &ctx->S->cg_done));
         if (prof) CK(cudaEventRecord(ctx->evs[1], s));
-        CK(cgv_q(ctx->dbl, ctx->Pbuf, G, ctx->ldp, ctx->n, ctx->p, ctx->q, ctx->U, sk, ctx->sc.part, ctx->S, s));
+        CK(cgv_q(ctx->dbl, ctx->Pbuf, G, ctx->ldp, ctx->n, ctx->p, ctx->q, ctx->U, sk, ctx->sc.part, ctx->S,
+                 nullptr, s));
         CK(cgv_iter(ctx->dbl, ctx->cgv, ctx->n, ctx->q, ctx->r, ctx->delta, ctx->p, ctx->U, sk, ctx->lam,
-                    ctx->S, ctx->sc.part, 0ull, 0, 0, s));
+                    ctx->S, ctx->sc.part, 0ull, 0, 0, nullptr, s));
         ctx->launches += 3;
         genios_status st = read_state(ctx);
         if (st != GENIOS_OK) return st;
@@ -835,7 +837,7 @@ extern "C" genios_status genios_solve(genios_ctx* ctx, const double* lambda1, co
         // ---- x-step rhs, CG
         CK(cgv_start(ctx->dbl, ctx->cgv, n, ctx->g, ctx->x, ctx->z, ctx->u, rho, u_scale, nu, tol,
                      o.max_cg_iter, ctx->r, ctx->delta, ctx->p, ctx->U,
-                     use_pc && ctx->have_precond ? ctx->sk : 0, ctx->lam, ctx->S, ctx->sc.part, s));
+                     use_pc && ctx->have_precond ? ctx->sk : 0, ctx->lam, ctx->S, ctx->sc.part, nullptr, s));
         ctx->launches++;
         int cgit = 0;
         st = cg_loop(ctx, dvec, &cgit, &hv_ms);
@@ -887,12 +889,180 @@ extern "C" genios_status genios_solve(genios_ctx* ctx, const double* lambda1, co
     return (genios_status)inf.status;
 }
 
+// t = A v through the gradient-pass kernel with the squared loss and b = 0 (its l' is t itself);
+// streams the accurate copy of A (float64 / float32 / bf16 hi + lo).
+static cudaError_t av_pass(genios_ctx* ctx, const void* v, void* t_out, const void* zero_m) {
+    RowpassArgs a{};
+    a.prec = ctx->gprec;
+    a.mode = RP_GRAD;
+    a.loss = LOSS_SQUARED;
+    a.m = ctx->m;
+    a.n = ctx->n;
+    a.lda = ctx->lda_g;
+    a.A = ctx->A_g;
+    a.A_lo = ctx->A_glo;
+    a.v = v;
+    a.b = zero_m;
+    a.W_out = t_out;
+    a.D_out = nullptr;
+    a.partial = ctx->Pbuf;
+    a.ldp = ctx->ldp;
+    a.loss_part = ctx->loss_part;
+    a.wait_limit = wait_cycles(ctx);
+    a.dbg = ctx->dbg;
+    a.smem_bytes = (long long)ctx->plan_g.smem;
+    a.partial_len = (long long)ctx->plan_g.grid * ctx->ldp;
+    ctx->launches++;
+    return rowpass_launch(a, ctx->plan_g, ctx->stream);
+}
+
+// Implicit gradient of a scalar loss L(z*) (the paper does not differentiate its solution map;
+// this differentiates the optimality conditions of App. A, Eq. (19), on the support S of z):
+//   (A_S^T D A_S + lambda_2 I) q_S = dL/dz_S      (D = l''(A z - b)),
+// solved with the same fused Hv and Nystrom-preconditioned CG restricted to S, then
+//   dL/dlambda_1 = -q^T sign(z),  dL/db = D A q,  dL/dA = -(l'(A z - b) q^T + (D A q) z^T).
 extern "C" genios_status genios_grad(genios_ctx* ctx, const void* dL_dx, double* dL_dlambda1,
                                      void* dL_db, void* dL_dA) {
-    if (!ctx) return GENIOS_EINVAL;
-    (void)dL_dx; (void)dL_dlambda1; (void)dL_db; (void)dL_dA;
+    if (!ctx || !dL_dx) return GENIOS_EINVAL;
     if (!ctx->solved) FAIL(GENIOS_ESTATE, "grad before a solve");
-    FAIL(GENIOS_EUNSUPPORTED, "implicit gradient not built yet");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    const int64_t m = ctx->m, n = ctx->n;
+    const size_t vt = ctx->vt;
+    std::vector<void*> tmp;
+    auto take = [&](void** p, size_t bytes) -> cudaError_t {
+        cudaError_t e = ctx->mem.get(p, bytes);
+        if (e == cudaSuccess) tmp.push_back(*p);
+        return e;
+    };
+    auto release = [&]() {
+        cudaStreamSynchronize(s);
+        for (void* p : tmp) ctx->mem.release(p);
+        tmp.clear();
+    };
+    genios_status result = GENIOS_OK;
+    do {
+        // dL/dz (float64) on the device
+        const double* g = static_cast<const double*>(dL_dx);
+        if (!is_device_ptr(dL_dx)) {
+            void* gd = nullptr;
+            if (take(&gd, (size_t)n * 8) != cudaSuccess ||
+                cudaMemcpyAsync(gd, dL_dx, (size_t)n * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+                result = GENIOS_ECUDA;
+                break;
+            }
+            g = static_cast<const double*>(gd);
+        }
+        void *zero_n = nullptr, *zero_m = nullptr, *t = nullptr, *dlam = nullptr;
+        if (take(&zero_n, (size_t)n * vt) != cudaSuccess || take(&zero_m, (size_t)m * vt) != cudaSuccess ||
+            take(&t, (size_t)m * vt) != cudaSuccess || take(&dlam, 64) != cudaSuccess) {
+            result = GENIOS_ENOMEM;
+            break;
+        }
+        cudaMemsetAsync(zero_n, 0, (size_t)n * vt, s);
+        cudaMemsetAsync(zero_m, 0, (size_t)m * vt, s);
+        // l'(t) and D = l''(t) at the solution z (t = A z - b)
+        if (grad_pass(ctx, ctx->z, ctx->W, ctx->D) != cudaSuccess ||
+            adj_rhs(ctx->dbl, n, g, ctx->z, ctx->zc, s) != cudaSuccess) {
+            result = GENIOS_ECUDA;
+            break;
+        }
+        // preconditioner: the last sketch's U, lam restricted to S, shift lambda_2; used only
+        // when lam_s + lambda_2 > 0 (Eq. (10) is singular otherwise)
+        int sk = 0;
+        if (ctx->sk > 0 && ctx->have_precond) {
+            double ls = 0.0;
+            if (cudaMemcpyAsync(&ls, ctx->lam + ctx->sk - 1, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) {
+                result = GENIOS_ECUDA;
+                break;
+            }
+            if (ls + ctx->lam2 > 0.0) sk = ctx->sk;
+        }
+        const double tol = ctx->dbl ? 1e-12 : 1e-6;
+        const int max_it = (int)std::min<int64_t>(10000, 4 * n + 50);
+        // r = -(0 + (-1)(rhs - 0 + 0)) = rhs on S
+        if (cgv_start(ctx->dbl, ctx->cgv, n, zero_n, ctx->zc, zero_n, zero_n, -1.0, 1.0, ctx->lam2, tol, max_it,
+                      ctx->r, ctx->delta, ctx->p, ctx->U, sk, ctx->lam, ctx->S, ctx->sc.part, ctx->z, s) !=
+            cudaSuccess) {
+            result = GENIOS_ECUDA;
+            break;
+        }
+        genios_status st = read_state(ctx);
+        if (st != GENIOS_OK) {
+            result = st;
+            break;
+        }
+        const int G = ctx->plan_hv.grid;
+        int it = 0;
+        while (!ctx->Sh->cg_done && it < max_it + 2) {
+            if (hv_pass(ctx, ctx->p, nullptr, ctx->D, &ctx->S->cg_done) != cudaSuccess ||
+                cgv_q(ctx->dbl, ctx->Pbuf, G, ctx->ldp, n, ctx->p, ctx->q, ctx->U, sk, ctx->sc.part, ctx->S,
+                      ctx->z, s) != cudaSuccess ||
+                cgv_iter(ctx->dbl, ctx->cgv, n, ctx->q, ctx->r, ctx->delta, ctx->p, ctx->U, sk, ctx->lam, ctx->S,
+                         ctx->sc.part, 0ull, 0, 0, ctx->z, s) != cudaSuccess) {
+                result = GENIOS_ECUDA;
+                break;
+            }
+            ctx->launches += 3;
+            st = read_state(ctx);
+            if (st != GENIOS_OK) {
+                result = st;
+                break;
+            }
+            ++it;
+        }
+        if (result != GENIOS_OK) break;
+        const bool converged = ctx->Sh->rr <= tol * tol * ctx->Sh->rhs2 || ctx->Sh->rhs2 == 0.0;
+        // t = A q, then the outputs
+        if (av_pass(ctx, ctx->delta, t, zero_m) != cudaSuccess) {
+            result = GENIOS_ECUDA;
+            break;
+        }
+        double* db = nullptr;
+        double* dA = nullptr;
+        const bool db_dev = dL_db && is_device_ptr(dL_db);
+        const bool dA_dev = dL_dA && is_device_ptr(dL_dA);
+        if (dL_db) {
+            if (db_dev) db = static_cast<double*>(dL_db);
+            else if (take((void**)&db, (size_t)m * 8) != cudaSuccess) { result = GENIOS_ENOMEM; break; }
+        }
+        if (dL_dA) {
+            if (dA_dev) dA = static_cast<double*>(dL_dA);
+            else if (take((void**)&dA, (size_t)m * n * 8) != cudaSuccess) { result = GENIOS_ENOMEM; break; }
+        }
+        if (adj_outputs(ctx->dbl, m, n, ctx->delta, ctx->z, t, ctx->D, ctx->W, static_cast<double*>(dlam), db,
+                        dA, n, s) != cudaSuccess) {
+            result = GENIOS_ECUDA;
+            break;
+        }
+        ctx->launches += 1 + (db ? 1 : 0) + (dA ? 1 : 0);
+        if (dL_dlambda1 && cudaMemcpyAsync(dL_dlambda1, dlam, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+            result = GENIOS_ECUDA;
+            break;
+        }
+        if (dL_db && !db_dev && cudaMemcpyAsync(dL_db, db, (size_t)m * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+            result = GENIOS_ECUDA;
+            break;
+        }
+        if (dL_dA && !dA_dev &&
+            cudaMemcpyAsync(dL_dA, dA, (size_t)m * n * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+            result = GENIOS_ECUDA;
+            break;
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            result = GENIOS_ECUDA;
+            break;
+        }
+        ctx->grad_cg_iters = it;
+        if (!converged) {
+            result = GENIOS_EMAXITER;
+            ctx->err = "implicit gradient: the adjoint CG did not reach its tolerance";
+        }
+    } while (false);
+    release();
+    if (result == GENIOS_ECUDA && ctx->err.empty()) ctx->err = "implicit gradient: CUDA error";
+    return result;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1230,7 +1400,8 @@ extern "C" genios_status genios_op_pcg(int precision, int64_t m, int64_t n, cons
             break;
         }
         cudaError_t e = cgv_start(ctx->dbl, ctx->cgv, n, ctx->g, r, ctx->g, ctx->g, -1.0, 1.0, nu, rtol,
-                                  max_iter, ctx->r, delta_out, ctx->p, U, s, lam, ctx->S, ctx->sc.part, st);
+                                  max_iter, ctx->r, delta_out, ctx->p, U, s, lam, ctx->S, ctx->sc.part, nullptr,
+                                  st);
         if (e != cudaSuccess) {
             result = op_err(e);
             break;

@@ -123,19 +123,21 @@ CgvPlan cgv_plan(bool dbl, int64_t n, int sk);
 // Per-block partials (cgv_blocks(n) blocks of 32 rows, 129 doubles each) live in `part`.
 int cgv_blocks(int64_t n);
 // q = sum_b P[b] + nu p; per-block partials of p^T q and U^T q.
+// mask (value type, may be NULL): restricts the operator and the preconditioner to the entries
+// where mask != 0 (the support, for the implicit gradient)
 cudaError_t cgv_q(bool dbl, const void* P, int G, int64_t ldp, int64_t n, const void* p, void* q,
-                  const void* U, int sk, double* part, const DevState* S, cudaStream_t s);
+                  const void* U, int sk, double* part, const DevState* S, const void* mask, cudaStream_t s);
 // Start of a CG solve on the step-form right-hand side r = -(g + rho (x - z + u_scale u))
 // (u <- u_scale u, delta = 0, p = P^{-1} r, DevState scalars set): three launches.
 cudaError_t cgv_start(bool dbl, const CgvPlan& pl, int64_t n, const void* g, const void* x, const void* z,
                       void* u, double rho, double u_scale, double nu, double tol, int cg_max, void* r,
                       void* delta, void* p, const void* U, int sk, const double* lam, DevState* S,
-                      double* part, cudaStream_t s);
+                      double* part, const void* mask, cudaStream_t s);
 // One CG iteration after cgv_q: the cluster step (scalars, stop test, graph condition when
 // use_cond) and the new direction (two launches).
 cudaError_t cgv_iter(bool dbl, const CgvPlan& pl, int64_t n, const void* q, void* r, void* delta, void* p,
                      const void* U, int sk, const double* lam, DevState* S, double* part,
-                     unsigned long long cond, int use_cond, int timed, cudaStream_t s);
+                     unsigned long long cond, int use_cond, int timed, const void* mask, cudaStream_t s);
 // x-step right-hand side and CG initialisation:
 //   u *= u_scale; r = -(g + rho (x - z + u)); delta = 0; p = 0; rhs2; U^T r
 cudaError_t rhs_init(bool dbl, int64_t n, const void* g, const void* x, const void* z, void* u,
@@ -234,5 +236,13 @@ cudaError_t nystrom_build(int prec, int64_t m, int64_t n, int sk, const void* A,
                           const float* row_scale, const void* d, const void* Om, void* U,
                           double* lam, double* eta_out, NysWork w, int* chol_ok, int flags,
                           const TcSketch* tc, cudaStream_t s);
+
+// implicit gradient: r = g on the support of z (z_j != 0), 0 elsewhere
+cudaError_t adj_rhs(bool dbl, int64_t n, const double* g, const void* z, void* r, cudaStream_t s);
+// dlam (device double) = -q^T sign(z); db (m doubles) = D t; dA (m x n doubles, row stride ld_dA)
+// = -(l1 q^T + (D t) z^T).  Any output may be NULL.
+cudaError_t adj_outputs(bool dbl, int64_t m, int64_t n, const void* q, const void* z, const void* t,
+                        const void* D, const void* l1, double* dlam, double* db, double* dA, int64_t ld_dA,
+                        cudaStream_t s);
 
 }  // namespace genios

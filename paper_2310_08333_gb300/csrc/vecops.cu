@@ -347,6 +347,47 @@ __global__ void convert_kernel(int64_t rows, int64_t cols, const S* src, int64_t
 }
 
 // ------------------------------------------------------------------------------------------
+// implicit gradient (adjoint of the optimality conditions on the support)
+// ------------------------------------------------------------------------------------------
+// r = g restricted to the support of z (z_j != 0), from a float64 gradient
+template <typename VT>
+__global__ void adj_rhs_kernel(int64_t n, const double* g, const VT* z, VT* r) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        r[j] = z[j] != VT(0) ? (VT)g[j] : VT(0);
+}
+
+// out[0] = -sum_j q_j sign(z_j)   (one block, fixed order)
+template <typename VT>
+__global__ void adj_lambda_kernel(int64_t n, const VT* q, const VT* z, double* out) {
+    double acc = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const VT zj = z[j];
+        if (zj != VT(0)) acc -= (double)q[j] * (zj > VT(0) ? 1.0 : -1.0);
+    }
+    double v[1] = {acc};
+    block_sum<1>(v);
+    if (threadIdx.x == 0) out[0] = v[0];
+}
+
+// dL/db_i = D_i t_i with t = A q (float64 output)
+template <typename VT>
+__global__ void adj_db_kernel(int64_t m, const VT* t, const VT* D, double* out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)D[i] * (double)t[i];
+}
+
+// dL/dA = -(l'(t_z) q^T + (D A q) z^T), m x n float64 row-major with row stride ld
+template <typename VT>
+__global__ void adj_da_kernel(int64_t m, int64_t n, const VT* l1, const VT* q, const VT* D, const VT* t,
+                              const VT* z, double* out, int64_t ld) {
+    const int64_t total = m * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / n, j = e % n;
+        out[i * ld + j] = -((double)l1[i] * (double)q[j] + (double)D[i] * (double)t[i] * (double)z[j]);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------------------------
 static int grid_for(int64_t n, int per, int cap = 4096) {
@@ -446,4 +487,35 @@ cudaError_t fill_zero(void* p, size_t bytes, cudaStream_t s) { return cudaMemset
 }  // namespace genios
 
 namespace genios {
+cudaError_t adj_rhs(bool dbl, int64_t n, const double* g, const void* z, void* r, cudaStream_t s) {
+    const int grid = grid_for(n, VT_THREADS, 1024);
+    if (dbl) adj_rhs_kernel<double><<<grid, VT_THREADS, 0, s>>>(n, g, CC<double>(z), C<double>(r));
+    else adj_rhs_kernel<float><<<grid, VT_THREADS, 0, s>>>(n, g, CC<float>(z), C<float>(r));
+    return cudaGetLastError();
+}
+
+cudaError_t adj_outputs(bool dbl, int64_t m, int64_t n, const void* q, const void* z, const void* t,
+                        const void* D, const void* l1, double* dlam, double* db, double* dA, int64_t ld_dA,
+                        cudaStream_t s) {
+    if (dlam) {
+        if (dbl) adj_lambda_kernel<double><<<1, 1024, 0, s>>>(n, CC<double>(q), CC<double>(z), dlam);
+        else adj_lambda_kernel<float><<<1, 1024, 0, s>>>(n, CC<float>(q), CC<float>(z), dlam);
+    }
+    const int gm = grid_for(m, VT_THREADS, 2048);
+    if (db) {
+        if (dbl) adj_db_kernel<double><<<gm, VT_THREADS, 0, s>>>(m, CC<double>(t), CC<double>(D), db);
+        else adj_db_kernel<float><<<gm, VT_THREADS, 0, s>>>(m, CC<float>(t), CC<float>(D), db);
+    }
+    if (dA) {
+        const int ga = grid_for(m * n, VT_THREADS, 8192);
+        if (dbl)
+            adj_da_kernel<double><<<ga, VT_THREADS, 0, s>>>(m, n, CC<double>(l1), CC<double>(q), CC<double>(D),
+                                                            CC<double>(t), CC<double>(z), dA, ld_dA);
+        else
+            adj_da_kernel<float><<<ga, VT_THREADS, 0, s>>>(m, n, CC<float>(l1), CC<float>(q), CC<float>(D),
+                                                           CC<float>(t), CC<float>(z), dA, ld_dA);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace genios

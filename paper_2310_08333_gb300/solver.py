@@ -89,6 +89,19 @@ class Solver:
         d["status_name"] = L.STATUS_NAMES[d["status"]]
         return out, d
 
+    def grad(self, dL_dz, want_db: bool = True, want_dA: bool = False):
+        """Implicit gradient at the last solve for a scalar loss with gradient dL_dz (n) w.r.t.
+        the solution.  Returns dict(dL_dlambda1, dL_db (m) or None, dL_dA (m x n) or None, status)."""
+        g = np.ascontiguousarray(np.asarray(dL_dz, dtype=np.float64).reshape(-1))
+        if g.size != self.n:
+            raise ValueError("dL_dz must have n entries")
+        dlam = C.c_double()
+        db = np.empty(self.m, dtype=np.float64) if want_db else None
+        dA = np.empty((self.m, self.n), dtype=np.float64) if want_dA else None
+        st = self._lib.genios_grad(self._ctx, _ptr(g), C.byref(dlam), _ptr(db), _ptr(dA))
+        L.check(st, self._ctx)
+        return {"dL_dlambda1": dlam.value, "dL_db": db, "dL_dA": dA, "status": L.STATUS_NAMES[st]}
+
     def last_error(self) -> str:
         return self._lib.genios_last_error(self._ctx).decode()
 
