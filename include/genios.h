@@ -152,13 +152,15 @@ genios_status genios_create(const genios_options* opts, int device, void* stream
 
 /* Load problem data (copied; the caller keeps ownership of its buffers).
  *   loss:     genios_loss.
- *   K:        number of problems; this build supports K = 1.
- *   m, n:     arrays of K sizes (m >= 1, n >= 1).
- *   A:        array of K pointers to row-major m x n matrices with leading dimension lda[k],
+ *   K:        number of problems (>= 1).
+ *   m, n:     arrays of sizes (m >= 1, n >= 1), one per data set.
+ *   A:        array of pointers to row-major m x n matrices with leading dimension lda[k],
  *             host or device memory (detected), element type A_dtype (F64 or F32).
- *   b:        array of K pointers to m-vectors of the same element type and memory kind.
- *   shared_A: reserved (0).
- * Builds the precision copies of A requested by opts.precision. */
+ *   b:        array of pointers to m-vectors of the same element type and memory kind.
+ *   shared_A: 1: one data set (m[0], n[0], A[0], b[0], lda[0]) shared by the K problems, which
+ *             differ only in (lambda_1, lambda_2): a regularisation path.  0: K independent data
+ *             sets of their own sizes (arrays of K entries).
+ * Builds the precision copies of A requested by opts.precision (per data set). */
 genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const int64_t* m, const int64_t* n,
                               const void* const* A, int A_dtype, const int64_t* lda,
                               const void* const* b, int shared_A);
@@ -168,10 +170,13 @@ genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const int64_t* m
 genios_status genios_lambda_max(genios_ctx* ctx, double* out);
 
 /* Solve.  lambda1, lambda2: host arrays of K doubles (>= 0).  x_out: caller-owned buffer of
- * K * n elements of out_dtype (F64 or F32), host or device; receives z (exact zeros off the
+ * out_dtype (F64 or F32), host or device, receiving the K solutions z back to back (K * n
+ * elements for a shared data set, sum of n_k for independent ones; exact zeros off the
  * support).  info: host array of K structs or NULL.  warm_start: 1 reuses x, z, u, rho of the
- * previous solve on this context.  Returns GENIOS_OK when the stop rule was met,
- * GENIOS_EMAXITER (iterate still written) otherwise. */
+ * previous solve on this context.  A shared data set solves its K problems in the order given,
+ * each started from the previous solution (pass lambda_1 decreasing for a path) and sharing the
+ * Nystrom sketch when loss'' is constant.  Returns GENIOS_OK when every problem met the stop
+ * rule, GENIOS_EMAXITER (iterates still written) if one did not. */
 genios_status genios_solve(genios_ctx* ctx, const double* lambda1, const double* lambda2,
                            void* x_out, int out_dtype, genios_info* info, int warm_start);
 
@@ -180,7 +185,10 @@ genios_status genios_solve(genios_ctx* ctx, const double* lambda1, const double*
  *   dL_dx:       n gradient of a scalar loss w.r.t. the solution (float64, host or device).
  *   dL_dlambda1: host double or NULL.
  *   dL_db:       m float64 output (host or device) or NULL.
- *   dL_dA:       m x n float64 output, row-major (host or device) or NULL. */
+ *   dL_dA:       m x n float64 output, row-major (host or device) or NULL.
+ * Contexts holding a batch (K > 1) return GENIOS_EUNSUPPORTED: differentiate each problem in a
+ * K = 1 context.  Returns GENIOS_EMAXITER if the adjoint CG did not reach its tolerance (outputs
+ * still written). */
 genios_status genios_grad(genios_ctx* ctx, const void* dL_dx, double* dL_dlambda1, void* dL_db,
                           void* dL_dA);
 

@@ -68,6 +68,10 @@ struct genios_ctx {
     genios_options opt;
     int device = 0;
     cudaStream_t stream = nullptr;
+    // batches (K > 1): a lambda path on one data set (shared) or one sub-context per problem
+    int K = 1;
+    bool shared = false;
+    std::vector<genios_ctx*> subs;
     std::string err = "no error";
     Alloc mem;
     // problem
@@ -232,6 +236,8 @@ extern "C" genios_status genios_create(const genios_options* opts, int device, v
 
 extern "C" void genios_destroy(genios_ctx* ctx) {
     if (!ctx) return;
+    for (genios_ctx* c : ctx->subs) genios_destroy(c);
+    ctx->subs.clear();
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
@@ -309,16 +315,12 @@ static cudaError_t tc_setup(genios_ctx* ctx, int src_prec, const void* A, int64_
     return cudaSuccess;
 }
 
-extern "C" genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const int64_t* m,
-                                         const int64_t* n, const void* const* A, int A_dtype,
-                                         const int64_t* lda, const void* const* b, int shared_A) {
-    if (!ctx) return GENIOS_EINVAL;
-    if (K != 1) FAIL(GENIOS_EUNSUPPORTED, "this build supports K = 1 problem per context");
+static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, const int64_t* n,
+                                  const void* const* A, int A_dtype, const int64_t* lda, const void* const* b) {
     if (!m || !n || !A || !lda || !b || !A[0] || !b[0]) FAIL(GENIOS_EINVAL, "NULL argument");
     if (m[0] < 1 || n[0] < 1 || lda[0] < n[0]) FAIL(GENIOS_EINVAL, "bad sizes");
     if (loss != GENIOS_LOSS_SQUARED && loss != GENIOS_LOSS_LOGISTIC) FAIL(GENIOS_EINVAL, "bad loss");
     if (A_dtype != GENIOS_DT_F64 && A_dtype != GENIOS_DT_F32) FAIL(GENIOS_EINVAL, "A_dtype must be F64 or F32");
-    (void)shared_A;
     CK(cudaSetDevice(ctx->device));
     const double t0 = now_ms();
     cudaStream_t s = ctx->stream;
@@ -669,7 +671,7 @@ static double cg_floor(const genios_ctx* ctx) {
     return std::max(res, std::min(1e-3, 10.0 * eps));
 }
 
-extern "C" genios_status genios_lambda_max(genios_ctx* ctx, double* out) {
+static genios_status lambda_max_one(genios_ctx* ctx, double* out) {
     if (!ctx || !out) return GENIOS_EINVAL;
     if (!ctx->has_data) FAIL(GENIOS_ESTATE, "lambda_max before set_data");
     CK(cudaSetDevice(ctx->device));
@@ -685,8 +687,8 @@ extern "C" genios_status genios_lambda_max(genios_ctx* ctx, double* out) {
     return GENIOS_OK;
 }
 
-extern "C" genios_status genios_solve(genios_ctx* ctx, const double* lambda1, const double* lambda2,
-                                      void* x_out, int out_dtype, genios_info* info, int warm_start) {
+static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const double* lambda2,
+                               void* x_out, int out_dtype, genios_info* info, int warm_start) {
     if (!ctx) return GENIOS_EINVAL;
     if (!ctx->has_data) FAIL(GENIOS_ESTATE, "solve before set_data");
     if (!lambda1 || !lambda2 || !x_out) FAIL(GENIOS_EINVAL, "NULL argument");
@@ -889,6 +891,97 @@ extern "C" genios_status genios_solve(genios_ctx* ctx, const double* lambda1, co
     return (genios_status)inf.status;
 }
 
+// ------------------------------------------------------------------------------------------
+// batches: K problems per context
+// ------------------------------------------------------------------------------------------
+static void drop_subs(genios_ctx* ctx) {
+    for (genios_ctx* c : ctx->subs) genios_destroy(c);
+    ctx->subs.clear();
+}
+
+extern "C" genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const int64_t* m,
+                                         const int64_t* n, const void* const* A, int A_dtype,
+                                         const int64_t* lda, const void* const* b, int shared_A) {
+    if (!ctx) return GENIOS_EINVAL;
+    if (K < 1) FAIL(GENIOS_EINVAL, "K must be >= 1");
+    if (!m || !n || !A || !lda || !b) FAIL(GENIOS_EINVAL, "NULL argument");
+    drop_subs(ctx);
+    ctx->K = 1;
+    ctx->shared = false;
+    if (K == 1 || shared_A) {
+        // one data set; with K > 1 the K problems share it and differ in (lambda_1, lambda_2)
+        genios_status st = set_data_one(ctx, loss, m, n, A, A_dtype, lda, b);
+        if (st == GENIOS_OK) {
+            ctx->K = K;
+            ctx->shared = K > 1;
+        }
+        return st;
+    }
+    // K independent problems: one sub-context each (same options, device and stream)
+    for (int k = 0; k < K; ++k) {
+        genios_ctx* c = nullptr;
+        genios_status st = genios_create(&ctx->opt, ctx->device, ctx->stream, &c);
+        if (st != GENIOS_OK) {
+            drop_subs(ctx);
+            FAIL(st, "batch: creating sub-context " + std::to_string(k) + ": " + g_create_error);
+        }
+        ctx->subs.push_back(c);
+        st = set_data_one(c, loss, m + k, n + k, A + k, A_dtype, lda + k, b + k);
+        if (st != GENIOS_OK) {
+            const std::string e = c->err;
+            drop_subs(ctx);
+            FAIL(st, "batch: problem " + std::to_string(k) + ": " + e);
+        }
+    }
+    ctx->K = K;
+    ctx->has_data = true;
+    ctx->solved = false;
+    return GENIOS_OK;
+}
+
+extern "C" genios_status genios_lambda_max(genios_ctx* ctx, double* out) {
+    if (!ctx || !out) return GENIOS_EINVAL;
+    if (ctx->subs.empty()) {
+        genios_status st = lambda_max_one(ctx, out);
+        for (int k = 1; k < ctx->K && st == GENIOS_OK; ++k) out[k] = out[0];
+        return st;
+    }
+    for (int k = 0; k < ctx->K; ++k) {
+        genios_status st = lambda_max_one(ctx->subs[k], out + k);
+        if (st != GENIOS_OK) FAIL(st, "batch: problem " + std::to_string(k) + ": " + ctx->subs[k]->err);
+    }
+    return GENIOS_OK;
+}
+
+// K = 1: one solve.  Shared data (lambda path): the K problems in the order given, each warm-
+// started from the previous solution (x, z, u, rho) and sharing the sketch when the loss'' is
+// constant.  Independent problems: each sub-context in turn.  x_out holds the K solutions back
+// to back (n each, or n_k for independent problems); the status is the worst of the K.
+extern "C" genios_status genios_solve(genios_ctx* ctx, const double* lambda1, const double* lambda2,
+                                      void* x_out, int out_dtype, genios_info* info, int warm_start) {
+    if (!ctx) return GENIOS_EINVAL;
+    if (ctx->K == 1 && ctx->subs.empty()) return solve_one(ctx, lambda1, lambda2, x_out, out_dtype, info, warm_start);
+    if (!ctx->has_data) FAIL(GENIOS_ESTATE, "solve before set_data");
+    if (!lambda1 || !lambda2 || !x_out) FAIL(GENIOS_EINVAL, "NULL argument");
+    if (out_dtype != GENIOS_DT_F64 && out_dtype != GENIOS_DT_F32) FAIL(GENIOS_EINVAL, "bad out_dtype");
+    const size_t es = out_dtype == GENIOS_DT_F64 ? 8 : 4;
+    char* out = static_cast<char*>(x_out);
+    genios_status worst = GENIOS_OK;
+    for (int k = 0; k < ctx->K; ++k) {
+        genios_ctx* c = ctx->subs.empty() ? ctx : ctx->subs[k];
+        const int warm = ctx->subs.empty() ? (k > 0 || warm_start) : warm_start;
+        genios_status st = solve_one(c, lambda1 + k, lambda2 + k, out, out_dtype, info ? info + k : nullptr, warm);
+        if (st != GENIOS_OK && st != GENIOS_EMAXITER) {
+            if (c != ctx) ctx->err = "batch: problem " + std::to_string(k) + ": " + c->err;
+            return st;
+        }
+        if (st == GENIOS_EMAXITER) worst = st;
+        out += (size_t)c->n * es;
+    }
+    ctx->solved = true;
+    return worst;
+}
+
 // t = A v through the gradient-pass kernel with the squared loss and b = 0 (its l' is t itself);
 // streams the accurate copy of A (float64 / float32 / bf16 hi + lo).
 static cudaError_t av_pass(genios_ctx* ctx, const void* v, void* t_out, const void* zero_m) {
@@ -924,6 +1017,8 @@ static cudaError_t av_pass(genios_ctx* ctx, const void* v, void* t_out, const vo
 extern "C" genios_status genios_grad(genios_ctx* ctx, const void* dL_dx, double* dL_dlambda1,
                                      void* dL_db, void* dL_dA) {
     if (!ctx || !dL_dx) return GENIOS_EINVAL;
+    if (ctx->K != 1 || !ctx->subs.empty())
+        FAIL(GENIOS_EUNSUPPORTED, "implicit gradient of a batch: use one K = 1 context per problem");
     if (!ctx->solved) FAIL(GENIOS_ESTATE, "grad before a solve");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = ctx->stream;

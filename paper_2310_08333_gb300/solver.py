@@ -70,6 +70,56 @@ class Solver:
         self.m, self.n = m, n
         return self
 
+    def set_batch(self, As, bs, loss: int | str = L.LOSS_SQUARED, path_size: int | None = None):
+        """Load a batch.  path_size = K: one data set (As[0], bs[0]) shared by K problems that
+        differ in lambda (a regularisation path).  Otherwise: len(As) independent problems."""
+        if isinstance(loss, str):
+            loss = {"squared": L.LOSS_SQUARED, "logistic": L.LOSS_LOGISTIC}[loss]
+        As = [np.ascontiguousarray(a) if isinstance(a, np.ndarray) else a for a in As]
+        bs = [np.ascontiguousarray(b, dtype=a.dtype) if isinstance(b, np.ndarray) else b for a, b in zip(As, bs)]
+        K = path_size if path_size is not None else len(As)
+        cnt = len(As)
+        ms = (C.c_int64 * cnt)(*[a.shape[0] for a in As])
+        ns = (C.c_int64 * cnt)(*[a.shape[1] for a in As])
+        lds = (C.c_int64 * cnt)(*[(a.stride(0) if torch is not None and isinstance(a, torch.Tensor)
+                                   else a.strides[0] // a.itemsize) for a in As])
+        Ap = (C.c_void_p * cnt)(*[_ptr(a).value for a in As])
+        bp = (C.c_void_p * cnt)(*[_ptr(b).value for b in bs])
+        st = self._lib.genios_set_data(self._ctx, loss, K, ms, ns, Ap, _dt(As[0]), lds, bp,
+                                       1 if path_size is not None else 0)
+        L.check(st, self._ctx)
+        self._keep = [As, bs]
+        self.K = K
+        self.ns = [As[0].shape[1]] * K if path_size is not None else [a.shape[1] for a in As]
+        self.m, self.n = As[0].shape
+        return self
+
+    def lambda_max_batch(self) -> np.ndarray:
+        out = (C.c_double * self.K)()
+        L.check(self._lib.genios_lambda_max(self._ctx, out), self._ctx)
+        return np.array(out[:])
+
+    def solve_batch(self, lams1, lams2=None, warm_start: bool = False):
+        """Returns (list of z arrays, list of info dicts) for the K problems of the batch."""
+        K = self.K
+        lams2 = np.zeros(K) if lams2 is None else lams2
+        l1 = (C.c_double * K)(*[float(v) for v in lams1])
+        l2 = (C.c_double * K)(*[float(v) for v in lams2])
+        out = np.empty(int(sum(self.ns)), dtype=np.float64)
+        infos = (L.Info * K)()
+        st = self._lib.genios_solve(self._ctx, l1, l2, _ptr(out), L.DT_F64, infos, int(warm_start))
+        L.check(st, self._ctx)
+        zs, o = [], 0
+        for nk in self.ns:
+            zs.append(out[o:o + nk])
+            o += nk
+        ds = []
+        for i in range(K):
+            d = infos[i].as_dict()
+            d["status_name"] = L.STATUS_NAMES[d["status"]]
+            ds.append(d)
+        return zs, ds
+
     def lambda_max(self) -> float:
         out = C.c_double()
         L.check(self._lib.genios_lambda_max(self._ctx, C.byref(out)), self._ctx)

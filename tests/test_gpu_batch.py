@@ -1,0 +1,74 @@
+"""Batches through the C ABI (K > 1): a regularisation path on one shared data set and a batch of
+independent problems of uneven sizes, each solution compared with the oracle's solve of that
+problem."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import problems  # noqa: E402
+from oracle import admm as oadmm, checks  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2310_08333_gb300 import build as b
+    b.build()
+    import paper_2310_08333_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lambda_path_matches_oracle(G, prec):
+    P = problems.lasso_iid(300, 600, nnz=30, seed=problems.seed_for(4, 1))
+    A, b = P.A, P.b
+    if prec == 1:
+        A, b = A.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)
+    lmax = checks.lambda_max(A, b, "squared")
+    lams = problems.lambda_path_fracs(8, lo=0.05) * lmax
+    dt = torch.float64 if prec == 0 else torch.float32
+    with G.Solver(precision=prec, stop_rule=G.STOP_KKT, eps_kkt=1e-10 if prec == 0 else 1e-6,
+                  sketch_rank=30, max_iter=20000) as s:
+        s.set_batch([torch.from_numpy(A).to("cuda", dt)], [torch.from_numpy(b).to("cuda", dt)], "squared",
+                    path_size=len(lams))
+        lm = s.lambda_max_batch()
+        zs, infos = s.solve_batch(lams)
+    assert np.allclose(lm, lmax, rtol=1e-6)
+    assert all(i["status"] == 0 for i in infos), [i["status_name"] for i in infos]
+    assert infos[0]["sketches"] == 1 and all(i["sketches"] == 0 for i in infos[1:])   # one sketch: D = I
+    for lam, z in zip(lams, zs):
+        ref = oadmm.solve(A, b, "squared", lam, tol=1e-13)["z"]
+        assert rel(z, ref) <= (1e-7 if prec == 0 else 5e-5), (lam, rel(z, ref))
+
+
+def test_uneven_batch_matches_oracle(G):
+    Ps = problems.uneven_batch(K=5, m_range=(100, 500), n_range=(150, 900), seed=problems.seed_for(4, 2))
+    dt = torch.float64
+    with G.Solver(precision=0, stop_rule=G.STOP_KKT, eps_kkt=1e-10, sketch_rank=20, max_iter=20000) as s:
+        s.set_batch([torch.from_numpy(P.A).to("cuda", dt) for P in Ps],
+                    [torch.from_numpy(P.b).to("cuda", dt) for P in Ps], "squared")
+        lm = s.lambda_max_batch()
+        lams = [P.lam_frac * l for P, l in zip(Ps, lm)]
+        zs, infos = s.solve_batch(lams)
+    assert all(i["status"] == 0 for i in infos)
+    for P, lam, z in zip(Ps, lams, zs):
+        assert z.shape == (P.A.shape[1],)
+        assert lam == pytest.approx(P.lam_frac * checks.lambda_max(P.A, P.b, "squared"), rel=1e-10)
+        ref = oadmm.solve(P.A, P.b, "squared", lam, tol=1e-13)["z"]
+        assert rel(z, ref) <= 1e-7
+
+
+def test_batch_grad_is_refused(G):
+    P = problems.lasso_iid(100, 200, nnz=10, seed=problems.seed_for(4, 3))
+    with G.Solver(precision=0, sketch_rank=10) as s:
+        s.set_batch([P.A], [P.b], "squared", path_size=2)
+        s.solve_batch([0.5 * s.lambda_max_batch()[0]] * 2)
+        with pytest.raises(G.GeniosError):
+            s.grad(np.ones(200))
