@@ -347,11 +347,95 @@ def run_ours(args):
             "clocks": clocks,
             "variants": variants,
         }
+        if args.extra:
+            out["configs"] = extra_configs(G, torch, args)
         print(json.dumps(out), flush=True)
     s.close()
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def extra_configs(G, torch, args) -> dict:
+    """The other workloads of the measurement plan, one timed pass each (rank 0, --extra):
+    the 1000 x 10000 AR(1) Lasso (FP32, BF16), the 32-level lambda path on a shared 5000 x 20000
+    Lasso and the 64 uneven Lasso problems (solved in one batched call each), and the
+    elastic-net logistic implicit gradient (solve + adjoint) on 8000 x 4000 problems."""
+    from oracle import losses
+    res = {}
+    sync = torch.cuda.synchronize
+
+    def tsolve(s, fn):
+        sync()
+        t0 = time.perf_counter()
+        out = fn()
+        sync()
+        return time.perf_counter() - t0, out
+
+    # cfg 2: dense Lasso at the paper's intro scale (A = 40 MB in FP32: L2-resident)
+    P = problems.lasso_ar1()
+    A = torch.from_numpy(P.A.astype(np.float32)).cuda()
+    b = torch.from_numpy(P.b.astype(np.float32)).cuda()
+    for name, prec in (("fp32", G.FP32), ("bf16", G.BF16)):
+        with G.Solver(precision=prec, stop_rule=G.STOP_KKT, eps_kkt=1e-4, sketch_rank=50, rho=1.0,
+                      max_iter=20000) as s:
+            s.set_data(A, b, "squared")
+            lam = P.lam_frac * s.lambda_max()
+            s.solve(lam)
+            el, (z, info) = tsolve(s, lambda: s.solve(lam))
+        res[f"lasso_1000x10000_{name}"] = {"time_s": el, "iters": info["iters"], "cg_iters": info["cg_iters_total"],
+                                          "status": info["status_name"], "rel_kkt": info["rel_kkt"]}
+    del A, b
+    # cfg 4a: 32-level lambda path on a shared 5000 x 20000 AR(1) Lasso
+    P = problems.lasso_ar1(5000, 20000, nnz=1000, seed=problems.seed_for(4, 0))
+    A = torch.from_numpy(P.A.astype(np.float32)).cuda()
+    b = torch.from_numpy(P.b.astype(np.float32)).cuda()
+    fr = problems.lambda_path_fracs(32)
+    with G.Solver(precision=G.FP32, stop_rule=G.STOP_KKT, eps_kkt=1e-4, sketch_rank=50, rho=1.0,
+                  max_iter=5000) as s:
+        s.set_batch([A], [b], "squared", path_size=len(fr))
+        lams = fr * s.lambda_max_batch()[0]
+        el, (zs, infos) = tsolve(s, lambda: s.solve_batch(lams))
+    res["lambda_path_32_5000x20000_fp32"] = {
+        "time_s": el, "iters": [i["iters"] for i in infos], "cg_iters": sum(i["cg_iters_total"] for i in infos),
+        "converged": sum(i["status"] == 0 for i in infos), "sketches": sum(i["sketches"] for i in infos),
+        "nnz": [i["nnz"] for i in infos], "note": "sequential warm-started solves in one genios_solve call"}
+    del A, b
+    # cfg 4b: 64 independent Lasso problems of uneven size
+    Ps = problems.uneven_batch(64)
+    As = [torch.from_numpy(Q.A.astype(np.float32)).cuda() for Q in Ps]
+    bs = [torch.from_numpy(Q.b.astype(np.float32)).cuda() for Q in Ps]
+    with G.Solver(precision=G.FP32, stop_rule=G.STOP_KKT, eps_kkt=1e-4, sketch_rank=50, rho=1.0,
+                  max_iter=5000) as s:
+        s.set_batch(As, bs, "squared")
+        lams = [Q.lam_frac * l for Q, l in zip(Ps, s.lambda_max_batch())]
+        el, (zs, infos) = tsolve(s, lambda: s.solve_batch(lams))
+    res["uneven_batch_64_fp32"] = {
+        "time_s": el, "converged": sum(i["status"] == 0 for i in infos),
+        "total_bytes_A": int(sum(Q.A.size for Q in Ps) * 4), "iters_total": sum(i["iters"] for i in infos),
+        "note": "one genios_solve call, problems solved in turn"}
+    del As, bs
+    # cfg 5: elastic-net logistic, solve + implicit gradient of the validation loss
+    mu = 1e-3
+    ts, tg, cg = [], [], []
+    for k in range(args.cfg5_problems):
+        P = problems.logistic_lowrank(10000, 4000, nnz=200, mu=mu, seed=problems.seed_for(5, k))
+        A = torch.from_numpy(P.A[:8000].astype(np.float32)).cuda()
+        b = torch.from_numpy(P.b[:8000].astype(np.float32)).cuda()
+        Av = P.A[8000:].astype(np.float32).astype(np.float64)
+        with G.Solver(precision=G.FP32, stop_rule=G.STOP_KKT, eps_kkt=1e-4, sketch_rank=100, rho=30.0,
+                      max_iter=20000) as s:
+            s.set_data(A, b, "logistic")
+            lam = 0.01 * s.lambda_max()
+            el, (z, info) = tsolve(s, lambda: s.solve(lam, mu))
+            g = Av.T @ losses.get("logistic").d1(Av @ z)
+            eg, out = tsolve(s, lambda: s.grad(g))
+        ts.append(el)
+        tg.append(eg)
+    res["implicit_grad_8000x4000_fp32"] = {"problems": args.cfg5_problems, "solve_s_mean": float(np.mean(ts)),
+                                           "grad_s_mean": float(np.mean(tg)),
+                                           "note": "grad = adjoint PCG on the support + outputs (dL/dlambda, dL/db)"}
+    return res
 
 
 def run_reference(args):
@@ -399,6 +483,8 @@ def main():
     ap.add_argument("--variant-list", default="bf16,fp8")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--extra", action="store_true", help="also time the other workloads (configs 2, 4, 5)")
+    ap.add_argument("--cfg5-problems", type=int, default=4)
     ap.add_argument("--no-event-leg", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
