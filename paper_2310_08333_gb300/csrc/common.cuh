@@ -99,6 +99,29 @@ GENIOS_DEV void decode_chunk(const uint4& c, float (&f)[16]) {
     fp8x4_to_float(c.z, f + 8); fp8x4_to_float(c.w, f + 12);
 }
 
+// Packed float32 pairs (sm_100 family): two IEEE float32 FMAs / adds per instruction on a
+// 64-bit register pair.  Packing adjacent values lets the compiler keep them in a register pair.
+GENIOS_DEV uint64_t f2pack(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+GENIOS_DEV float2 f2unpack(uint64_t r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+GENIOS_DEV uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+GENIOS_DEV uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // ------------------------------------------------------------------------------------------
 // PTX: shared-memory addresses, mbarriers, bulk async copies (sm_90+)
 // ------------------------------------------------------------------------------------------

@@ -49,6 +49,7 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
     constexpr int RB = rp_rb(P, NCH);
     constexpr bool HOLD = (NCH * RB <= 8);
     constexpr int SPLIT = HILO ? 2 : 1;
+    constexpr bool PK = sizeof(VT) == 4 && !HILO;   // float32 lanes: packed f32x2 FMAs
 
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x;
@@ -158,9 +159,11 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
             uint4 hold[HOLD ? RB : 1][HOLD ? NCH : 1];
             uint4 holdlo[(HOLD && HILO) ? RB : 1][(HOLD && HILO) ? NCH : 1];
             VT dot[RB];
+            uint64_t dot2[RB];
 #pragma unroll
             for (int q = 0; q < RB; ++q) {
                 dot[q] = VT(0);
+                dot2[q] = 0ull;   // +0.0f, +0.0f
                 if (rr + q < rows) {
                     const unsigned char* rowp = sb + (size_t)(rr + q) * row_bytes;
 #pragma unroll
@@ -180,10 +183,20 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
                                 if constexpr (HOLD) holdlo[q][k] = rl;
                             }
                             if constexpr (HOLD) hold[q][k] = raw;
+                            if constexpr (PK) {
 #pragma unroll
-                            for (int e = 0; e < VEC; ++e) dot[q] = fma(f[e], vr[k][e], dot[q]);
+                                for (int e = 0; e < VEC; e += 2)
+                                    dot2[q] = fma2(f2pack(f[e], f[e + 1]), f2pack(vr[k][e], vr[k][e + 1]), dot2[q]);
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < VEC; ++e) dot[q] = fma(f[e], vr[k][e], dot[q]);
+                            }
                         }
                     }
+                }
+                if constexpr (PK) {
+                    const float2 d2 = f2unpack(dot2[q]);
+                    dot[q] = d2.x + d2.y;
                 }
             }
 #pragma unroll
@@ -247,8 +260,19 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
 #pragma unroll
                                 for (int e = 0; e < VEC; ++e) f[e] += g[e];
                             }
+                            if constexpr (PK) {
+                                const uint64_t w2 = f2pack(wq[q], wq[q]);
 #pragma unroll
-                            for (int e = 0; e < VEC; ++e) yr[k][e] = fma(wq[q], f[e], yr[k][e]);
+                                for (int e = 0; e < VEC; e += 2) {
+                                    const float2 y2 = f2unpack(fma2(w2, f2pack(f[e], f[e + 1]),
+                                                                    f2pack(yr[k][e], yr[k][e + 1])));
+                                    yr[k][e] = y2.x;
+                                    yr[k][e + 1] = y2.y;
+                                }
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < VEC; ++e) yr[k][e] = fma(wq[q], f[e], yr[k][e]);
+                            }
                         }
                     }
                 }
