@@ -10,3 +10,7 @@ from ._lib import (  # noqa: F401
     GeniosError, Info, Options, default_options, lib,
 )
 from .solver import Solver, ops  # noqa: F401
+try:
+    from .solver import solve_differentiable  # noqa: F401
+except ImportError:  # pragma: no cover - torch absent
+    pass

@@ -330,3 +330,40 @@ def pcg(prec, A, n, d, nu, r, U=None, lam=None, rtol=1e-6, max_iter=100, row_sca
 ops = SimpleNamespace(lda=lda, pad=pad, hv=hv, hv_noalloc=hv_noalloc, gradient=gradient, zu_update=zu_update, nystrom=nystrom,
                       nystrom_workspace=nystrom_workspace, sketch=sketch,
                       precond=precond, omega=omega, philox=philox, quantize=quantize, pcg=pcg)
+
+
+# ----------------------------------------------------------------------------------------
+# differentiable solve (torch autograd over genios_solve / genios_grad)
+# ----------------------------------------------------------------------------------------
+if torch is not None:
+    class _SolveFn(torch.autograd.Function):
+        """z*(lambda_1, b, A) with the implicit gradient of genios_grad in backward."""
+
+        @staticmethod
+        def forward(fctx, A, b, lam1, lam2, loss, options):
+            s = Solver(options)
+            s.set_data(A.detach(), b.detach(), loss)
+            z, info = s.solve(float(lam1), float(lam2))
+            fctx.solver = s
+            fctx.info = info
+            fctx.needs = (A.requires_grad, b.requires_grad, torch.is_tensor(lam1) and lam1.requires_grad)
+            return torch.as_tensor(z, dtype=A.dtype, device=A.device)
+
+        @staticmethod
+        def backward(fctx, gz):
+            s = fctx.solver
+            need_A, need_b, need_lam = fctx.needs
+            out = s.grad(gz.detach().double().cpu().numpy(), want_db=need_b, want_dA=need_A)
+            s.close()
+            dev, dt = gz.device, gz.dtype
+            dA = torch.as_tensor(out["dL_dA"], dtype=dt, device=dev) if need_A else None
+            db = torch.as_tensor(out["dL_db"], dtype=dt, device=dev) if need_b else None
+            dlam = torch.tensor(out["dL_dlambda1"], dtype=dt, device=dev) if need_lam else None
+            return dA, db, dlam, None, None, None
+
+    def solve_differentiable(A, b, lam1, lam2: float = 0.0, loss: str = "squared", **opts):
+        """Solution z of  min sum_i loss(a_i^T x - b_i) + lam1 ||x||_1 + lam2/2 ||x||^2  as a torch
+        tensor that carries gradients to lam1 (0-d tensor), b and A through the implicit
+        gradient at the solution (genios_grad).  opts: genios_options fields."""
+        options = L.default_options(**opts)
+        return _SolveFn.apply(A, b, lam1, lam2, loss, options)

@@ -135,3 +135,26 @@ def test_config5_shape_fp32(G):
     ref = implicit.adjoint(A, b, z, "logistic", lam, mu, g, thresh=0.0)
     assert abs(out["dL_dlambda1"] - ref["dL_dlambda1"]) <= 1e-3 * abs(ref["dL_dlambda1"])
     np.testing.assert_allclose(out["dL_db"], ref["dL_db"], atol=1e-3 * np.abs(ref["dL_db"]).max())
+
+
+def test_autograd_function_matches_grad_and_fd(G):
+    """torch autograd through the solve: d(w^T z)/d(lambda, b) equals genios_grad's values and
+    a central difference in lambda."""
+    P = problems.logistic_lowrank(800, 200, rank=8, nnz=12, mu=1e-3, seed=problems.seed_for(5, 6))
+    mu = 1e-3
+    A = torch.from_numpy(P.A).cuda()
+    b = torch.from_numpy(P.b).cuda().requires_grad_(True)
+    lmax = checks.lambda_max(P.A, P.b, "logistic")
+    lam = torch.tensor(0.05 * lmax, dtype=torch.float64, requires_grad=True)
+    w = torch.from_numpy(np.random.default_rng(44).standard_normal(200)).cuda()
+    opts = dict(precision=0, stop_rule=G.STOP_KKT, eps_kkt=1e-11, rho=10.0, sketch_rank=20, max_iter=20000)
+    z = G.solve_differentiable(A, b, lam, mu, "logistic", **opts)
+    (w * z).sum().backward()
+    g = w.cpu().numpy()
+    _, _, ref = solve_and_grad(G, P.A, P.b, "logistic", float(lam), mu, 0, g, rho=10.0, sketch_rank=20)
+    assert lam.grad.item() == pytest.approx(ref["dL_dlambda1"], rel=1e-9, abs=1e-12)
+    np.testing.assert_allclose(b.grad.cpu().numpy(), ref["dL_db"], rtol=1e-9, atol=1e-12)
+    h = 1e-5 * float(lam)
+    zp, _, _ = solve_and_grad(G, P.A, P.b, "logistic", float(lam) + h, mu, 0, g, rho=10.0, sketch_rank=20)
+    zm, _, _ = solve_and_grad(G, P.A, P.b, "logistic", float(lam) - h, mu, 0, g, rho=10.0, sketch_rank=20)
+    assert lam.grad.item() == pytest.approx(g @ (zp - zm) / (2 * h), rel=1e-4, abs=1e-8)
