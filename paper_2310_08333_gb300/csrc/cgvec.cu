@@ -34,15 +34,37 @@ int cgv_blocks(int64_t n) { return (int)((n + CGV_ROWS - 1) / CGV_ROWS); }
 // the U^T r partials of cgv_p follow the cgv_q / cgv_r0 partials in the same buffer
 static inline size_t part_r_offset(int nb) { return ((size_t)nb * CGV_STRIDE + 31) & ~size_t(31); }
 
+// Block-wide sum of NV values of type T (float in float32 mode: this part's float64 pipe is
+// narrow and the CG scalars need no more than float32), broadcast to every thread.
+template <typename T, int NV>
+GENIOS_DEV void bsum(T (&v)[NV]) {
+    __shared__ T sh[32 * NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k * 32 + wid] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const T t = lane < nw ? sh[k * 32 + lane] : T(0);
+        v[k] = warp_sum(t);
+    }
+    __syncthreads();
+}
+
 // Block partial of U^T v over the block's 32 rows (v staged in shared memory), written with the
 // block's scalar partial to part[blockIdx.x * 129 ...].  Threads: column c = t % 128, row half
 // h = t / 128.
 template <typename VT>
-GENIOS_DEV void ut_partial(const VT* U, int sk, const VT* vsh, int64_t j0, int rows, double scalar,
+GENIOS_DEV void ut_partial(const VT* U, int sk, const VT* vsh, int64_t j0, int rows, VT scalar,
                            double* part) {
-    __shared__ double half1[128];
+    __shared__ VT half1[128];
     const int t = threadIdx.x, c = t & 127, h = t >> 7;
-    double acc = 0.0;
+    VT acc = VT(0);
     if (c < sk) {
         VT a = VT(0);
 #pragma unroll
@@ -50,13 +72,13 @@ GENIOS_DEV void ut_partial(const VT* U, int sk, const VT* vsh, int64_t j0, int r
             const int i = h * 16 + k;
             if (i < rows) a = fma(U[(j0 + i) * sk + c], vsh[i], a);
         }
-        acc = (double)a;
+        acc = a;
     }
     if (h == 1) half1[c] = acc;
     __syncthreads();
     double* out = part + (size_t)blockIdx.x * CGV_STRIDE;
-    if (h == 0 && c < sk) out[1 + c] = acc + half1[c];
-    if (t == 0) out[0] = scalar;
+    if (h == 0 && c < sk) out[1 + c] = (double)(acc + half1[c]);
+    if (t == 0) out[0] = (double)scalar;
 }
 
 // start: u <- u_scale u; r = -(g + rho (x - z + u)); delta = 0; partials of ||r||^2 and U^T r
@@ -67,7 +89,7 @@ __global__ void __launch_bounds__(CGV_BT) cgv_r0_kernel(int64_t n, const VT* g, 
     __shared__ VT rsh[CGV_ROWS];
     const int64_t j0 = (int64_t)blockIdx.x * CGV_ROWS;
     const int rows = (int)min((int64_t)CGV_ROWS, n - j0);
-    double rr = 0.0;
+    VT rr = VT(0);
     if (threadIdx.x < CGV_ROWS) {
         VT rj = VT(0);
         if (threadIdx.x < rows) {
@@ -77,12 +99,12 @@ __global__ void __launch_bounds__(CGV_BT) cgv_r0_kernel(int64_t n, const VT* g, 
             rj = -(g[j] + (VT)rho * (x[j] - z[j] + uj));
             r[j] = rj;
             delta[j] = VT(0);
-            rr = (double)rj * (double)rj;
+            rr = rj * rj;
         }
         rsh[threadIdx.x] = rj;
     }
-    double v[1] = {rr};
-    block_sum<1>(v);   // its barriers also publish rsh
+    VT v[1] = {rr};
+    bsum<VT, 1>(v);   // its barriers also publish rsh
     ut_partial<VT>(U, sk, rsh, j0, rows, v[0], part);
 }
 
@@ -109,7 +131,7 @@ __global__ void __launch_bounds__(CGV_BT) cgv_q_kernel(const VT* P, int G, int64
     }
     sh[ty][tx] = a0 + a1;
     __syncthreads();
-    double pq = 0.0;
+    VT pq = VT(0);
     if (ty == 0) {
         VT qj = VT(0);
         if (j < n) {
@@ -120,12 +142,12 @@ __global__ void __launch_bounds__(CGV_BT) cgv_q_kernel(const VT* P, int G, int64
             qj = s + (VT)S->nu * pj;
             if (mask != nullptr && mask[j] == VT(0)) qj = VT(0);   // operator restricted to the mask
             q[j] = qj;
-            pq = (double)pj * (double)qj;
+            pq = pj * qj;
         }
         qsh[tx] = qj;
     }
-    double v[1] = {pq};
-    block_sum<1>(v);
+    VT v[1] = {pq};
+    bsum<VT, 1>(v);
     ut_partial<VT>(U, sk, qsh, j0, rows, v[0], part);
 }
 
@@ -154,24 +176,25 @@ __global__ void __launch_bounds__(CGV_THREADS, 1) cgv_kernel(CgvArgs<VT> a) {
     const int rank = (int)cluster.block_rank();
     const int CL = (int)cluster.num_blocks();
     const int tid = threadIdx.x;
-    __shared__ double mypart[CGV_STRIDE];   // [0] ||r_slice||^2, [1 + c] this CTA's share of U^T (q or r)
-    __shared__ double tot[CGV_STRIDE];
-    __shared__ double grp[4][128];
-    __shared__ double lamsh[128];
+    using AT = VT;   // accumulation type: float in float32 mode
+    __shared__ AT mypart[CGV_STRIDE];   // [0] ||r_slice||^2, [1 + c] this CTA's share of U^T (q or r)
+    __shared__ AT tot[CGV_STRIDE];
+    __shared__ AT grp[4][128];
+    __shared__ AT lamsh[128];
     DevState* S = a.S;
     const int sk = a.sk;
     // device state of the previous launches, read once; this launch writes it only after its
     // last cluster barrier, when every CTA has read it
     const int done_in = a.mode == 1 ? S->cg_done : 0;
-    const double rz_old = S->rz, nu_s = S->nu, tol_s = S->tol, rhs2_in = S->rhs2;
+    const AT rz_old = (AT)S->rz, nu_s = (AT)S->nu, tol_s = (AT)S->tol, rhs2_in = (AT)S->rhs2;
     const int cgmax_s = S->cg_max, it_in = S->cg_it;
-    if (tid < sk) lamsh[tid] = a.lam[tid];
+    if (tid < sk) lamsh[tid] = (AT)a.lam[tid];
     if (done_in) {
         if (a.use_cond && rank == 0 && tid == 0) cudaGraphSetConditional(a.cond, 0u);
         return;
     }
-    const double nu = a.mode == 1 ? nu_s : a.nu;
-    const double tol = a.mode == 1 ? tol_s : a.tol;
+    const AT nu = a.mode == 1 ? nu_s : (AT)a.nu;
+    const AT tol = a.mode == 1 ? tol_s : (AT)a.tol;
     const int cg_max = a.mode == 1 ? cgmax_s : a.cg_max;
 
     // Every global load of this step is issued here, before any reduction, so that the step
@@ -192,31 +215,31 @@ __global__ void __launch_bounds__(CGV_THREADS, 1) cgv_kernel(CgvArgs<VT> a) {
             }
         }
     }
-    double pqv = 0.0;
+    AT pqv = AT(0);
     if (a.mode == 1)
-        for (int b = tid; b < a.nb; b += CGV_THREADS) pqv += a.part[(size_t)b * CGV_STRIDE];
+        for (int b = tid; b < a.nb; b += CGV_THREADS) pqv += (AT)a.part[(size_t)b * CGV_STRIDE];
     const int c = tid & 127, g4 = tid >> 7;
     const int b0 = (int)((int64_t)a.nb * rank / CL), b1 = (int)((int64_t)a.nb * (rank + 1) / CL);
-    double vq[UNR], vr[UNR];
+    AT vq[UNR], vr[UNR];
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
         const int bb = b0 + g4 + 4 * u;
         const bool ok = c < sk && bb < b1;
-        vq[u] = ok ? a.part[(size_t)bb * CGV_STRIDE + 1 + c] : 0.0;
-        vr[u] = (ok && a.mode == 1) ? a.part_r[(size_t)bb * CGV_STRIDE + 1 + c] : 0.0;
+        vq[u] = ok ? (AT)a.part[(size_t)bb * CGV_STRIDE + 1 + c] : AT(0);
+        vr[u] = (ok && a.mode == 1) ? (AT)a.part_r[(size_t)bb * CGV_STRIDE + 1 + c] : AT(0);
     }
 
     // alpha from the block partials of p^T q (same order in every CTA)
-    double pq = 0.0, alpha = 0.0;
+    AT pq = AT(0), alpha = AT(0);
     if (a.mode == 1) {
-        double v[1] = {pqv};
-        block_sum<1>(v);
+        AT v[1] = {pqv};
+        bsum<AT, 1>(v);
         pq = v[0];
-        alpha = pq > 0.0 ? rz_old / pq : 0.0;
+        alpha = pq > AT(0) ? rz_old / pq : AT(0);
     }
 
     // this CTA's rows: delta += alpha p, r -= alpha q, ||r||^2
-    double rr_loc = 0.0;
+    AT rr_loc = AT(0);
 #pragma unroll
     for (int t = 0; t < RPT; ++t) {
         const int64_t j = j0 + tid + (int64_t)t * CGV_THREADS;
@@ -227,20 +250,20 @@ __global__ void __launch_bounds__(CGV_THREADS, 1) cgv_kernel(CgvArgs<VT> a) {
                 rj = rv[t] - (VT)alpha * qv[t];
                 a.r[j] = rj;
             }
-            rr_loc += (double)rj * (double)rj;
+            rr_loc += rj * rj;
         }
     }
     // this CTA's share of the block partials: start: U^T r; iteration: U^T r_old - alpha U^T q
     // (the direct U^T r of the previous residual comes from cgv_p, so the recurrence spans one step)
     {
-        double sacc = 0.0;
+        AT sacc = AT(0);
 #pragma unroll
         for (int u = 0; u < UNR; ++u) sacc += a.mode == 1 ? vr[u] - alpha * vq[u] : vq[u];
         grp[g4][c] = sacc;
     }
     {
-        double v[1] = {rr_loc};
-        block_sum<1>(v);   // its barriers also publish grp
+        AT v[1] = {rr_loc};
+        bsum<AT, 1>(v);   // its barriers also publish grp
         if (tid == 0) mypart[0] = v[0];
     }
     if (tid < sk) mypart[1 + tid] = (grp[0][tid] + grp[1][tid]) + (grp[2][tid] + grp[3][tid]);
@@ -248,28 +271,28 @@ __global__ void __launch_bounds__(CGV_THREADS, 1) cgv_kernel(CgvArgs<VT> a) {
 
     // cluster totals, summed over ranks in order by every CTA
     for (int k = tid; k <= sk; k += CGV_THREADS) {
-        double vals[16];   // all remote loads in flight at once; zeros past CL leave the sum exact
+        AT vals[16];   // all remote loads in flight at once; zeros past CL leave the sum exact
 #pragma unroll
-        for (int q = 0; q < 16; ++q) vals[q] = q < CL ? cluster.map_shared_rank(mypart, q)[k] : 0.0;
-        double s = 0.0;
+        for (int q = 0; q < 16; ++q) vals[q] = q < CL ? cluster.map_shared_rank(mypart, q)[k] : AT(0);
+        AT s = AT(0);
 #pragma unroll
         for (int q = 0; q < 16; ++q) s += vals[q];
         tot[k] = s;
     }
     __syncthreads();
-    const double rr = tot[0];
-    const double ls = sk > 0 ? lamsh[sk - 1] : 0.0;
-    double rzc = 0.0;
+    const AT rr = tot[0];
+    const AT ls = sk > 0 ? lamsh[sk - 1] : AT(0);
+    AT rzc = AT(0);
     if (tid < sk) {
-        const double w = tot[1 + tid];
-        const double cw = ((ls + nu) / (lamsh[tid] + nu) - 1.0) * w;
+        const AT w = tot[1 + tid];
+        const AT cw = ((ls + nu) / (lamsh[tid] + nu) - AT(1)) * w;
         rzc = cw * w;
-        if (rank == 0) S->cgc[tid] = cw;
+        if (rank == 0) S->cgc[tid] = (double)cw;
     }
-    double v[1] = {rzc};
-    block_sum<1>(v);
-    const double rz = rr + v[0];
-    const double beta = a.mode == 1 && rz_old > 0.0 ? rz / rz_old : 0.0;
+    AT v[1] = {rzc};
+    bsum<AT, 1>(v);
+    const AT rz = rr + v[0];
+    const AT beta = a.mode == 1 && rz_old > AT(0) ? rz / rz_old : AT(0);
     cluster.sync();   // no CTA leaves while another still reads its mypart
 
     if (rank == 0 && tid == 0) {
@@ -280,7 +303,7 @@ __global__ void __launch_bounds__(CGV_THREADS, 1) cgv_kernel(CgvArgs<VT> a) {
             S->tol = tol;
             S->cg_it = 0;
             S->cg_max = cg_max;
-            S->cg_done = rr > 0.0 ? 0 : 1;
+            S->cg_done = rr > AT(0) ? 0 : 1;
             S->cg_first = 0;
             S->cg_guard = 0;
             S->hv_t0 = ~0ull;
@@ -291,7 +314,7 @@ __global__ void __launch_bounds__(CGV_THREADS, 1) cgv_kernel(CgvArgs<VT> a) {
             S->rz = rz;
         } else {
             const int it = it_in + 1;
-            const bool done = !(pq > 0.0) || rr <= tol * tol * rhs2_in || it >= cg_max;
+            const bool done = !(pq > AT(0)) || rr <= tol * tol * rhs2_in || it >= cg_max;
             S->pq = pq;
             S->alpha = alpha;
             S->rr = rr;
@@ -321,7 +344,7 @@ __global__ void __launch_bounds__(CGV_BT) cgv_p_kernel(int64_t n, const VT* r, V
     __shared__ VT csh[128];
     __shared__ VT ush[CGV_BT / 32][128];
     for (int c = threadIdx.x; c < 128; c += CGV_BT) csh[c] = c < sk ? (VT)S->cgc[c] : VT(0);
-    const double beta = S->beta;
+    const VT beta = (VT)S->beta;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t j0 = (int64_t)blockIdx.x * CGV_ROWS;
@@ -364,7 +387,7 @@ __global__ void __launch_bounds__(CGV_BT) cgv_p_kernel(int64_t n, const VT* r, V
                 if (lane == t) rj = rv[t];
             const VT zj = rj + mine;
             if (mask != nullptr && mask[j] == VT(0)) p[j] = VT(0);   // preconditioner restricted too
-            else p[j] = beta != 0.0 ? zj + (VT)beta * p[j] : zj;
+            else p[j] = beta != VT(0) ? zj + beta * p[j] : zj;
         }
     }
     if (sk > 0) {
@@ -373,10 +396,10 @@ __global__ void __launch_bounds__(CGV_BT) cgv_p_kernel(int64_t n, const VT* r, V
         __syncthreads();
         double* out = part_r + (size_t)blockIdx.x * CGV_STRIDE;
         for (int c = threadIdx.x; c < sk; c += CGV_BT) {
-            double s = 0.0;
+            VT s = VT(0);
 #pragma unroll
-            for (int w = 0; w < CGV_BT / 32; ++w) s += (double)ush[w][c];
-            out[1 + c] = s;
+            for (int w = 0; w < CGV_BT / 32; ++w) s += ush[w][c];
+            out[1 + c] = (double)s;
         }
     }
 }
