@@ -602,7 +602,10 @@ static genios_status build_cg_graph(genios_ctx* ctx, const void* d, bool pc) {
 // device-side loop and one read of the device state.  Host mode (profile, or use_graphs = 0):
 // the host launches each iteration and reads S->cg_done after it, with CUDA events around the
 // Hv launches.
-static genios_status cg_loop(genios_ctx* ctx, const void* d, int* iters, std::vector<float>* hv_ms) {
+// deferred (graph mode only): launch the loop and return at once; *iters is then left at -1 and
+// the caller reads the count (DevState::cg_it, kept until the next solve starts) at its next sync.
+static genios_status cg_loop(genios_ctx* ctx, const void* d, int* iters, std::vector<float>* hv_ms,
+                             bool deferred = false) {
     cudaStream_t s = ctx->stream;
     if (!ctx->delta || !ctx->r || !ctx->p || !ctx->q || !ctx->S || !ctx->Pbuf)
         FAIL(GENIOS_EINVAL, "cg_loop: work vector not allocated");
@@ -614,6 +617,10 @@ static genios_status cg_loop(genios_ctx* ctx, const void* d, int* iters, std::ve
             if (st != GENIOS_OK) return st;
         }
         CK(cudaGraphLaunch(ctx->cg_exec, s));
+        if (deferred) {
+            *iters = -1;
+            return GENIOS_OK;
+        }
         genios_status st = read_state(ctx);
         if (st != GENIOS_OK) return st;
         if (ctx->Sh->cg_fault) FAIL(GENIOS_ETIMEOUT, "CG vector kernel: a bounded device wait ran out");
@@ -709,6 +716,7 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
     inf.t_setup_ms = ctx->t_setup_ms;
     ctx->launches = 0;
     std::vector<float> hv_ms;
+    bool cg_pending = false;   // a deferred CG whose iteration count is read at the next sync
 
     if (!warm_start || !ctx->solved) {
         CK(cudaMemsetAsync(ctx->x, 0, vbytes, s));
@@ -748,6 +756,13 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
         ctx->launches++;
         genios_status st = read_state(ctx);
         if (st != GENIOS_OK) return st;
+        if (cg_pending) {   // the previous x-update's CG ran without a sync of its own
+            if (ctx->Sh->cg_fault) FAIL(GENIOS_ETIMEOUT, "CG vector kernel: a bounded device wait ran out");
+            inf.cg_iters_total += ctx->Sh->cg_it;
+            inf.hv_launches += ctx->Sh->cg_it;
+            ctx->launches += (int64_t)ctx->Sh->cg_guard * 4;
+            cg_pending = false;
+        }
         if (o.profile) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, ctx->evs[2], ctx->evs[3]));
@@ -842,10 +857,14 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
                      use_pc && ctx->have_precond ? ctx->sk : 0, ctx->lam, ctx->S, ctx->sc.part, nullptr, s));
         ctx->launches++;
         int cgit = 0;
-        st = cg_loop(ctx, dvec, &cgit, &hv_ms);
+        st = cg_loop(ctx, dvec, &cgit, &hv_ms, /*deferred=*/true);
         if (st != GENIOS_OK) return st;
-        inf.cg_iters_total += cgit;
-        inf.hv_launches += cgit;
+        if (cgit >= 0) {
+            inf.cg_iters_total += cgit;
+            inf.hv_launches += cgit;
+        } else {
+            cg_pending = true;
+        }
         // ---- z/u update (§2.5, §3.1, Eq. (5)); x <- x + delta
         CK(zu_update(ctx->dbl, n, ctx->x, ctx->delta, ctx->z, ctx->u, rho, lam1, o.alpha, ctx->S, nullptr,
                      ctx->sc, s));
@@ -869,6 +888,12 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
     }
     genios_status rs = read_state(ctx);
     if (rs != GENIOS_OK) return rs;
+    if (cg_pending) {
+        inf.cg_iters_total += ctx->Sh->cg_it;
+        inf.hv_launches += ctx->Sh->cg_it;
+        ctx->launches += (int64_t)ctx->Sh->cg_guard * 4;
+        cg_pending = false;
+    }
     inf.iters = iters;
     inf.rho = rho;
     inf.rho_updates = n_rho;
