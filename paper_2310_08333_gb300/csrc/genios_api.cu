@@ -178,6 +178,7 @@ extern "C" void genios_default_options(genios_options* o) {
     o->verbose = 0;
     o->profile = 0;
     o->tensor_sketch = 1;
+    o->batch_lockstep = 0;
 }
 
 extern "C" genios_status genios_create(const genios_options* opts, int device, void* stream,
@@ -978,6 +979,96 @@ extern "C" genios_status genios_lambda_max(genios_ctx* ctx, double* out) {
     return GENIOS_OK;
 }
 
+// Lockstep path (batch.cu): one sketch of A^T A, the gradient of the loss at x = 0, then all K
+// problems together; the K solutions z are written back to back in out_dtype.
+static genios_status solve_lockstep(genios_ctx* ctx, const double* lambda1, const double* lambda2, void* x_out,
+                                    int out_dtype, genios_info* info) {
+    for (int k = 0; k < ctx->K; ++k)
+        if (!(lambda1[k] >= 0) || !(lambda2[k] >= 0)) FAIL(GENIOS_EINVAL, "lambda must be >= 0");
+    CK(cudaSetDevice(ctx->device));
+    const double t0 = now_ms();
+    cudaStream_t s = ctx->stream;
+    const genios_options& o = ctx->opt;
+    const int64_t n = ctx->n, K = ctx->K;
+    double sketch_ms = 0.0;
+    if (!ctx->have_precond) {
+        genios_status st = build_precond(ctx, nullptr, &sketch_ms);
+        if (st != GENIOS_OK) return st;
+    }
+    // g0 = A^T l'(-b) into ctx->g (grad pass at x = 0; zc serves as the zero vector)
+    CK(cudaMemsetAsync(ctx->zc, 0, (size_t)ctx->ldp * ctx->vt, s));
+    CK(grad_pass(ctx, ctx->zc, nullptr, nullptr));
+    CK(grad_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, ctx->loss_part, n, ctx->zc, ctx->zc, 0.0, 0.0,
+                   0.0, ctx->g, ctx->S, ctx->sc, s));
+    void* zdev = nullptr;
+    CK(ctx->mem.get(&zdev, (size_t)K * n * 4));
+    BatchInput in{};
+    in.m = ctx->m;
+    in.n = n;
+    in.lda = ctx->lda;
+    in.K = (int)K;
+    in.sk = ctx->sk;
+    in.A = static_cast<const float*>(ctx->A_hv);
+    in.g0 = static_cast<const float*>(ctx->g);
+    in.U = static_cast<const float*>(ctx->U);
+    in.lam = ctx->lam;
+    in.lam1 = lambda1;
+    in.lam2 = lambda2;
+    in.rho0 = o.rho;
+    in.alpha = o.alpha;
+    in.eps_abs = o.eps_abs;
+    in.eps_rel = o.eps_rel;
+    in.eps_kkt = o.eps_kkt;
+    in.gamma = o.gamma;
+    in.cg_first = o.cg_tol_first;
+    in.cg_floor = cg_floor(ctx);
+    in.rho_tau = o.rho_tau;
+    in.rho_mu = o.rho_mu;
+    in.max_iter = o.max_iter;
+    in.max_cg = o.max_cg_iter;
+    in.kkt_every = o.kkt_check_every;
+    in.rho_every = o.rho_update_every;
+    in.rho_max = o.rho_update_max;
+    in.rho_until = o.rho_update_until;
+    in.wait_limit = wait_cycles(ctx);
+    in.stream = s;
+    in.z_out = zdev;
+    std::vector<genios_info> inf(K);
+    for (auto& f : inf) {
+        f = genios_info{};
+        f.rel_gap = NAN;
+        f.rel_kkt = NAN;
+    }
+    BatchResult r = batch_path_solve(in, inf);
+    if (r.status != GENIOS_OK && r.status != GENIOS_EMAXITER) {
+        ctx->mem.release(zdev);
+        FAIL((genios_status)r.status, r.err);
+    }
+    // z of every problem into the caller's buffer
+    const bool odev = is_device_ptr(x_out);
+    const int odt = out_dtype == GENIOS_DT_F64 ? 0 : 1;
+    const size_t ob = odt == 0 ? 8 : 4;
+    void* tmp = x_out;
+    if (!odev) CK(ctx->mem.get(&tmp, (size_t)K * n * ob));
+    CK(convert_copy(1, odt, 1, K * n, zdev, K * n, tmp, K * n, s));
+    if (!odev) CK(cudaMemcpyAsync(x_out, tmp, (size_t)K * n * ob, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!odev) ctx->mem.release(tmp);
+    ctx->mem.release(zdev);
+    const double el = now_ms() - t0;
+    for (int64_t k = 0; k < K; ++k) {
+        inf[k].t_setup_ms = ctx->t_setup_ms;
+        inf[k].t_sketch_ms = k == 0 ? sketch_ms : 0.0;
+        inf[k].sketches = (k == 0 && sketch_ms > 0.0) ? 1 : 0;
+        inf[k].t_solve_ms = el;
+        inf[k].cg_iters_total = (int32_t)r.cg_iterations;
+        inf[k].kernel_launches = r.launches;
+        if (info) info[k] = inf[k];
+    }
+    ctx->solved = false;   // the lockstep state is not kept: no warm start or gradient from it
+    return (genios_status)r.status;
+}
+
 // K = 1: one solve.  Shared data (lambda path): the K problems in the order given, each warm-
 // started from the previous solution (x, z, u, rho) and sharing the sketch when the loss'' is
 // constant.  Independent problems: each sub-context in turn.  x_out holds the K solutions back
@@ -989,6 +1080,9 @@ extern "C" genios_status genios_solve(genios_ctx* ctx, const double* lambda1, co
     if (!ctx->has_data) FAIL(GENIOS_ESTATE, "solve before set_data");
     if (!lambda1 || !lambda2 || !x_out) FAIL(GENIOS_EINVAL, "NULL argument");
     if (out_dtype != GENIOS_DT_F64 && out_dtype != GENIOS_DT_F32) FAIL(GENIOS_EINVAL, "bad out_dtype");
+    if (ctx->shared && ctx->opt.batch_lockstep && ctx->loss == GENIOS_LOSS_SQUARED && ctx->prec == GENIOS_FP32 &&
+        ctx->sk > 0 && ctx->K <= 128)
+        return solve_lockstep(ctx, lambda1, lambda2, x_out, out_dtype, info);
     const size_t es = out_dtype == GENIOS_DT_F64 ? 8 : 4;
     char* out = static_cast<char*>(x_out);
     genios_status worst = GENIOS_OK;

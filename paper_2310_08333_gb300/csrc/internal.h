@@ -5,6 +5,9 @@
 #include <stdint.h>
 #include <stddef.h>
 #include <string>
+#include <vector>
+
+struct genios_info;   // include/genios.h
 
 namespace genios {
 
@@ -218,13 +221,27 @@ struct TcSketch {
     TcWork work;
     long long wait_limit;
 };
+// Blocked operand layout of the tensor-core products: tiles of rt rows x 64 k, 8-row x 16-byte
+// core matrices ordered along k first (byte offset of element (row, k) of a bf16 operand).
+__host__ __device__ inline int64_t blk_off(int64_t row, int64_t k, int64_t ktiles, int64_t rt) {
+    const int64_t tile = (row / rt) * ktiles + (k >> 6);
+    const int64_t r = row % rt, kk = k & 63;
+    return tile * rt * 128 + ((r >> 3) * 8 + (kk >> 3)) * 128 + (r & 7) * 16 + (kk & 7) * 2;
+}
+int tc_sm_count();
+int tc_splits_for(int64_t mtiles, int64_t ktiles);
+// out[split][mtiles * 128][N] = A (mtiles x 128 rows, ktiles x 64 k, blocked) x B^T (N rows, blocked)
+cudaError_t tc_gemm(const unsigned char* A, const unsigned char* B, float* out, int64_t mtiles,
+                    int64_t ktiles, int N, int splits, int* err, long long wait_limit, cudaStream_t s);
 TcPlan tc_plan(int64_t m, int64_t n, int sk);
 size_t tc_bytes(const TcPlan& p, size_t* off = nullptr);
 TcWork tc_carve(void* base, const TcPlan& p);
 // Packs A (m x n, row stride lda, stored as src_prec: P_FP32, P_BF16, or P_FP8 with row scales)
 // into the two blocked bf16 operands.
+// lo != 0 packs the remainders A - bf16(A) (the low half of a bf16 hi + lo split) instead.
 cudaError_t tc_pack_a(const TcPlan& p, TcWork w, int src_prec, const void* A, int64_t lda,
-                      const float* row_scale, cudaStream_t s);
+                      const float* row_scale, cudaStream_t s, int lo = 0);
+cudaError_t batch_pack_lo(const TcPlan& p, TcWork w, const float* A, int64_t lda, cudaStream_t s);
 // Rounds Om (n x s float) to bf16 values in place and packs it.
 cudaError_t tc_pack_omega(const TcPlan& p, TcWork w, float* Om, cudaStream_t s);
 // Y (n x s float) = A^T diag(d) A Om with the packed operands (d may be NULL: identity).
@@ -244,5 +261,29 @@ cudaError_t adj_rhs(bool dbl, int64_t n, const double* g, const void* z, void* r
 cudaError_t adj_outputs(bool dbl, int64_t m, int64_t n, const void* q, const void* z, const void* t,
                         const void* D, const void* l1, double* dlam, double* db, double* dA, int64_t ld_dA,
                         cudaStream_t s);
+
+// Lockstep regularisation path (batch.cu): K problems on one data set, squared loss, float32.
+struct BatchInput {
+    int64_t m, n, lda;
+    int K, sk;
+    const float* A;        // m x n float32, row stride lda (device)
+    const float* g0;       // A^T l'(-b) = -A^T b, the gradient of the loss at x = 0 (n, device)
+    const float* U;        // n x sk Nystrom basis of A^T A (device)
+    const double* lam;     // sk Nystrom eigenvalues (device)
+    const double* lam1;    // K host values
+    const double* lam2;    // K host values
+    double rho0, alpha, eps_abs, eps_rel, eps_kkt, gamma, cg_first, cg_floor, rho_tau, rho_mu;
+    int max_iter, max_cg, kkt_every, rho_every, rho_max, rho_until;
+    long long wait_limit;
+    cudaStream_t stream;
+    void* z_out;           // K x n float32 (device), back to back
+};
+struct BatchResult {
+    int status;
+    std::string err;
+    int iterations;
+    int64_t cg_iterations, launches;
+};
+BatchResult batch_path_solve(const BatchInput& in, std::vector<::genios_info>& info);
 
 }  // namespace genios

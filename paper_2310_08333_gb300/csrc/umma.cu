@@ -28,11 +28,6 @@ constexpr int UM_THREADS = 192;       // warp 0 producer, warp 1 MMA issuer + TM
 constexpr int UM_MAX_STAGES = 8;
 constexpr uint32_t UM_TILE_A = 128 * 128;   // 128 rows x 64 bf16
 
-__host__ __device__ inline int64_t blk_off(int64_t row, int64_t k, int64_t ktiles, int64_t rt) {
-    const int64_t tile = (row / rt) * ktiles + (k >> 6);
-    const int64_t r = row % rt, kk = k & 63;
-    return tile * rt * 128 + ((r >> 3) * 8 + (kk >> 3)) * 128 + (r & 7) * 16 + (kk & 7) * 2;
-}
 
 // ------------------------------------------------------------------------------------------
 // tcgen05 PTX
@@ -233,6 +228,11 @@ template <> GENIOS_DEV float load_src<uint8_t>(const uint8_t* A, int64_t idx, co
     return (float)q * rs[row];
 }
 
+// lo != 0: the remainder x - bf16(x), whose own bf16 rounding is the low half of a hi + lo split
+GENIOS_DEV float lo_part(float x, int lo) {
+    return lo ? x - __bfloat162float(__float2bfloat16_rn(x)) : x;
+}
+
 GENIOS_DEV uint4 pack8(const float (&v)[8]) {
     uint4 u;
     uint32_t w[4];
@@ -249,7 +249,7 @@ GENIOS_DEV uint4 pack8(const float (&v)[8]) {
 // A (m x n, row stride lda) -> blocked bf16 with rows = samples (M-side of W = A Omega).
 template <typename TA>
 __global__ void pack_rows_kernel(int64_t m, int64_t n, const TA* A, int64_t lda, const float* rs,
-                                 int64_t rpad, int64_t kpad, unsigned char* out) {
+                                 int64_t rpad, int64_t kpad, unsigned char* out, int lo) {
     const int64_t kch = kpad / 8, total = rpad * kch;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -257,7 +257,7 @@ __global__ void pack_rows_kernel(int64_t m, int64_t n, const TA* A, int64_t lda,
         float v[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t)
-            v[t] = (row < m && k0 + t < n) ? load_src<TA>(A, row * lda + k0 + t, rs, row) : 0.0f;
+            v[t] = (row < m && k0 + t < n) ? lo_part(load_src<TA>(A, row * lda + k0 + t, rs, row), lo) : 0.0f;
         *reinterpret_cast<uint4*>(out + blk_off(row, k0, kpad / 64, 128)) = pack8(v);
     }
 }
@@ -266,7 +266,7 @@ __global__ void pack_rows_kernel(int64_t m, int64_t n, const TA* A, int64_t lda,
 // take consecutive features so that the column reads of A coalesce.
 template <typename TA>
 __global__ void pack_cols_kernel(int64_t m, int64_t n, const TA* A, int64_t lda, const float* rs,
-                                 int64_t rpad, int64_t kpad, unsigned char* out) {
+                                 int64_t rpad, int64_t kpad, unsigned char* out, int lo) {
     const int64_t total = rpad * (kpad / 8);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -274,7 +274,7 @@ __global__ void pack_cols_kernel(int64_t m, int64_t n, const TA* A, int64_t lda,
         float v[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t)
-            v[t] = (j < n && i0 + t < m) ? load_src<TA>(A, (i0 + t) * lda + j, rs, i0 + t) : 0.0f;
+            v[t] = (j < n && i0 + t < m) ? lo_part(load_src<TA>(A, (i0 + t) * lda + j, rs, i0 + t), lo) : 0.0f;
         *reinterpret_cast<uint4*>(out + blk_off(j, i0, kpad / 64, 128)) = pack8(v);
     }
 }
@@ -350,7 +350,7 @@ __global__ void finish_y_kernel(int64_t n, int sk, int np, const float* part, in
 // ------------------------------------------------------------------------------------------
 static int64_t rup(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
 
-static int sm_count() {
+static int sm_count_impl() {
     static int v = 0;
     if (v == 0) {
         int dev = 0;
@@ -361,13 +361,16 @@ static int sm_count() {
     return v;
 }
 
+int tc_sm_count() { return sm_count_impl(); }
+static int sm_count() { return sm_count_impl(); }
+
 static int stages_for(int N) {
     // two CTAs per SM: about 110 KB of operand stages each
     const int64_t sb = UM_TILE_A + (int64_t)N * 128;
     return (int)std::max<int64_t>(2, std::min<int64_t>(UM_MAX_STAGES, (110 * 1024) / sb));
 }
 
-static int splits_for(int64_t mtiles, int64_t ktiles) {
+int tc_splits_for(int64_t mtiles, int64_t ktiles) {
     const int64_t slots = 2 * (int64_t)sm_count();
     return (int)std::max<int64_t>(1, std::min<int64_t>(ktiles, slots / std::max<int64_t>(1, mtiles)));
 }
@@ -382,8 +385,8 @@ TcPlan tc_plan(int64_t m, int64_t n, int sk) {
     p.kpad_n = rup(n, 64);
     p.rpad_n = rup(n, 128);
     p.kpad_m = rup(m, 64);
-    p.splits1 = splits_for(p.rpad_m / 128, p.kpad_n / 64);
-    p.splits2 = splits_for(p.rpad_n / 128, p.kpad_m / 64);
+    p.splits1 = tc_splits_for(p.rpad_m / 128, p.kpad_n / 64);
+    p.splits2 = tc_splits_for(p.rpad_n / 128, p.kpad_m / 64);
     p.ok = sk >= 1 && p.np <= 128;
     return p;
 }
@@ -418,20 +421,20 @@ TcWork tc_carve(void* base, const TcPlan& p) {
 }
 
 cudaError_t tc_pack_a(const TcPlan& p, TcWork w, int src_prec, const void* A, int64_t lda,
-                      const float* row_scale, cudaStream_t s) {
+                      const float* row_scale, cudaStream_t s, int lo) {
     const int T = 256;
     const int G = 4 * sm_count();
     if (src_prec == P_FP32) {
-        pack_rows_kernel<float><<<G, T, 0, s>>>(p.m, p.n, static_cast<const float*>(A), lda, nullptr, p.rpad_m, p.kpad_n, w.A_rows);
-        pack_cols_kernel<float><<<G, T, 0, s>>>(p.m, p.n, static_cast<const float*>(A), lda, nullptr, p.rpad_n, p.kpad_m, w.A_cols);
+        pack_rows_kernel<float><<<G, T, 0, s>>>(p.m, p.n, static_cast<const float*>(A), lda, nullptr, p.rpad_m, p.kpad_n, w.A_rows, lo);
+        pack_cols_kernel<float><<<G, T, 0, s>>>(p.m, p.n, static_cast<const float*>(A), lda, nullptr, p.rpad_n, p.kpad_m, w.A_cols, lo);
     } else if (src_prec == P_BF16) {
         auto Ab = static_cast<const __nv_bfloat16*>(A);
-        pack_rows_kernel<__nv_bfloat16><<<G, T, 0, s>>>(p.m, p.n, Ab, lda, nullptr, p.rpad_m, p.kpad_n, w.A_rows);
-        pack_cols_kernel<__nv_bfloat16><<<G, T, 0, s>>>(p.m, p.n, Ab, lda, nullptr, p.rpad_n, p.kpad_m, w.A_cols);
+        pack_rows_kernel<__nv_bfloat16><<<G, T, 0, s>>>(p.m, p.n, Ab, lda, nullptr, p.rpad_m, p.kpad_n, w.A_rows, lo);
+        pack_cols_kernel<__nv_bfloat16><<<G, T, 0, s>>>(p.m, p.n, Ab, lda, nullptr, p.rpad_n, p.kpad_m, w.A_cols, lo);
     } else if (src_prec == P_FP8) {
         auto Aq = static_cast<const uint8_t*>(A);
-        pack_rows_kernel<uint8_t><<<G, T, 0, s>>>(p.m, p.n, Aq, lda, row_scale, p.rpad_m, p.kpad_n, w.A_rows);
-        pack_cols_kernel<uint8_t><<<G, T, 0, s>>>(p.m, p.n, Aq, lda, row_scale, p.rpad_n, p.kpad_m, w.A_cols);
+        pack_rows_kernel<uint8_t><<<G, T, 0, s>>>(p.m, p.n, Aq, lda, row_scale, p.rpad_m, p.kpad_n, w.A_rows, lo);
+        pack_cols_kernel<uint8_t><<<G, T, 0, s>>>(p.m, p.n, Aq, lda, row_scale, p.rpad_n, p.kpad_m, w.A_cols, lo);
     } else {
         return cudaErrorInvalidValue;
     }
@@ -443,9 +446,8 @@ cudaError_t tc_pack_omega(const TcPlan& p, TcWork w, float* Om, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-static cudaError_t launch_gemm(const unsigned char* A, const unsigned char* B, float* out, int64_t mtiles,
-                               int64_t ktiles, int N, int splits, int* err, long long wait_limit,
-                               cudaStream_t s) {
+cudaError_t tc_gemm(const unsigned char* A, const unsigned char* B, float* out, int64_t mtiles,
+                    int64_t ktiles, int N, int splits, int* err, long long wait_limit, cudaStream_t s) {
     UmmaArgs a{};
     a.A = A;
     a.B = B;
@@ -468,14 +470,18 @@ static cudaError_t launch_gemm(const unsigned char* A, const unsigned char* B, f
 
 cudaError_t tc_sketch(const TcPlan& p, TcWork w, const float* d, float* Y, long long wait_limit, cudaStream_t s) {
     if (!p.ok) return cudaErrorInvalidValue;
-    cudaError_t e = launch_gemm(w.A_rows, w.Om, w.part, p.rpad_m / 128, p.kpad_n / 64, p.np, p.splits1, w.err,
-                                wait_limit, s);
+    cudaError_t e = tc_gemm(w.A_rows, w.Om, w.part, p.rpad_m / 128, p.kpad_n / 64, p.np, p.splits1, w.err,
+                            wait_limit, s);
     if (e != cudaSuccess) return e;
     finish_w_kernel<<<2 * sm_count(), 256, 0, s>>>(p.m, p.sk, p.np, w.part, p.splits1, p.rpad_m, d, p.kpad_m, w.W);
-    e = launch_gemm(w.A_cols, w.W, w.part, p.rpad_n / 128, p.kpad_m / 64, 2 * p.np, p.splits2, w.err, wait_limit, s);
+    e = tc_gemm(w.A_cols, w.W, w.part, p.rpad_n / 128, p.kpad_m / 64, 2 * p.np, p.splits2, w.err, wait_limit, s);
     if (e != cudaSuccess) return e;
     finish_y_kernel<<<2 * sm_count(), 256, 0, s>>>(p.n, p.sk, p.np, w.part, p.splits2, p.rpad_n, Y);
     return cudaGetLastError();
+}
+
+cudaError_t batch_pack_lo(const TcPlan& p, TcWork w, const float* A, int64_t lda, cudaStream_t s) {
+    return tc_pack_a(p, w, P_FP32, A, lda, nullptr, s, 1);
 }
 
 }  // namespace genios

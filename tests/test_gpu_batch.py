@@ -27,6 +27,7 @@ def rel(a, b):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_lambda_path_matches_oracle(G, prec):
+    """The K problems in turn, warm-started (batch_lockstep = 0)."""
     P = problems.lasso_iid(300, 600, nnz=30, seed=problems.seed_for(4, 1))
     A, b = P.A, P.b
     if prec == 1:
@@ -72,3 +73,29 @@ def test_batch_grad_is_refused(G):
         s.solve_batch([0.5 * s.lambda_max_batch()[0]] * 2)
         with pytest.raises(G.GeniosError):
             s.grad(np.ones(200))
+
+
+def test_lockstep_path_matches_oracle(G):
+    """All K problems in lockstep with tensor-core products for the whole batch (float32, squared
+    loss): every problem reaches the 1e-4 relative KKT of its own lambda (checked in float64 at
+    the GPU's z), with the oracle's support, and the solution error the KKT residual implies."""
+    from test_gpu_solver import derived_tol
+    P = problems.lasso_ar1(500, 2000, nnz=60, seed=problems.seed_for(4, 5))
+    A, b = P.A.astype(np.float32).astype(np.float64), P.b.astype(np.float32).astype(np.float64)
+    lmax = checks.lambda_max(A, b, "squared")
+    lams = problems.lambda_path_fracs(12, lo=0.05) * lmax
+    with G.Solver(precision=1, stop_rule=G.STOP_KKT, eps_kkt=1e-4, sketch_rank=40, max_iter=20000,
+                  batch_lockstep=1) as s:
+        s.set_batch([torch.from_numpy(A).to("cuda", torch.float32)], [torch.from_numpy(b).to("cuda", torch.float32)],
+                    "squared", path_size=len(lams))
+        zs, infos = s.solve_batch(lams)
+    assert all(i["status"] == 0 for i in infos), [(i["status_name"], i["iters"]) for i in infos]
+    assert infos[0]["sketches"] == 1
+    for lam, z, inf in zip(lams, zs, infos):
+        kkt = checks.rel_kkt(A, b, z, "squared", lam)
+        assert kkt <= 2e-4, (lam, kkt)
+        ref = oadmm.solve(A, b, "squared", lam, tol=1e-13)["z"]
+        big = np.abs(ref) > 1e-3 * np.abs(ref).max()
+        assert np.all(z[big] != 0) and np.all(np.sign(z[big]) == np.sign(ref[big]))
+        if np.any(ref):
+            assert rel(z, ref) <= max(1e-3, derived_tol(A, b, ref, "squared", lam, 0.0, kkt)), (lam, rel(z, ref))
