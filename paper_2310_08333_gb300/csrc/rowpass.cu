@@ -199,22 +199,50 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
                     dot[q] = d2.x + d2.y;
                 }
             }
+            // Row totals of the RB dot products.  Within the warp a transposed reduce-scatter:
+            // each halving step sends half of a lane's values across and keeps the other half,
+            // so after log2(RB) steps lane group g = lane / GS (GS = 32 / RB lanes) holds row g's
+            // partial, finished over the group (RB - 1 + log2(GS) shuffles instead of 5 RB).
+            // Across the 16 warps, group g folds row g's 16 warp partials the same way and the
+            // totals are broadcast from the groups.
+            constexpr int LR = RB == 1 ? 0 : RB == 2 ? 1 : RB == 4 ? 2 : 3;
+            static_assert((1 << LR) == RB, "rows per barrier group must be 1, 2, 4 or 8");
+            constexpr int GS = 32 >> LR;
+            {
 #pragma unroll
-            for (int q = 0; q < RB; ++q) dot[q] = warp_sum(dot[q]);
-            if (lane == 0) {
+                for (int l = 0; l < LR; ++l) {
+                    const int off = 16 >> l;
+                    const bool up = (lane & off) != 0;
+                    const int half = RB >> (l + 1);
 #pragma unroll
-                for (int q = 0; q < RB; ++q)
-                    if (GCHK(a.dbg, (long long)(reinterpret_cast<unsigned char*>(red + (par * RB + q) * RP_CWARPS + wid) - smem) + (long long)sizeof(VT) - 1, a.smem_bytes))
-                        red[(par * RB + q) * RP_CWARPS + wid] = dot[q];
+                    for (int i = 0; i < half; ++i) {
+                        const VT keep = up ? dot[i + half] : dot[i];
+                        const VT send = up ? dot[i] : dot[i + half];
+                        dot[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                    }
+                }
+#pragma unroll
+                for (int off = GS >> 1; off > 0; off >>= 1) dot[0] += __shfl_xor_sync(0xffffffffu, dot[0], off);
+                if ((lane & (GS - 1)) == 0 &&
+                    GCHK(a.dbg, (long long)(reinterpret_cast<unsigned char*>(red + (par * RB + lane / GS) * RP_CWARPS + wid) - smem) + (long long)sizeof(VT) - 1, a.smem_bytes))
+                    red[(par * RB + lane / GS) * RP_CWARPS + wid] = dot[0];
             }
             named_bar_sync(1, RP_CTHREADS);
+            VT tot[RB];
+            {
+                const int g = lane / GS, sidx = lane & (GS - 1);
+                VT t = VT(0);
+#pragma unroll
+                for (int w = sidx; w < RP_CWARPS; w += GS) t += red[(par * RB + g) * RP_CWARPS + w];
+#pragma unroll
+                for (int off = GS >> 1; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+#pragma unroll
+                for (int q = 0; q < RB; ++q) tot[q] = __shfl_sync(0xffffffffu, t, q * GS);
+            }
             VT wq[RB];
 #pragma unroll
             for (int q = 0; q < RB; ++q) {
-                VT t = lane < RP_CWARPS ? red[(par * RB + q) * RP_CWARPS + lane] : VT(0);
-#pragma unroll
-                for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                t = __shfl_sync(0xffffffffu, t, 0);
+                VT t = tot[q];
                 wq[q] = VT(0);
                 if (rr + q < rows) {
                     const int64_t i = r0 + (int64_t)st * rps + rr + q;
