@@ -122,6 +122,12 @@ typedef struct genios_options {
                                 two tensor-core GEMMs over A and gradients from a bf16 hi + lo split
                                 of A (relative KKT floor about 1e-4 at small lambda); on the 32-level
                                 5000 x 20000 path the warm-started sequence is faster */
+    int32_t persistent_cg;   /* 1 (default): each CG solve (x-step, implicit-gradient adjoint,
+                                genios_op_pcg) runs as one cooperative kernel with one CTA per SM,
+                                Hv passes and vector work separated by grid barriers, when the
+                                shape allows (n <= 1024 x SMs, s <= 128, not the split-BF16
+                                stream); 0: one Hv launch plus vector kernels per CG iteration
+                                (CUDA graph when use_graphs = 1) */
 } genios_options;
 
 typedef struct genios_info {
@@ -147,6 +153,10 @@ typedef struct genios_info {
     int64_t grad_launches;   /* gradient rowpass launches */
     double grad_ms;          /* their total device time (profile = 1), else 0 */
     double hv_bytes;         /* algorithmic bytes of one Hv launch (A once + vectors) */
+    int64_t cg_launches;     /* persistent CG launches (persistent_cg = 1), else 0 */
+    double cg_ms;            /* their total device time (first CTA start to end), else 0 */
+    double cg_phase_ms[6];   /* the device time of CTA 0 in those launches by phase: Hv pass,
+                                barrier, residual update, barrier, new direction, barrier */
 } genios_info;
 
 /* Fill *o with the defaults listed above.  o != NULL. */

@@ -38,7 +38,7 @@ class Options(C.Structure):
         ("precision", C.c_int32), ("kkt_check_every", C.c_int32), ("use_graphs", C.c_int32),
         ("seed", C.c_uint64), ("device_wait_limit_us", C.c_int64),
         ("verbose", C.c_int32), ("profile", C.c_int32), ("tensor_sketch", C.c_int32),
-        ("batch_lockstep", C.c_int32),
+        ("batch_lockstep", C.c_int32), ("persistent_cg", C.c_int32),
     ]
 
 
@@ -51,11 +51,16 @@ class Info(C.Structure):
         ("objective", C.c_double), ("t_setup_ms", C.c_double), ("t_sketch_ms", C.c_double),
         ("t_solve_ms", C.c_double), ("kernel_launches", C.c_int64), ("hv_launches", C.c_int64),
         ("hv_ms", C.c_double), ("grad_launches", C.c_int64), ("grad_ms", C.c_double),
-        ("hv_bytes", C.c_double),
+        ("hv_bytes", C.c_double), ("cg_launches", C.c_int64), ("cg_ms", C.c_double),
+        ("cg_phase_ms", C.c_double * 6),
     ]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if isinstance(v, C.Array) else v
+        return out
 
 
 _vp = C.c_void_p

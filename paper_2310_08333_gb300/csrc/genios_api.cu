@@ -101,6 +101,7 @@ struct genios_ctx {
     double* lam = nullptr;
     void* nyswork = nullptr;
     CgvPlan cgv{};              // cluster CG vector kernel
+    CgLoopPlan cgl{};           // persistent CG kernel (ok = false: per-iteration kernels)
     void* tcbuf = nullptr;      // tensor-core sketch operands (value type float only)
     TcSketch tc{};
     bool use_tc = false;
@@ -179,6 +180,7 @@ extern "C" void genios_default_options(genios_options* o) {
     o->profile = 0;
     o->tensor_sketch = 1;
     o->batch_lockstep = 0;
+    o->persistent_cg = 1;
 }
 
 extern "C" genios_status genios_create(const genios_options* opts, int device, void* stream,
@@ -414,7 +416,12 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
     if (!ctx->plan_hv.ok || !ctx->plan_g.ok)
         FAIL(GENIOS_EUNSUPPORTED, "n too large for the fused rowpass in this precision");
     ctx->ldp = std::max(ctx->lda, ctx->lda_g);
-    const int G = std::max(ctx->plan_hv.grid, ctx->plan_g.grid);
+    int sk = ctx->opt.sketch_rank;
+    if (sk < 0) sk = (int)std::min<int64_t>(50, N / 20);
+    sk = (int)std::min<int64_t>(sk, N);
+    ctx->sk = std::max(0, sk);
+    ctx->cgl = ctx->opt.persistent_cg ? cgloop_plan(hvp, M, N, ctx->lda, ctx->sk) : CgLoopPlan{};
+    const int G = std::max(std::max(ctx->plan_hv.grid, ctx->plan_g.grid), ctx->cgl.ok ? ctx->cgl.rp.grid : 0);
     CK(ctx->mem.get(&ctx->Pbuf, (size_t)G * ctx->ldp * vt));
     CK(ctx->mem.get((void**)&ctx->loss_part, (size_t)G * 8));
     void** vecs[] = {&ctx->x, &ctx->z, &ctx->u, &ctx->g, &ctx->r, &ctx->p, &ctx->q, &ctx->zc, &ctx->delta};
@@ -425,10 +432,6 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
     CK(ctx->mem.get(&ctx->D, (size_t)M * vt));
     CK(ctx->mem.get(&ctx->W, (size_t)M * vt));
     // Nystrom
-    int sk = ctx->opt.sketch_rank;
-    if (sk < 0) sk = (int)std::min<int64_t>(50, N / 20);
-    sk = (int)std::min<int64_t>(sk, N);
-    ctx->sk = std::max(0, sk);
     ctx->cgv = cgv_plan(ctx->dbl, N, ctx->sk);
     if (!ctx->cgv.ok) FAIL(GENIOS_EUNSUPPORTED, "no thread-block cluster configuration for the CG vector kernel");
     if (ctx->sk > 0) {
@@ -511,6 +514,48 @@ static cudaError_t hv_pass(genios_ctx* ctx, const void* v, const void* v_aux, co
     a.partial_len = (long long)ctx->plan_hv.grid * ctx->ldp;
     ctx->launches++;
     return rowpass_launch(a, ctx->plan_hv, ctx->stream);
+}
+
+// One persistent CG solve (cgloop.cu) on r = -(g + rho (x - z + u_scale u)); the result is left in
+// ctx->delta and the final scalars in DevState (cg_it, rr, rhs2, ...).
+static cudaError_t cg_persistent(genios_ctx* ctx, const void* d, const void* g, const void* x, const void* z,
+                                 void* u, double rho, double u_scale, double nu, double tol, int cg_max, int sk,
+                                 const void* mask) {
+    CgLoopArgs a{};
+    a.rp.prec = hv_prec(ctx);
+    a.rp.mode = RP_HV;
+    a.rp.m = ctx->m;
+    a.rp.n = ctx->n;
+    a.rp.lda = ctx->lda;
+    a.rp.A = ctx->A_hv;
+    a.rp.row_scale = ctx->A_scale;
+    a.rp.d = d;
+    a.rp.partial = ctx->Pbuf;
+    a.rp.ldp = ctx->ldp;
+    a.rp.wait_limit = wait_cycles(ctx);
+    a.rp.dbg = ctx->dbg;
+    a.g = g;
+    a.x = x;
+    a.z = z;
+    a.u = u;
+    a.r = ctx->r;
+    a.delta = ctx->delta;
+    a.p = ctx->p;
+    a.U = ctx->U;
+    a.sk = sk;
+    a.lam = ctx->lam;
+    a.mask = mask;
+    a.rho = rho;
+    a.u_scale = u_scale;
+    a.nu = nu;
+    a.tol = tol;
+    a.cg_max = cg_max;
+    a.part = ctx->sc.part;
+    a.bar = ctx->sc.counter + 32;
+    a.S = ctx->S;
+    a.timed = 1;
+    ctx->launches++;
+    return cgloop_launch(ctx->cgl, a, ctx->stream);
 }
 
 static genios_status read_state(genios_ctx* ctx) {
@@ -853,13 +898,20 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
                             : std::min(std::sqrt(last_rp * last_rd), 1.0) / std::pow((double)k, o.gamma);
         tol = std::max(tol, floor);
         // ---- x-step rhs, CG
-        CK(cgv_start(ctx->dbl, ctx->cgv, n, ctx->g, ctx->x, ctx->z, ctx->u, rho, u_scale, nu, tol,
-                     o.max_cg_iter, ctx->r, ctx->delta, ctx->p, ctx->U,
-                     use_pc && ctx->have_precond ? ctx->sk : 0, ctx->lam, ctx->S, ctx->sc.part, nullptr, s));
-        ctx->launches++;
+        const int sk_now = use_pc && ctx->have_precond ? ctx->sk : 0;
         int cgit = 0;
-        st = cg_loop(ctx, dvec, &cgit, &hv_ms, /*deferred=*/true);
-        if (st != GENIOS_OK) return st;
+        if (ctx->cgl.ok && !o.profile) {   // the whole CG solve in one launch; its count is read later
+            CK(cg_persistent(ctx, dvec, ctx->g, ctx->x, ctx->z, ctx->u, rho, u_scale, nu, tol, o.max_cg_iter,
+                             sk_now, nullptr));
+            cgit = -1;
+        } else {
+            CK(cgv_start(ctx->dbl, ctx->cgv, n, ctx->g, ctx->x, ctx->z, ctx->u, rho, u_scale, nu, tol,
+                         o.max_cg_iter, ctx->r, ctx->delta, ctx->p, ctx->U, sk_now, ctx->lam, ctx->S,
+                         ctx->sc.part, nullptr, s));
+            ctx->launches++;
+            st = cg_loop(ctx, dvec, &cgit, &hv_ms, /*deferred=*/true);
+            if (st != GENIOS_OK) return st;
+        }
         if (cgit >= 0) {
             inf.cg_iters_total += cgit;
             inf.hv_launches += cgit;
@@ -902,10 +954,13 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
     inf.t_solve_ms = now_ms() - t_start;
     inf.kernel_launches = ctx->launches;
     for (float ms : hv_ms) inf.hv_ms += ms;
-    if (ctx->opt.use_graphs && !o.profile && ctx->Sh->hv_count > 0) {
-        inf.hv_ms = ctx->Sh->hv_ns * 1e-6;   // device-timed Hv launches inside the graph
+    if ((ctx->opt.use_graphs || ctx->cgl.ok) && !o.profile && ctx->Sh->hv_count > 0) {
+        inf.hv_ms = ctx->Sh->hv_ns * 1e-6;   // device-timed Hv passes (graph launches or CG phases)
         inf.hv_launches = ctx->Sh->hv_count;
     }
+    inf.cg_launches = ctx->Sh->cgl_count;
+    inf.cg_ms = ctx->Sh->cgl_ns * 1e-6;
+    for (int k = 0; k < 6; ++k) inf.cg_phase_ms[k] = ctx->Sh->cgl_phase_ns[k] * 1e-6;
     {
         const size_t es = ctx->prec == GENIOS_FP64 ? 8 : ctx->prec == GENIOS_FP32 ? 4
                           : ctx->prec == GENIOS_BF16 ? 2 : 1;
@@ -1196,37 +1251,57 @@ extern "C" genios_status genios_grad(genios_ctx* ctx, const void* dL_dx, double*
         const double tol = ctx->dbl ? 1e-12 : 1e-6;
         const int max_it = (int)std::min<int64_t>(10000, 4 * n + 50);
         // r = -(0 + (-1)(rhs - 0 + 0)) = rhs on S
-        if (cgv_start(ctx->dbl, ctx->cgv, n, zero_n, ctx->zc, zero_n, zero_n, -1.0, 1.0, ctx->lam2, tol, max_it,
-                      ctx->r, ctx->delta, ctx->p, ctx->U, sk, ctx->lam, ctx->S, ctx->sc.part, ctx->z, s) !=
-            cudaSuccess) {
-            result = GENIOS_ECUDA;
-            break;
-        }
-        genios_status st = read_state(ctx);
-        if (st != GENIOS_OK) {
-            result = st;
-            break;
-        }
-        const int G = ctx->plan_hv.grid;
-        int it = 0;
-        while (!ctx->Sh->cg_done && it < max_it + 2) {
-            if (hv_pass(ctx, ctx->p, nullptr, ctx->D, &ctx->S->cg_done) != cudaSuccess ||
-                cgv_q(ctx->dbl, ctx->Pbuf, G, ctx->ldp, n, ctx->p, ctx->q, ctx->U, sk, ctx->sc.part, ctx->S,
-                      ctx->z, s) != cudaSuccess ||
-                cgv_iter(ctx->dbl, ctx->cgv, n, ctx->q, ctx->r, ctx->delta, ctx->p, ctx->U, sk, ctx->lam, ctx->S,
-                         ctx->sc.part, 0ull, 0, 0, ctx->z, s) != cudaSuccess) {
+        if (ctx->cgl.ok) {
+            if (cg_persistent(ctx, ctx->D, zero_n, ctx->zc, zero_n, zero_n, -1.0, 1.0, ctx->lam2, tol, max_it, sk,
+                              ctx->z) != cudaSuccess) {
                 result = GENIOS_ECUDA;
                 break;
             }
-            ctx->launches += 3;
-            st = read_state(ctx);
+            genios_status st = read_state(ctx);
             if (st != GENIOS_OK) {
                 result = st;
                 break;
             }
-            ++it;
+            if (ctx->Sh->cg_fault) {
+                ctx->err = "persistent CG: a bounded device wait ran out";
+                result = GENIOS_ETIMEOUT;
+                break;
+            }
+            ctx->grad_cg_iters = ctx->Sh->cg_it;
+        } else {
+            if (cgv_start(ctx->dbl, ctx->cgv, n, zero_n, ctx->zc, zero_n, zero_n, -1.0, 1.0, ctx->lam2, tol, max_it,
+                          ctx->r, ctx->delta, ctx->p, ctx->U, sk, ctx->lam, ctx->S, ctx->sc.part, ctx->z, s) !=
+                cudaSuccess) {
+                result = GENIOS_ECUDA;
+                break;
+            }
+            genios_status st = read_state(ctx);
+            if (st != GENIOS_OK) {
+                result = st;
+                break;
+            }
+            const int G = ctx->plan_hv.grid;
+            int it = 0;
+            while (!ctx->Sh->cg_done && it < max_it + 2) {
+                if (hv_pass(ctx, ctx->p, nullptr, ctx->D, &ctx->S->cg_done) != cudaSuccess ||
+                    cgv_q(ctx->dbl, ctx->Pbuf, G, ctx->ldp, n, ctx->p, ctx->q, ctx->U, sk, ctx->sc.part, ctx->S,
+                          ctx->z, s) != cudaSuccess ||
+                    cgv_iter(ctx->dbl, ctx->cgv, n, ctx->q, ctx->r, ctx->delta, ctx->p, ctx->U, sk, ctx->lam, ctx->S,
+                             ctx->sc.part, 0ull, 0, 0, ctx->z, s) != cudaSuccess) {
+                    result = GENIOS_ECUDA;
+                    break;
+                }
+                ctx->launches += 3;
+                st = read_state(ctx);
+                if (st != GENIOS_OK) {
+                    result = st;
+                    break;
+                }
+                ++it;
+            }
+            if (result != GENIOS_OK) break;
+            ctx->grad_cg_iters = it;
         }
-        if (result != GENIOS_OK) break;
         const bool converged = ctx->Sh->rr <= tol * tol * ctx->Sh->rhs2 || ctx->Sh->rhs2 == 0.0;
         // t = A q, then the outputs
         if (av_pass(ctx, ctx->delta, t, zero_m) != cudaSuccess) {
@@ -1268,7 +1343,6 @@ extern "C" genios_status genios_grad(genios_ctx* ctx, const void* dL_dx, double*
             result = GENIOS_ECUDA;
             break;
         }
-        ctx->grad_cg_iters = it;
         if (!converged) {
             result = GENIOS_EMAXITER;
             ctx->err = "implicit gradient: the adjoint CG did not reach its tolerance";
@@ -1589,8 +1663,10 @@ extern "C" genios_status genios_op_pcg(int precision, int64_t m, int64_t n, cons
     ctx->opt.profile = 0;
     const size_t vb = (size_t)lda * ctx->vt;
     genios_status result = GENIOS_OK;
+    ctx->cgl = cgloop_plan(P, m, n, lda, s);
+    const int Gp = std::max(plan.grid, ctx->cgl.ok ? ctx->cgl.rp.grid : 0);
     do {
-        if (ctx->mem.get(&ctx->Pbuf, (size_t)plan.grid * lda * ctx->vt) != cudaSuccess ||
+        if (ctx->mem.get(&ctx->Pbuf, (size_t)Gp * lda * ctx->vt) != cudaSuccess ||
             ctx->mem.get((void**)&ctx->S, sizeof(DevState)) != cudaSuccess ||
             cudaMallocHost(&ctx->Sh, sizeof(DevState)) != cudaSuccess ||
             ctx->mem.get((void**)&ctx->sc.part, 262144 * 8) != cudaSuccess ||
@@ -1608,21 +1684,36 @@ extern "C" genios_status genios_op_pcg(int precision, int64_t m, int64_t n, cons
         cudaMemsetAsync(ctx->S, 0, sizeof(DevState), st);
         cudaMemsetAsync(ctx->g, 0, vb, st);
         // rhs: r = -(0 + (-1)(r_in - 0 + 0)) = r_in   (g doubles as the zero z and u)
-        ctx->cgv = cgv_plan(ctx->dbl, n, s);
-        if (!ctx->cgv.ok) {
-            result = GENIOS_EUNSUPPORTED;
-            break;
-        }
-        cudaError_t e = cgv_start(ctx->dbl, ctx->cgv, n, ctx->g, r, ctx->g, ctx->g, -1.0, 1.0, nu, rtol,
-                                  max_iter, ctx->r, delta_out, ctx->p, U, s, lam, ctx->S, ctx->sc.part, nullptr,
-                                  st);
-        if (e != cudaSuccess) {
-            result = op_err(e);
-            break;
-        }
         int it = 0;
-        std::vector<float> dummy;
-        result = cg_loop(ctx, d, &it, &dummy);
+        if (ctx->cgl.ok) {
+            cudaError_t e = cg_persistent(ctx, d, ctx->g, r, ctx->g, ctx->g, -1.0, 1.0, nu, rtol, max_iter, s,
+                                          nullptr);
+            if (e != cudaSuccess) {
+                result = op_err(e);
+                break;
+            }
+            result = read_state(ctx);
+            if (result == GENIOS_OK && ctx->Sh->cg_fault) {
+                ctx->err = "persistent CG: a bounded device wait ran out";
+                result = GENIOS_ETIMEOUT;
+            }
+            it = ctx->Sh->cg_it;
+        } else {
+            ctx->cgv = cgv_plan(ctx->dbl, n, s);
+            if (!ctx->cgv.ok) {
+                result = GENIOS_EUNSUPPORTED;
+                break;
+            }
+            cudaError_t e = cgv_start(ctx->dbl, ctx->cgv, n, ctx->g, r, ctx->g, ctx->g, -1.0, 1.0, nu, rtol,
+                                      max_iter, ctx->r, delta_out, ctx->p, U, s, lam, ctx->S, ctx->sc.part, nullptr,
+                                      st);
+            if (e != cudaSuccess) {
+                result = op_err(e);
+                break;
+            }
+            std::vector<float> dummy;
+            result = cg_loop(ctx, d, &it, &dummy);
+        }
 #ifdef GENIOS_CHECKED
         {
             long long rec[4] = {0, 0, 0, 0};

@@ -51,7 +51,10 @@ struct DevState {
     int32_t hv_count; // rowpass (Hv) launches timed on the device
     unsigned long long hv_t0, hv_t1;  // first-CTA start / last-CTA end of the current Hv launch (ns)
     double hv_ns;     // accumulated device time of the timed Hv launches
-    double pad[1];
+    double cgl_ns;    // accumulated device time of the persistent CG launches (timed)
+    int32_t cgl_count, cgl_iters;   // those launches and their CG iterations
+    double cgl_phase_ns[6];         // CTA 0's time by phase: Hv, barrier, update, barrier,
+                                    // direction, barrier
     double w[256];    // U^T r (Nystrom preconditioner), s <= 256 (op-level preconditioner)
     double cgw[128];  // U^T r of the current CG residual (cluster CG path, s <= 128)
     double cgc[128];  // preconditioner coefficients c_i w_i for the next direction
@@ -98,8 +101,44 @@ struct RowpassPlan {
 int device_sm_count();
 // Message returned by genios_last_error(NULL) on this thread.
 void set_last_error(const std::string& msg);
-RowpassPlan rowpass_plan(int prec, int64_t m, int64_t n, int64_t lda);
+// smem_budget: bytes of dynamic shared memory for the stage ring (0: the rowpass default)
+RowpassPlan rowpass_plan(int prec, int64_t m, int64_t n, int64_t lda, size_t smem_budget = 0);
 cudaError_t rowpass_launch(const RowpassArgs& a, const RowpassPlan& p, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// Persistent CG (cgloop.cu): the whole preconditioned CG solve of one x-subproblem in one
+// cooperative launch (one CTA per SM), Hv pass and vector work separated by grid barriers.
+// ------------------------------------------------------------------------------------------
+struct CgLoopPlan {
+    bool ok;
+    RowpassPlan rp;   // ring of the Hv pass; rp.grid = SM count
+};
+struct CgLoopArgs {
+    RowpassArgs rp;            // Hv pass: prec, A, row_scale, d, m, n, lda, partial (grid x ldp), ldp,
+                               // wait_limit, dbg
+    const void* g;             // right-hand side r = -(g + rho (x - z + u_scale u))
+    const void* x;
+    const void* z;
+    void* u;                   // scaled in place by u_scale
+    void* r;
+    void* delta;               // the solution (x-step), zeroed at the start
+    void* p;
+    const void* U;             // n x sk Nystrom basis (row-major), 0 <= sk <= 128
+    int sk;
+    const double* lam;         // sk eigenvalue estimates, descending
+    const void* mask;          // value type or NULL: operator and preconditioner restricted to it
+    double rho, u_scale, nu, tol;
+    int cg_max;
+    void* part;                // cgloop_part_elems(grid) value-type partials
+    unsigned* bar;             // grid-barrier counter (zeroed by cgloop_launch)
+    DevState* S;               // cg_fault must be 0 at launch; results: cg_it, rr, rz, ...
+    int timed;                 // accumulate H-phase and launch device times in S
+};
+// ok = false when the shape does not fit (n > 1024 per SM, s > 128, the split-BF16 stream, or a
+// ring that does not fit one CTA per SM); the caller then uses the per-kernel CG path.
+CgLoopPlan cgloop_plan(int prec, int64_t m, int64_t n, int64_t lda, int sk);
+size_t cgloop_part_elems(int grid);
+cudaError_t cgloop_launch(const CgLoopPlan& pl, const CgLoopArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // Vector kernels (value type float or double chosen by `dbl`)
