@@ -175,24 +175,26 @@ def seconds_per_solve(ms_total_max: float, steps: int, ws: int) -> float:
     return ms_total_max / 1e3 / (steps * ws)
 
 
-def rowpass_source_hash() -> str:
+CGLOOP_SOURCES = ("cgloop.cu", "rowpass_core.cuh", "common.cuh", "internal.h")
+
+
+def cgloop_source_hash() -> str:
     csrc = os.path.join(ROOT, "paper_2310_08333_gb300", "csrc")
-    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("rowpass.cu", "common.cuh"))
+    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in CGLOOP_SOURCES)
     return hashlib.sha256(src).hexdigest()[:16]
 
 
 def traffic_record(kernel: str, workload: str):
-    """dram bytes per launch from a committed ncu summary, valid only while the kernel source
-    is unchanged (hash of the rowpass source and the device helpers it includes)."""
+    """DRAM bytes per CG iteration of the persistent CG kernel from a committed ncu summary,
+    valid only while the kernel source is unchanged (hash of its sources)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
-        h = rowpass_source_hash()
         rec = d.get(f"{kernel}|{workload}")
-        if rec and rec.get("source_hash") == h:
-            return rec["dram_bytes_per_launch"]
+        if rec and rec.get("source_hash") == cgloop_source_hash():
+            return rec["dram_bytes_per_iteration"]
     except (OSError, ValueError, KeyError):
         return None
     return None
@@ -221,7 +223,8 @@ def run_ours(args):
         return G.Solver(precision=p, stop_rule=G.STOP_KKT, eps_kkt=args.eps_kkt,
                         sketch_rank=P.sketch_rank, rho=rho, max_iter=args.max_iter,
                         profile=1 if args.no_graphs else profile,
-                        use_graphs=0 if args.no_graphs else 1)
+                        use_graphs=0 if args.no_graphs else 1,
+                        persistent_cg=0 if args.per_kernel_cg else 1)
 
     s = solver(prec)
     s.set_data(Ad, bd, P.loss)
@@ -247,34 +250,57 @@ def run_ours(args):
     ms_step = ms_total / args.steps
     status_ok = all(i["status"] == 0 for i in infos)
 
-    # roofline of the dominant kernel, the fused Hv rowpass.  Inside the timed region it runs in
-    # the CUDA graph of the CG loop and is timed on the device (globaltimer, first CTA start to
-    # last CTA end, every launch); one extra solve on the host-driven path times it with CUDA
-    # events on the launching stream as a cross-check.
-    hv_ms = sum(i["hv_ms"] for i in infos)
-    hv_n = sum(i["hv_launches"] for i in infos)
-    hv_avg_ms = hv_ms / max(1, hv_n)
-    hv_bytes = infos[0]["hv_bytes"]
+    # roofline of the dominant kernel, the persistent CG kernel (one launch per x-step; each CG
+    # iteration streams A once).  Inside the timed region every launch is timed on the device
+    # (globaltimer of CTA 0, launch start to end); one extra solve with profile = 1 times each
+    # launch with CUDA events on its stream as a cross-check.
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    achieved = hv_bytes / (hv_avg_ms * 1e-3) / 1e9 if hv_n and hv_ms > 0 else None
-    ev_achieved = ev_avg_us = None
-    if not args.no_event_leg:
-        sp = solver(prec, profile=1)
-        sp.set_data(Ad, bd, P.loss)
-        _, ip = sp.solve(lam)
-        sp.close()
-        if ip["hv_launches"]:
-            ev_avg_us = ip["hv_ms"] / ip["hv_launches"] * 1e3
-            ev_achieved = hv_bytes / (ev_avg_us * 1e-6) / 1e9
-    roof = {"bound": "hbm", "kernel": "rowpass_kernel<FP32,Hv>", "achieved": achieved, "peak": hbm,
-            "peak_kind": f"{peak_kind} STREAM copy (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-            "unit": "GB/s", "frac": achieved / hbm if achieved else None,
-            "traffic": traffic_record("rowpass_hv_fp32", args.workload),
-            "bytes_per_launch": hv_bytes, "avg_launch_us": hv_avg_ms * 1e3,
-            "launches": hv_n, "timing": "device globaltimer per launch inside the timed region",
-            "achieved_cuda_events": ev_achieved, "avg_launch_us_cuda_events": ev_avg_us,
-            "cuda_events_leg": "one extra solve, host-driven CG loop, events around each Hv launch"}
+    hv_bytes = infos[0]["hv_bytes"]
+    cg_it = sum(i["cg_iters_total"] for i in infos)
+    cg_ms = sum(i["cg_ms"] for i in infos)
+    cg_n = sum(i["cg_launches"] for i in infos)
+    hv_ms = sum(i["hv_ms"] for i in infos)
+    hv_n = sum(i["hv_launches"] for i in infos)
+    if cg_n:
+        it_per_launch = cg_it / cg_n
+        bytes_launch = it_per_launch * hv_bytes
+        avg_ms = cg_ms / cg_n
+        achieved = bytes_launch / (avg_ms * 1e-3) / 1e9 if cg_ms > 0 else None
+        ev_achieved = ev_avg_us = None
+        if not args.no_event_leg:
+            sp = solver(prec, profile=1)
+            sp.set_data(Ad, bd, P.loss)
+            _, ip = sp.solve(lam)
+            sp.close()
+            if ip["cg_launches"] and ip["cg_ms"] > 0:
+                ev_avg_us = ip["cg_ms"] / ip["cg_launches"] * 1e3
+                ev_achieved = (ip["cg_iters_total"] * hv_bytes) / (ip["cg_ms"] * 1e-3) / 1e9
+        tpi = traffic_record("cgloop_fp32", args.workload) if args.precision == "fp32" else None
+        ph = [sum(i["cg_phase_ms"][k] for i in infos) * 1e3 / max(1, cg_it) for k in range(6)]
+        roof = {"bound": "hbm", "kernel": "cgloop_kernel<FP32> (persistent CG, one launch per x-step)",
+                "achieved": achieved, "peak": hbm,
+                "peak_kind": f"{peak_kind} STREAM copy (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "unit": "GB/s", "frac": achieved / hbm if achieved else None,
+                "traffic": tpi * it_per_launch if tpi else None,
+                "bytes_per_launch": bytes_launch, "bytes_per_cg_iteration": hv_bytes,
+                "cg_iterations_per_launch": it_per_launch, "avg_launch_us": avg_ms * 1e3, "launches": cg_n,
+                "timing": "device globaltimer per launch inside the timed region",
+                "achieved_cuda_events": ev_achieved, "avg_launch_us_cuda_events": ev_avg_us,
+                "cuda_events_leg": "one extra solve (profile = 1), events around each persistent CG launch",
+                "hv_phase": {"avg_us": hv_ms / hv_n * 1e3 if hv_n else None,
+                             "gbs": hv_bytes / (hv_ms / hv_n * 1e-3) / 1e9 if hv_n and hv_ms > 0 else None,
+                             "note": "the A-streaming phase of each CG iteration, first CTA start to last CTA end"},
+                "phase_us_per_cg_iteration": dict(zip(["hv_cta0", "barrier_after_hv", "update", "barrier_after_update",
+                                                       "direction", "barrier_after_direction"], ph))}
+    else:   # per-kernel CG path (--per-kernel-cg): the Hv rowpass launches
+        hv_avg_ms = hv_ms / max(1, hv_n)
+        achieved = hv_bytes / (hv_avg_ms * 1e-3) / 1e9 if hv_n and hv_ms > 0 else None
+        roof = {"bound": "hbm", "kernel": "rowpass_kernel<FP32,Hv>", "achieved": achieved, "peak": hbm,
+                "peak_kind": "measured STREAM copy" if peak_kind == "measured" else "fallback",
+                "unit": "GB/s", "frac": achieved / hbm if achieved else None, "traffic": None,
+                "bytes_per_launch": hv_bytes, "avg_launch_us": hv_avg_ms * 1e3, "launches": hv_n,
+                "timing": "device globaltimer per launch inside the timed region"}
     grad_n = sum(i["grad_launches"] for i in infos)
     launches = sum(i["kernel_launches"] for i in infos)
 
@@ -484,6 +510,27 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_pcg_capture(args):
+    """One PCG solve of exactly N iterations (relative tolerance 0) through genios_op_pcg on the
+    workload's A in FP32: the persistent CG kernel's launch, for ncu captures.  Prints one line."""
+    import torch
+    import paper_2310_08333_gb300 as G
+    P = make_problem(args.workload, seed_k=0)
+    n = P.n
+    Ad = G.ops.pad(torch.from_numpy(P.A.astype(np.float32)), G.FP32).cuda()
+    rng = np.random.default_rng(11)
+    d = torch.from_numpy(rng.uniform(0.05, 0.25, P.m).astype(np.float32)).cuda()
+    r = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).cuda()
+    Om = G.ops.omega(G.FP32, n, P.sketch_rank, seed=8)
+    U, lam, _ = G.ops.nystrom(G.FP32, Ad, n, P.sketch_rank, d, Om)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, it, rel = G.ops.pcg(G.FP32, Ad, n, d, 1.0, r, U, lam, rtol=0.0, max_iter=args.pcg_capture)
+    torch.cuda.synchronize()
+    print(json.dumps({"pcg_capture": {"iterations": it, "rel_res": rel, "wall_ms": (time.perf_counter() - t0) * 1e3,
+                                      "m": P.m, "n": n, "s": P.sketch_rank}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -498,6 +545,11 @@ def main():
     ap.add_argument("--variant-list", default="bf16,fp8")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--per-kernel-cg", action="store_true",
+                    help="one Hv launch plus vector kernels per CG iteration instead of the persistent CG kernel")
+    ap.add_argument("--pcg-capture", type=int, default=0,
+                    help="profiling target: one persistent PCG launch of exactly N iterations on the workload's A "
+                         "(rank-s Nystrom preconditioner, logistic-like weights), then exit")
     ap.add_argument("--extra", action="store_true", help="also time the other workloads (configs 2, 4, 5)")
     ap.add_argument("--cfg5-problems", type=int, default=4)
     ap.add_argument("--no-event-leg", action="store_true")
@@ -505,6 +557,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=25.0)
     args = ap.parse_args()
+    if args.pcg_capture > 0:
+        run_pcg_capture(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

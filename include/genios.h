@@ -112,7 +112,8 @@ typedef struct genios_options {
     uint64_t seed;           /* seed of the Gaussian test matrix (Philox4x32-10) */
     int64_t device_wait_limit_us; /* bound on any device-side wait (default 2e6 us) */
     int32_t verbose;         /* 0 silent; N > 0: log every N-th iteration to stderr */
-    int32_t profile;         /* 1: time the rowpass kernels with CUDA events (info.hv_ms...) */
+    int32_t profile;         /* 1: time the gradient passes and the CG launches with CUDA events
+                                (info.grad_ms, info.cg_ms; per Hv launch on the per-kernel path) */
     int32_t tensor_sketch;   /* 1 (default): float value types sketch A^T D A Omega on the tensor
                                 cores (bf16 operands, genios_op_sketch); 0: CUDA-core sketch in
                                 the streaming precision */
@@ -154,7 +155,8 @@ typedef struct genios_info {
     double grad_ms;          /* their total device time (profile = 1), else 0 */
     double hv_bytes;         /* algorithmic bytes of one Hv launch (A once + vectors) */
     int64_t cg_launches;     /* persistent CG launches (persistent_cg = 1), else 0 */
-    double cg_ms;            /* their total device time (first CTA start to end), else 0 */
+    double cg_ms;            /* their total time: CUDA events around each launch on its stream
+                                (profile = 1), else the device's globaltimer (CTA 0, start to end) */
     double cg_phase_ms[6];   /* the device time of CTA 0 in those launches by phase: Hv pass,
                                 barrier, residual update, barrier, new direction, barrier */
 } genios_info;

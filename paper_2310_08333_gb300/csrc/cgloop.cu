@@ -123,17 +123,30 @@ GENIOS_DEV VT strided_sum(const VT* X, size_t ld, int k, int h, int step, int G)
     return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
-// The CTA's partial [scalar, U_slice^T v_slice] into out[0 .. sk].  vsl: the slice of v in shared
-// memory (published by the caller's last barrier); U rows j0 .. j0 + ns - 1.
+// Rows jb, jb + 4, ..., jb + 60 of the CTA's slice of U at column threadIdx.x % 128 (zero past the
+// slice or past column s).
 template <typename VT>
-GENIOS_DEV void slice_partial(const VT* U, int sk, int64_t j0, int ns, VT scalar, VT* out, CglShared<VT>& sh) {
+GENIOS_DEV void slice_u_rows(const VT* U, int sk, int64_t j0, int ns, int jb, VT (&u)[16]) {
+    const int c = threadIdx.x & 127;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) u[t] = (c < sk && jb + 4 * t < ns) ? U[(j0 + jb + 4 * t) * sk + c] : VT(0);
+}
+
+// The CTA's partial [scalar, U_slice^T v_slice] into out[0 .. sk].  vsl: the slice of v in shared
+// memory (published by the caller's last barrier); U rows j0 .. j0 + ns - 1, the first 16 of the
+// thread's rows (jb = threadIdx.x / 128) already in u0.
+template <typename VT>
+GENIOS_DEV void slice_partial(const VT* U, int sk, int64_t j0, int ns, VT scalar, VT* out, CglShared<VT>& sh,
+                              const VT (&u0)[16]) {
     const int tid = threadIdx.x, c = tid & 127, h = tid >> 7;
     VT acc[4] = {VT(0), VT(0), VT(0), VT(0)};
     if (c < sk) {
-        for (int jb = h; jb < ns; jb += 64) {   // 16 rows of U in flight
-            VT u[16];
 #pragma unroll
-            for (int t = 0; t < 16; ++t) u[t] = jb + 4 * t < ns ? U[(j0 + jb + 4 * t) * sk + c] : VT(0);
+        for (int t = 0; t < 16; ++t)
+            if (h + 4 * t < ns) acc[t & 3] = fma(u0[t], sh.vsl[h + 4 * t], acc[t & 3]);
+        for (int jb = h + 64; jb < ns; jb += 64) {
+            VT u[16];
+            slice_u_rows(U, sk, j0, ns, jb, u);
 #pragma unroll
             for (int t = 0; t < 16; ++t)
                 if (jb + 4 * t < ns) acc[t & 3] = fma(u[t], sh.vsl[jb + 4 * t], acc[t & 3]);
@@ -157,6 +170,8 @@ GENIOS_DEV void cg_start(const CgLoopArgs& a, CglShared<VT>& sh) {
     VT* u = static_cast<VT*>(a.u);
     VT* r = static_cast<VT*>(a.r);
     VT* delta = static_cast<VT*>(a.delta);
+    VT u0[16];
+    slice_u_rows(static_cast<const VT*>(a.U), a.sk, j0, ns, tid >> 7, u0);
     VT rr = VT(0);
     for (int jj = tid; jj < ns; jj += RP_CTHREADS) {
         const int64_t j = j0 + jj;
@@ -170,7 +185,30 @@ GENIOS_DEV void cg_start(const CgLoopArgs& a, CglShared<VT>& sh) {
     }
     named_bar_sync(1, RP_CTHREADS);
     slice_partial<VT>(static_cast<const VT*>(a.U), a.sk, j0, ns, rr,
-                      static_cast<VT*>(a.part) + (size_t)blockIdx.x * CGL_ST, sh);
+                      static_cast<VT*>(a.part) + (size_t)blockIdx.x * CGL_ST, sh, u0);
+}
+
+// Rows jb + 16 t (t < 4) of the CTA's slice for the new direction: U row entries at columns
+// lane + 32 k (zero past s), and in lane 0 r_j and p_j.
+template <typename VT>
+GENIOS_DEV void dir_rows_load(const CgLoopArgs& a, int64_t j0, int ns, int jb, VT (&ur)[4][4], VT (&rv)[4],
+                              VT (&pv)[4]) {
+    const int lane = threadIdx.x & 31, sk = a.sk;
+    const VT* U = static_cast<const VT*>(a.U);
+    const VT* r = static_cast<const VT*>(a.r);
+    const VT* p = static_cast<const VT*>(a.p);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int jj = jb + t * RP_CWARPS;
+        const int64_t j = j0 + jj;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = lane + 32 * k;
+            ur[t][k] = (jj < ns && c < sk) ? U[j * sk + c] : VT(0);
+        }
+        rv[t] = (jj < ns && lane == 0) ? r[j] : VT(0);
+        pv[t] = (jj < ns && lane == 0) ? p[j] : VT(0);
+    }
 }
 
 // P: w = U^T r and ||r||^2 from the partials, the stop test, c, r^T z, beta, and on the slice
@@ -181,6 +219,8 @@ GENIOS_DEV bool cg_direction(const CgLoopArgs& a, CglShared<VT>& sh) {
     const int G = gridDim.x, sk = a.sk;
     const VT nu = (VT)a.nu;
     const VT* partW = static_cast<const VT*>(a.part);
+    const int64_t j0 = sh.j0;
+    const int ns = sh.ns;
     {   // sum of the G partial rows [||r||^2, U^T r]: 16-byte columns x row groups, 8 loads in flight
         constexpr int VW = 16 / sizeof(VT);
         const int nq = (sk + 1 + VW - 1) / VW;
@@ -223,6 +263,8 @@ GENIOS_DEV bool cg_direction(const CgLoopArgs& a, CglShared<VT>& sh) {
         const VT c = ((ls + nu) / (sh.lamsh[tid] + nu) - VT(1)) * w;
         sh.csh[tid] = c;
         cw = c * w;
+    } else if (tid < 128) {
+        sh.csh[tid] = VT(0);
     }
     const bool start = sh.start != 0;
     const VT rz_old = sh.rz_old;
@@ -239,27 +281,21 @@ GENIOS_DEV bool cg_direction(const CgLoopArgs& a, CglShared<VT>& sh) {
     }
     const VT beta = (!start && rz_old > VT(0)) ? rz / rz_old : VT(0);
     if (!done) {
-        const int64_t j0 = sh.j0;
-        const int ns = sh.ns;
-        const VT* U = static_cast<const VT*>(a.U);
         const VT* mask = static_cast<const VT*>(a.mask);
-        const VT* r = static_cast<const VT*>(a.r);
         VT* p = static_cast<VT*>(a.p);
+        VT cl[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cl[k] = sh.csh[lane + 32 * k];
         VT pp = VT(0);
         for (int jb = wid; jb < ns; jb += 4 * RP_CWARPS) {   // four rows per warp in flight
-            VT acc[4], rv[4], pv[4];
+            VT ur[4][4], rv[4], pv[4];
+            dir_rows_load(a, j0, ns, jb, ur, rv, pv);
+            VT acc[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                const int jj = jb + t * RP_CWARPS;
-                acc[t] = rv[t] = pv[t] = VT(0);
-                if (jj < ns) {
-                    const int64_t j = j0 + jj;
-                    if (lane == 0) {
-                        rv[t] = r[j];
-                        pv[t] = p[j];
-                    }
-                    for (int c = lane; c < sk; c += 32) acc[t] = fma(U[j * sk + c], sh.csh[c], acc[t]);
-                }
+                acc[t] = VT(0);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[t] = fma(ur[t][k], cl[k], acc[t]);
             }
 #pragma unroll
             for (int t = 0; t < 4; ++t) acc[t] = warp_sum(acc[t]);
@@ -311,6 +347,8 @@ GENIOS_DEV bool cg_step(const CgLoopArgs& a, CglShared<VT>& sh) {
     VT* r = static_cast<VT*>(a.r);
     VT* delta = static_cast<VT*>(a.delta);
     const int64_t ldp = a.rp.ldp;
+    VT u0[16];   // the first rows of U for the partial of U^T r, loaded with everything else
+    slice_u_rows(static_cast<const VT*>(a.U), a.sk, j0, ns, tid >> 7, u0);
     VT rl = VT(0), pq = VT(0), alpha = VT(0);
     for (int cb = 0; cb < max(ns, 1); cb += 64) {   // at least once: pq is formed in every CTA
         // every load of the chunk at once: 8 row groups x 64 columns of the partials y_b, the
@@ -370,7 +408,7 @@ GENIOS_DEV bool cg_step(const CgLoopArgs& a, CglShared<VT>& sh) {
         if (tid == 0) sh.pq = pq;
         return false;
     }
-    slice_partial<VT>(static_cast<const VT*>(a.U), a.sk, j0, ns, rl, partW + (size_t)blockIdx.x * CGL_ST, sh);
+    slice_partial<VT>(static_cast<const VT*>(a.U), a.sk, j0, ns, rl, partW + (size_t)blockIdx.x * CGL_ST, sh, u0);
     if (tid == 0) {
         sh.pq = pq;
         sh.alpha = alpha;

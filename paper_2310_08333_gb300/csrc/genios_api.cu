@@ -763,6 +763,8 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
     ctx->launches = 0;
     std::vector<float> hv_ms;
     bool cg_pending = false;   // a deferred CG whose iteration count is read at the next sync
+    bool cg_ev_pending = false;   // profile: events around the last persistent CG launch
+    double cg_ev_ms = 0.0;
 
     if (!warm_start || !ctx->solved) {
         CK(cudaMemsetAsync(ctx->x, 0, vbytes, s));
@@ -808,6 +810,12 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
             inf.hv_launches += ctx->Sh->cg_it;
             ctx->launches += (int64_t)ctx->Sh->cg_guard * 4;
             cg_pending = false;
+        }
+        if (cg_ev_pending) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ctx->evs[4], ctx->evs[5]));
+            cg_ev_ms += ms;
+            cg_ev_pending = false;
         }
         if (o.profile) {
             float ms = 0.f;
@@ -900,9 +908,21 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
         // ---- x-step rhs, CG
         const int sk_now = use_pc && ctx->have_precond ? ctx->sk : 0;
         int cgit = 0;
-        if (ctx->cgl.ok && !o.profile) {   // the whole CG solve in one launch; its count is read later
+        if (ctx->cgl.ok) {   // the whole CG solve in one launch; its count is read at the next sync
+            if (o.profile) {   // CUDA events around the launch on its stream
+                while (ctx->evs.size() < 6) {
+                    cudaEvent_t e;
+                    CK(cudaEventCreate(&e));
+                    ctx->evs.push_back(e);
+                }
+                CK(cudaEventRecord(ctx->evs[4], s));
+            }
             CK(cg_persistent(ctx, dvec, ctx->g, ctx->x, ctx->z, ctx->u, rho, u_scale, nu, tol, o.max_cg_iter,
                              sk_now, nullptr));
+            if (o.profile) {
+                CK(cudaEventRecord(ctx->evs[5], s));
+                cg_ev_pending = true;
+            }
             cgit = -1;
         } else {
             CK(cgv_start(ctx->dbl, ctx->cgv, n, ctx->g, ctx->x, ctx->z, ctx->u, rho, u_scale, nu, tol,
@@ -942,10 +962,17 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
     genios_status rs = read_state(ctx);
     if (rs != GENIOS_OK) return rs;
     if (cg_pending) {
+        if (ctx->Sh->cg_fault) FAIL(GENIOS_ETIMEOUT, "CG vector kernel: a bounded device wait ran out");
         inf.cg_iters_total += ctx->Sh->cg_it;
         inf.hv_launches += ctx->Sh->cg_it;
         ctx->launches += (int64_t)ctx->Sh->cg_guard * 4;
         cg_pending = false;
+    }
+    if (cg_ev_pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->evs[4], ctx->evs[5]));
+        cg_ev_ms += ms;
+        cg_ev_pending = false;
     }
     inf.iters = iters;
     inf.rho = rho;
@@ -954,12 +981,12 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
     inf.t_solve_ms = now_ms() - t_start;
     inf.kernel_launches = ctx->launches;
     for (float ms : hv_ms) inf.hv_ms += ms;
-    if ((ctx->opt.use_graphs || ctx->cgl.ok) && !o.profile && ctx->Sh->hv_count > 0) {
+    if ((ctx->cgl.ok || (ctx->opt.use_graphs && !o.profile)) && ctx->Sh->hv_count > 0) {
         inf.hv_ms = ctx->Sh->hv_ns * 1e-6;   // device-timed Hv passes (graph launches or CG phases)
         inf.hv_launches = ctx->Sh->hv_count;
     }
     inf.cg_launches = ctx->Sh->cgl_count;
-    inf.cg_ms = ctx->Sh->cgl_ns * 1e-6;
+    inf.cg_ms = o.profile ? cg_ev_ms : ctx->Sh->cgl_ns * 1e-6;
     for (int k = 0; k < 6; ++k) inf.cg_phase_ms[k] = ctx->Sh->cgl_phase_ns[k] * 1e-6;
     {
         const size_t es = ctx->prec == GENIOS_FP64 ? 8 : ctx->prec == GENIOS_FP32 ? 4
