@@ -79,8 +79,9 @@ enum {
     GENIOS_STOP_GAP = 2,   /* App. A relative duality gap (min-denominator form) <= eps_gap */
     GENIOS_STOP_KKT = 4    /* relative KKT residual at z, ||dist(0, dF(z))|| / max(||grad f(z)||,
                               lambda_1) <= eps_kkt (one extra pass over A per check; checked
-                              when the residual test passes and every kkt_check_every
-                              iterations) */
+                              when the residual test first passes, then at intervals of 1 to
+                              kkt_check_every iterations predicted from the decrease between
+                              the last two checks) */
 };
 
 typedef struct genios_options {
@@ -107,7 +108,8 @@ typedef struct genios_options {
     int32_t max_cg_iter;     /* CG iterations per x-subproblem (default 50) */
     int32_t stop_rule;       /* GENIOS_STOP_* bitmask (default GENIOS_STOP_KKT) */
     int32_t precision;       /* genios_precision (default GENIOS_FP32) */
-    int32_t kkt_check_every; /* with STOP_KKT: also check every this many iterations (default 10) */
+    int32_t kkt_check_every; /* with STOP_KKT: at most this many iterations between checks
+                                (default 10) */
     int32_t use_graphs;      /* capture the CG loop in a CUDA graph (default 1) */
     uint64_t seed;           /* seed of the Gaussian test matrix (Philox4x32-10) */
     int64_t device_wait_limit_us; /* bound on any device-side wait (default 2e6 us) */

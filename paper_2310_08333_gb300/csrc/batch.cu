@@ -15,7 +15,7 @@
 // U^T R and U C products stage U in shared memory once per row block for all K columns.
 #include "common.cuh"
 #include "internal.h"
-#include "../../include/genios.h"
+#include "genios.h"
 
 #include <algorithm>
 #include <cmath>
@@ -510,7 +510,8 @@ BatchResult batch_path_solve(const BatchInput& in, std::vector<::genios_info>& i
     cudaMemsetAsync(c.err, 0, 256, s);
     std::vector<BState> h(K);
     std::vector<double> rho(K, in.rho0);
-    std::vector<int> n_rho(K, 0), iters(K, 0), conv(K, 0), kkt_last(K, -1000000);
+    std::vector<int> n_rho(K, 0), iters(K, 0), conv(K, 0);
+    std::vector<KktSchedule> kkt(K, KktSchedule(in.kkt_every, -1000000));
     std::vector<double> last_rp(K, 0.0), last_rd(K, 0.0);
     for (int k = 0; k < K; ++k) {
         BState& b = h[k];
@@ -569,7 +570,7 @@ BatchResult batch_path_solve(const BatchInput& in, std::vector<::genios_info>& i
                 last_rd[k] = rd;
                 const bool resid_ok = rp <= sqn * in.eps_abs + in.eps_rel * std::max(std::sqrt(b.x2), std::sqrt(b.z2)) &&
                                       rd <= sqn * in.eps_abs + in.eps_rel * std::sqrt(b.rhou2);
-                if ((resid_ok && k_iter - kkt_last[k] >= 1) || k_iter - kkt_last[k] >= std::max(1, in.kkt_every)) {
+                if (kkt[k].due(k_iter, resid_ok)) {
                     check[k] = 1;
                     need_kkt = true;
                 }
@@ -584,9 +585,9 @@ BatchResult batch_path_solve(const BatchInput& in, std::vector<::genios_info>& i
             if ((e = pull()) != cudaSuccess) break;
             for (int k = 0; k < K; ++k) {
                 if (!check[k]) continue;
-                kkt_last[k] = k_iter;
                 BState& b = h[k];
                 const double rk = std::sqrt(b.kd2) / std::max(std::max(std::sqrt(b.kg2), b.lam1), 1e-30);
+                kkt[k].record(k_iter, rk, in.eps_kkt);
                 info[k].rel_kkt = rk;
                 if (rk <= in.eps_kkt) {
                     b.active = 0;

@@ -416,6 +416,83 @@ GENIOS_DEV bool cg_step(const CgLoopArgs& a, CglShared<VT>& sh) {
     return true;
 }
 
+// The z/u update of §2.5 / Eq. (5) after the x-step, on the CTA's slice: x += delta,
+// x_hat = alpha x + (1 - alpha) z, z = S_{lambda_1 / rho}(x_hat + u), u += x_hat - z; and the norms
+// ||x - z||^2, ||x||^2, ||z||^2, ||u||^2, ||z||_1, nnz(z) into DevState.  The CTA partials (float64)
+// are summed in a fixed order by the last CTA to finish, so no grid barrier is needed.
+template <typename VT>
+GENIOS_DEV void zu_phase(const CgLoopArgs& a, CglShared<VT>& sh) {
+    __shared__ double zsh[RP_CWARPS][6];
+    __shared__ int last;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int G = gridDim.x;
+    const int64_t j0 = sh.j0;
+    const int ns = sh.ns;
+    VT* x = static_cast<VT*>(a.zu_x);
+    VT* z = static_cast<VT*>(a.zu_z);
+    VT* u = static_cast<VT*>(a.u);
+    const VT* delta = static_cast<const VT*>(a.delta);
+    const double kappa = a.zu_lam1 / a.zu_rho;
+    const double alpha = a.zu_alpha;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int jj = tid; jj < ns; jj += RP_CTHREADS) {
+        const int64_t j = j0 + jj;
+        const VT xj = x[j] + delta[j];
+        x[j] = xj;
+        const VT zj = z[j];
+        const VT xh = (VT)alpha * xj + (VT)(1.0 - alpha) * zj;
+        const VT vv = xh + u[j];
+        VT zn;
+        if (vv > (VT)kappa) zn = vv - (VT)kappa;
+        else if (vv < -(VT)kappa) zn = vv + (VT)kappa;
+        else zn = VT(0);
+        const VT un = u[j] + xh - zn;
+        z[j] = zn;
+        u[j] = un;
+        const double dxz = (double)xj - (double)zn;
+        v[0] += dxz * dxz;
+        v[1] += (double)xj * (double)xj;
+        v[2] += (double)zn * (double)zn;
+        v[3] += (double)un * (double)un;
+        v[4] += fabs((double)zn);
+        v[5] += zn != VT(0) ? 1.0 : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) zsh[wid][k] = v[k];
+    named_bar_sync(1, RP_CTHREADS);
+    double* zpart = a.zu_part;
+    if (tid == 0) {
+        double t[6] = {0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < RP_CWARPS; ++w)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) t[k] += zsh[w][k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) zpart[(size_t)blockIdx.x * 6 + k] = t[k];
+        __threadfence();
+        last = atomicAdd(a.bar + 1, 1u) == (unsigned)(G - 1) ? 1 : 0;
+    }
+    named_bar_sync(1, RP_CTHREADS);
+    if (!last) return;
+    __threadfence();
+    if (wid < 6) {   // warp k sums norm k over the CTAs in a fixed order
+        double t = 0.0;
+        for (int bb = lane; bb < G; bb += 32) t += __ldcg(zpart + (size_t)bb * 6 + wid);
+        t = warp_sum(t);
+        if (lane == 0) {
+            DevState* S = a.S;
+            if (wid == 0) S->rp2 = t;
+            else if (wid == 1) S->x2 = t;
+            else if (wid == 2) S->z2 = t;
+            else if (wid == 3) S->u2 = t;
+            else if (wid == 4) S->z1 = t;
+            else S->nnz = t;
+        }
+    }
+}
+
 // CTA 0, thread 0 of a timed launch: adds the time since the last mark to phase k
 template <typename VT>
 GENIOS_DEV void phase_mark(const CgLoopArgs& a, CglShared<VT>& sh, int k) {
@@ -521,11 +598,11 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
     // ------------------------------------------------------------------ consumers
     const int lane = tid & 31;
     cg_start<VT>(a, sh);
-    bool ok = grid_sync(a, sh);
+    bool ok = grid_sync(a, sh);   // false once a wait ran out here or in another CTA
     int cs = 0, par = 0;   // stages consumed (the ring position), row-total scratch half
     while (ok && cg_direction<VT>(a, sh)) {
         phase_mark(a, sh, 4);
-        if (!grid_sync(a, sh)) break;
+        if (!(ok = grid_sync(a, sh))) break;
         phase_mark(a, sh, 5);
 
         // ---- H: y_b = A_b^T diag(d_b) A_b p
@@ -565,7 +642,10 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
         }
-        if (hfault) break;
+        if (hfault) {
+            ok = false;
+            break;
+        }
         {   // the partial y_b, and p^T y_b (summed over the CTAs: p^T A^T diag(d) A p)
             VT* Pout = static_cast<VT*>(rp.partial) + (int64_t)b * rp.ldp;
             VT py = VT(0);
@@ -589,7 +669,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
             if (tid == 0) atomicMax(&S->hv_t1, gtimer());
         }
         phase_mark(a, sh, 0);
-        if (!grid_sync(a, sh)) break;
+        if (!(ok = grid_sync(a, sh))) break;
         phase_mark(a, sh, 1);
         if (a.timed && b == 0 && tid == 0) {
             const unsigned long long t0 = S->hv_t0, t1 = S->hv_t1;
@@ -604,12 +684,14 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
         // ---- Q
         if (!cg_step<VT>(a, sh)) break;
         phase_mark(a, sh, 2);
-        if (!grid_sync(a, sh)) break;
+        if (!(ok = grid_sync(a, sh))) break;
         phase_mark(a, sh, 3);
     }
 
-    // ---- the producer stops; the result is in delta; one thread records the final scalars
+    // ---- the producer stops; the result is in delta
     if (tid == 0) *reinterpret_cast<volatile int32_t*>(&sh.stop) = 1;
+    if (ok && a.zu) zu_phase<VT>(a, sh);
+    // one thread records the final scalars
     if (b == 0 && tid == 0) {
         S->cg_it = sh.it;
         S->cg_done = 1;
@@ -690,6 +772,7 @@ CgLoopPlan cgloop_plan(int prec, int64_t m, int64_t n, int64_t lda, int sk) {
 }
 
 size_t cgloop_part_elems(int grid) { return (size_t)grid * (CGL_ST + 2); }
+size_t cgloop_zu_offset_bytes(int grid) { return ((size_t)grid * (CGL_ST + 2) * 8 + 255) & ~size_t(255); }
 
 template <int P, int NCH>
 static cudaError_t launch_cgl(const CgLoopArgs& a, const RowpassPlan& p, cudaStream_t s) {
@@ -728,7 +811,7 @@ cudaError_t cgloop_launch(const CgLoopPlan& pl, const CgLoopArgs& c, cudaStream_
     a.rp.mode = RP_HV;
     a.rp.smem_bytes = (long long)pl.rp.smem;
     a.rp.partial_len = (long long)pl.rp.grid * c.rp.ldp;
-    cudaError_t e = cudaMemsetAsync(c.bar, 0, sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), s);   // grid barrier, last-CTA count
     if (e != cudaSuccess) return e;
     switch (c.rp.prec) {
         case P_FP64: return dispatch_cgl<P_FP64>(a, pl.rp, s);

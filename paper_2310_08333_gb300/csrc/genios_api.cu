@@ -11,7 +11,7 @@
 // penalty update of §2.5.
 #include "common.cuh"
 #include "internal.h"
-#include "../../include/genios.h"
+#include "genios.h"
 
 #include <chrono>
 #include <cmath>
@@ -518,9 +518,12 @@ static cudaError_t hv_pass(genios_ctx* ctx, const void* v, const void* v_aux, co
 
 // One persistent CG solve (cgloop.cu) on r = -(g + rho (x - z + u_scale u)); the result is left in
 // ctx->delta and the final scalars in DevState (cg_it, rr, rhs2, ...).
+// zu: with the CG solve, the z/u update (x += delta; Eq. (5)) with penalty zu_rho, lambda_1 = zu_lam1
+// and relaxation zu_alpha on ctx->x, ctx->z, ctx->u.
 static cudaError_t cg_persistent(genios_ctx* ctx, const void* d, const void* g, const void* x, const void* z,
                                  void* u, double rho, double u_scale, double nu, double tol, int cg_max, int sk,
-                                 const void* mask) {
+                                 const void* mask, bool zu = false, double zu_rho = 1.0, double zu_lam1 = 0.0,
+                                 double zu_alpha = 1.0) {
     CgLoopArgs a{};
     a.rp.prec = hv_prec(ctx);
     a.rp.mode = RP_HV;
@@ -552,6 +555,14 @@ static cudaError_t cg_persistent(genios_ctx* ctx, const void* d, const void* g, 
     a.cg_max = cg_max;
     a.part = ctx->sc.part;
     a.bar = ctx->sc.counter + 32;
+    a.zu = zu ? 1 : 0;
+    a.zu_x = ctx->x;
+    a.zu_z = ctx->z;
+    a.zu_rho = zu_rho;
+    a.zu_lam1 = zu_lam1;
+    a.zu_alpha = zu_alpha;
+    a.zu_part = reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->sc.part) +
+                                          cgloop_zu_offset_bytes(ctx->cgl.rp.grid));
     a.S = ctx->S;
     a.timed = 1;
     ctx->launches++;
@@ -781,7 +792,7 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
     bool converged = false;
     int iters = 0;
     double last_rp = 0, last_rd = 0;
-    int kkt_last_checked = 1;
+    KktSchedule kkt(o.kkt_check_every, 1);
     const double sqn = std::sqrt((double)n);
     const double floor = cg_floor(ctx);
 
@@ -852,12 +863,8 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
                 inf.rel_gap = den > 0 ? (P - Dv) / den : INFINITY;
                 if (inf.rel_gap <= o.eps_gap) stop = true;
             }
-            // relative KKT at z: one extra pass over A, taken when the paper's residual test
-            // passes or every kkt_check_every iterations
-            if (!stop && (o.stop_rule & GENIOS_STOP_KKT) &&
-                ((resid_ok && k - kkt_last_checked >= 1) ||
-                 k - kkt_last_checked >= std::max(1, o.kkt_check_every))) {
-                kkt_last_checked = k;
+            // relative KKT at z: one extra pass over A, on the schedule of KktSchedule
+            if (!stop && (o.stop_rule & GENIOS_STOP_KKT) && kkt.due(k, resid_ok)) {
                 CK(grad_pass(ctx, ctx->z, nullptr, nullptr));
                 CK(kkt_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, n, ctx->z, lam2, lam1,
                               ctx->S, ctx->sc, s));
@@ -866,6 +873,7 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
                 st = read_state(ctx);
                 if (st != GENIOS_OK) return st;
                 inf.rel_kkt = std::sqrt(H.kd2) / std::max(std::max(std::sqrt(H.kg2), lam1), 1e-30);
+                kkt.record(k, inf.rel_kkt, o.eps_kkt);
                 if (inf.rel_kkt <= o.eps_kkt) stop = true;
             }
             if (o.verbose > 0 && (k % o.verbose == 0 || stop))
@@ -918,7 +926,7 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
                 CK(cudaEventRecord(ctx->evs[4], s));
             }
             CK(cg_persistent(ctx, dvec, ctx->g, ctx->x, ctx->z, ctx->u, rho, u_scale, nu, tol, o.max_cg_iter,
-                             sk_now, nullptr));
+                             sk_now, nullptr, /*zu=*/true, rho, lam1, o.alpha));
             if (o.profile) {
                 CK(cudaEventRecord(ctx->evs[5], s));
                 cg_ev_pending = true;
@@ -938,10 +946,12 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
         } else {
             cg_pending = true;
         }
-        // ---- z/u update (§2.5, §3.1, Eq. (5)); x <- x + delta
-        CK(zu_update(ctx->dbl, n, ctx->x, ctx->delta, ctx->z, ctx->u, rho, lam1, o.alpha, ctx->S, nullptr,
-                     ctx->sc, s));
-        ctx->launches++;
+        // ---- z/u update (§2.5, §3.1, Eq. (5)); x <- x + delta (inside the persistent CG launch)
+        if (!ctx->cgl.ok) {
+            CK(zu_update(ctx->dbl, n, ctx->x, ctx->delta, ctx->z, ctx->u, rho, lam1, o.alpha, ctx->S, nullptr,
+                         ctx->sc, s));
+            ctx->launches++;
+        }
     }
     ctx->rho = rho;
     ctx->solved = true;

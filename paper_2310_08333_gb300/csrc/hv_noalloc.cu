@@ -16,7 +16,7 @@
 // Nothing in the array needs to start at zero: every CTA overwrites its whole partial row.
 #include "common.cuh"
 #include "internal.h"
-#include "../../include/genios.h"
+#include "genios.h"
 
 #include <mutex>
 #include <string>

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -119,7 +120,7 @@ struct CgLoopArgs {
     const void* g;             // right-hand side r = -(g + rho (x - z + u_scale u))
     const void* x;
     const void* z;
-    void* u;                   // scaled in place by u_scale
+    void* u;                   // scaled in place by u_scale; updated by the z/u step (zu)
     void* r;
     void* delta;               // the solution (x-step), zeroed at the start
     void* p;
@@ -130,7 +131,12 @@ struct CgLoopArgs {
     double rho, u_scale, nu, tol;
     int cg_max;
     void* part;                // cgloop_part_elems(grid) value-type partials
-    unsigned* bar;             // grid-barrier counter (zeroed by cgloop_launch)
+    unsigned* bar;             // [0] grid-barrier counter, [1] last-CTA count (zeroed by cgloop_launch)
+    int zu;                    // 1: after the CG solve, the z/u update of Eq. (5) on zu_x, zu_z, u
+    void* zu_x;                // x (x += delta) and z, value type
+    void* zu_z;
+    double zu_rho, zu_lam1, zu_alpha;
+    double* zu_part;           // grid x 6 float64 partials of the z/u norms
     DevState* S;               // cg_fault must be 0 at launch; results: cg_it, rr, rz, ...
     int timed;                 // accumulate H-phase and launch device times in S
 };
@@ -138,6 +144,8 @@ struct CgLoopArgs {
 // ring that does not fit one CTA per SM); the caller then uses the per-kernel CG path.
 CgLoopPlan cgloop_plan(int prec, int64_t m, int64_t n, int64_t lda, int sk);
 size_t cgloop_part_elems(int grid);
+// byte offset in the partials buffer where the z/u norm partials start
+size_t cgloop_zu_offset_bytes(int grid);
 cudaError_t cgloop_launch(const CgLoopPlan& pl, const CgLoopArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
@@ -302,6 +310,35 @@ cudaError_t adj_outputs(bool dbl, int64_t m, int64_t n, const void* q, const voi
                         cudaStream_t s);
 
 // Lockstep regularisation path (batch.cu): K problems on one data set, squared loss, float32.
+// When to evaluate the relative KKT residual at z (one extra pass over A per check): once when the
+// residual test of §2.3 first passes, and otherwise `gap` iterations after the previous check,
+// where gap is predicted from the decrease between the last two checks (the iterations a linear
+// rate needs to reach eps), at least 1 and at most `every`.
+struct KktSchedule {
+    int every, last, gap;
+    double v_last;
+    bool resid_seen;
+    KktSchedule(int every_, int last_) : every(every_ < 1 ? 1 : every_), last(last_), gap(every_ < 1 ? 1 : every_),
+                                         v_last(-1.0), resid_seen(false) {}
+    bool due(int k, bool resid_ok) {
+        const bool first = resid_ok && !resid_seen;
+        if (resid_ok) resid_seen = true;
+        return first || k - last >= gap;
+    }
+    void record(int k, double v, double eps) {
+        int g = every;
+        if (v_last > 0.0 && v > eps && v < v_last && k > last) {
+            const double rate = std::log(v / v_last) / (double)(k - last);   // < 0 per iteration
+            const double need = std::log(eps / v) / rate;
+            g = need < (double)every ? (int)std::ceil(need) : every;
+            if (g < 1) g = 1;
+        }
+        gap = g;
+        last = k;
+        v_last = v;
+    }
+};
+
 struct BatchInput {
     int64_t m, n, lda;
     int K, sk;
