@@ -132,10 +132,16 @@ def brute_force_lasso(A, b, lam1, lam2=0.0, tol=1e-9):
 
 
 def brute_force_logistic(A, b, lam1, lam2=0.0, tol=1e-8, newton_iters=60):
+    """brute_force_smooth with the logistic loss."""
+    return brute_force_smooth(A, b, "logistic", lam1, lam2, tol, newton_iters)
+
+
+def brute_force_smooth(A, b, loss, lam1, lam2=0.0, tol=1e-8, newton_iters=60):
     """Enumerate 3^n sign patterns; for each, minimise the smooth restricted objective
     sum l(A_S x_S - b) + lam1 s^T x_S + lam2/2 ||x_S||^2 by damped Newton, keep sign- and
-    KKT-consistent points, return the best."""
-    L = _losses.Logistic
+    KKT-consistent points, return the best.  Any loss with a continuous l' (the Huber loss's
+    l'' jumps at |w| = 1; the line search still converges)."""
+    L = _L(loss)
     m, n = A.shape
     assert n <= 12
     best, best_obj = None, np.inf
@@ -168,10 +174,9 @@ def brute_force_logistic(A, b, lam1, lam2=0.0, tol=1e-8, newton_iters=60):
             if np.any(np.sign(xs) != s[S]):
                 continue
             x[S] = xs
-        g = grad_f(A, b, x, "logistic", lam2)
-        if kkt_violation(A, b, x, "logistic", lam1, lam2) > tol * max(1.0, lam1):
+        if kkt_violation(A, b, x, L, lam1, lam2) > tol * max(1.0, lam1):
             continue
-        obj = objective(A, b, x, "logistic", lam1, lam2)
+        obj = objective(A, b, x, L, lam1, lam2)
         if obj < best_obj:
             best, best_obj = x, obj
     return best
@@ -182,9 +187,9 @@ def brute_force_logistic(A, b, lam1, lam2=0.0, tol=1e-8, newton_iters=60):
 # ----------------------------------------------------------------------------------------
 def fista(A, b, loss, lam1, lam2=0.0, max_iter=200000, tol=1e-13, x0=None):
     """Accelerated proximal gradient with function-value restart; step 1/L where
-    L = c ||A||_2^2 + lam2 (c = 1 squared, 1/4 logistic)."""
+    L = c ||A||_2^2 + lam2 (c = sup l'': 1 squared, 1/4 logistic, 2 Huber)."""
     L_ = _L(loss)
-    c = 1.0 if L_ is _losses.Squared else 0.25
+    c = L_.curvature
     Lip = c * np.linalg.norm(A, 2) ** 2 + lam2
     x = np.zeros(A.shape[1]) if x0 is None else x0.copy()
     y = x.copy()

@@ -23,6 +23,7 @@ SEED_BASE = 20231012
 
 SQUARED = "squared"
 LOGISTIC = "logistic"
+HUBER = "huber"
 
 
 @dataclass
@@ -32,8 +33,9 @@ class Problem:
     name: str
     A: np.ndarray            # (m, n) float64, row-major, rows a_i^T
     b: np.ndarray            # (m,)   float64
-    loss: str                # "squared" or "logistic"
-    lam_frac: float          # lambda_1 = lam_frac * lambda_max (lambda_max computed by each side)
+    loss: str                # "squared", "logistic" or "huber"
+    lam_frac: float          # lambda_1 = lam_frac * lambda_max (lambda_max computed by each side),
+                             # or lam_frac * ||A^T b||_inf when extra["lam_of"] == "atb_inf"
     mu: float = 0.0          # lambda_2 (elastic-net weight)
     rho: float = 1.0
     sketch_rank: int = 50
@@ -151,6 +153,27 @@ def logistic_lowrank(m: int = 20000, n: int = 8000, rank: int = 50, nnz: int = 4
                    sketch_rank, w_true, extra)
 
 
+def huber_outliers(n: int = 16000, m: int | None = None, density: float = 0.1, noise: float = 0.1,
+                   outlier_frac: float = 0.05, outlier_size: float = 10.0, lam_frac: float = 0.1,
+                   seed: int | None = None, cfg: int = 6, k: int = 0, sketch_rank: int = 50) -> Problem:
+    """The Huber fitting data of §4.4: m = n / 2 samples of n N(0, 1) features, columns
+    centred and scaled to unit l2 norm; a planted x with 10 % N(0, 1) nonzeros; b = A x + 0.1 v
+    with 5 % of its entries shifted by +-10 (outliers); lambda_1 = 0.1 ||A^T b||_inf."""
+    rng = np.random.default_rng(seed_for(cfg, k) if seed is None else seed)
+    m = n // 2 if m is None else m
+    A = rng.standard_normal((m, n))
+    A = A - A.mean(axis=0, keepdims=True)
+    A = A / np.linalg.norm(A, axis=0, keepdims=True)
+    x_true = np.zeros(n)
+    S = rng.choice(n, size=max(1, int(round(density * n))), replace=False)
+    x_true[S] = rng.standard_normal(S.size)
+    b = A @ x_true + noise * rng.standard_normal(m)
+    O = rng.choice(m, size=max(1, int(round(outlier_frac * m))), replace=False)
+    b[O] += outlier_size * rng.choice(np.array([-1.0, 1.0]), size=O.size)
+    return Problem(f"huber_{m}x{n}", A, b, HUBER, lam_frac, 0.0, 10.0, sketch_rank, x_true,
+                   {"lam_of": "atb_inf", "outliers": np.sort(O)})
+
+
 def lambda_path_fracs(K: int = 32, lo: float = 1e-3) -> np.ndarray:
     """K regularisation levels log-spaced from lambda_max down to lo * lambda_max."""
     return np.logspace(0.0, np.log10(lo), K)
@@ -173,4 +196,5 @@ CONFIGS = {
     3: "Dense l1-logistic 20000x8000 low rank (50) + 0.1 noise, 400 nonzeros, lambda=0.02 lambda_max, rank 100",
     4: "Batched: 32-level lambda path on a shared 5000x20000 AR(1) Lasso; 64 uneven Lasso problems",
     5: "Differentiation: 16 elastic-net logistic problems 8000x4000 (+2000 validation rows)",
+    6: "Huber fitting (§4.4): 8000x16000, unit centred columns, 10% N(0,1) nonzeros, 5% +-10 outliers, lambda=0.1 ||A^T b||_inf",
 }

@@ -18,7 +18,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 # ----------------------------------------------------------------------------- losses
-@pytest.mark.parametrize("name", ["squared", "logistic"])
+@pytest.mark.parametrize("name", ["squared", "logistic", "huber"])
 def test_loss_derivatives_by_finite_differences(name):
     L = losses.get(name)
     w = np.linspace(-8, 8, 101)
@@ -29,7 +29,7 @@ def test_loss_derivatives_by_finite_differences(name):
     np.testing.assert_allclose(L.d2(w), fd2, rtol=1e-6, atol=1e-9)
 
 
-@pytest.mark.parametrize("name", ["squared", "logistic"])
+@pytest.mark.parametrize("name", ["squared", "logistic", "huber"])
 def test_loss_conjugate_fenchel_young_equality(name):
     # l(w) + l*(l'(w)) = w l'(w) holds with equality for differentiable convex l
     L = losses.get(name)
@@ -44,6 +44,20 @@ def test_logistic_special_values_and_overflow():
     assert L.conj(0.5) == pytest.approx(-np.log(2.0), abs=1e-15)
     assert L.conj(0.0) == 0.0 and L.conj(1.0) == 0.0 and np.isinf(L.conj(1.5))
     assert L.value(1000.0) == pytest.approx(1000.0) and L.value(-1000.0) == 0.0
+
+
+def test_huber_special_values_and_conjugate_by_grid_search():
+    """The §4.4 loss: w^2 inside |w| <= 1, 2|w| - 1 outside; its conjugate is the supremum
+    sup_w (v w - l(w)), found here by a dense grid over w."""
+    L = losses.Huber
+    np.testing.assert_array_equal(L.value(np.array([0.0, 0.5, 1.0, 2.0, -3.0])), [0.0, 0.25, 1.0, 3.0, 5.0])
+    np.testing.assert_array_equal(L.d1(np.array([0.5, 1.0, 5.0, -5.0])), [1.0, 2.0, 2.0, -2.0])
+    np.testing.assert_array_equal(L.d2(np.array([0.3, -1.0, 1.5])), [2.0, 2.0, 0.0])
+    w = np.linspace(-60, 60, 1200001)
+    for v in (-2.0, -1.3, 0.0, 0.7, 2.0):
+        assert L.conj(v) == pytest.approx(np.max(v * w - L.value(w)), abs=1e-8)
+    # outside [-2, 2] the supremum grows without bound
+    assert np.isinf(L.conj(2.1)) and np.max(2.1 * w - L.value(w)) > 5.0
 
 
 # ----------------------------------------------------------------------------- prox
@@ -230,10 +244,39 @@ def test_logistic_matches_brute_force():
     np.testing.assert_allclose(r["z"], bf, atol=1e-7)
 
 
-@pytest.mark.parametrize("loss", ["squared", "logistic"])
+def test_huber_matches_brute_force():
+    """A small Huber fit with outliers (some residuals beyond the kink): the ADMM oracle and the
+    enumeration of sign patterns with a damped Newton on each support agree."""
+    P = problems.huber_outliers(n=6, m=30, density=0.5, outlier_frac=0.1, seed=21)
+    lam = 0.2 * np.max(np.abs(P.A.T @ P.b))
+    bf = checks.brute_force_smooth(P.A, P.b, "huber", lam)
+    r = admm.solve(P.A, P.b, "huber", lam, tol=1e-12, polish_below=None, max_iter=20000)
+    assert np.any(np.abs(P.A @ bf - P.b) > 1.0)           # the linear pieces are exercised
+    np.testing.assert_allclose(r["z"], bf, atol=1e-7)
+
+
+def test_huber_solution_kkt_gap_and_fista():
+    """§4.4 data (m = n/2, fewer samples than features: the oracle's x-step uses Woodbury).
+    rho = 10: the second-order model of a loss whose l'' jumps from 0 to 2 at the kink
+    under-estimates the curvature of rows that cross it, and a small penalty lets the x-step
+    overshoot (rho = 1 stalls near a 0.5 relative KKT residual on this instance)."""
+    P = problems.huber_outliers(n=160, seed=22)
+    lam = P.lam_frac * np.max(np.abs(P.A.T @ P.b))
+    r = admm.solve(P.A, P.b, "huber", lam, rho=P.rho, tol=1e-12, check_every=5)
+    assert r["converged"]
+    assert checks.kkt_violation(P.A, P.b, r["z"], "huber", lam) <= 1e-9 * max(1, lam)
+    assert r["gap"]["rel_gap_min"] <= 1e-9
+    f = checks.fista(P.A, P.b, "huber", lam, tol=1e-15, max_iter=100000)
+    F = checks.objective(P.A, P.b, r["z"], "huber", lam)
+    assert checks.objective(P.A, P.b, f, "huber", lam) >= F - 1e-9 * abs(F)
+
+
+@pytest.mark.parametrize("loss", ["squared", "logistic", "huber"])
 def test_lambda_max_threshold(loss):
     if loss == "squared":
         P = problems.lasso_iid(60, 150, nnz=6, seed=17)
+    elif loss == "huber":
+        P = problems.huber_outliers(n=120, seed=17)
     else:
         P = problems.logistic_lowrank(80, 60, rank=5, nnz=5, seed=17)
     lmax = checks.lambda_max(P.A, P.b, loss)
@@ -454,3 +497,9 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     B = Y @ np.linalg.inv(C).T
     Ub, sb, _ = np.linalg.svd(B, full_matrices=False)
     assert not np.allclose((Ub * sb ** 2) @ Ub.T, H, atol=1e-8 * ev[0])
+    # 5) the Huber derivative without its factor 2 fails the finite-difference pin
+    w = np.linspace(-3, 3, 61) + 0.013
+    h = 1e-6
+    fd1 = (losses.Huber.value(w + h) - losses.Huber.value(w - h)) / (2 * h)
+    assert np.allclose(losses.Huber.d1(w), fd1, atol=1e-6)
+    assert not np.allclose(np.clip(w, -1.0, 1.0), fd1, atol=1e-6)
