@@ -400,8 +400,9 @@ def run_ours(args):
 def extra_configs(G, torch, args) -> dict:
     """The other workloads of the measurement plan, one timed pass each (rank 0, --extra):
     the 1000 x 10000 AR(1) Lasso (FP32, BF16), the 32-level lambda path on a shared 5000 x 20000
-    Lasso and the 64 uneven Lasso problems (solved in one batched call each), and the
-    elastic-net logistic implicit gradient (solve + adjoint) on 8000 x 4000 problems."""
+    Lasso and the 64 uneven Lasso problems (solved in one batched call each), the
+    elastic-net logistic implicit gradient (solve + adjoint) on 8000 x 4000 problems, and the
+    §4.4 Huber fit at 8000 x 16000 (FP32, BF16)."""
     from oracle import losses
     res = {}
     sync = torch.cuda.synchronize
@@ -476,6 +477,22 @@ def extra_configs(G, torch, args) -> dict:
     res["implicit_grad_8000x4000_fp32"] = {"problems": args.cfg5_problems, "solve_s_mean": float(np.mean(ts)),
                                            "grad_s_mean": float(np.mean(tg)),
                                            "note": "grad = adjoint PCG on the support + outputs (dL/dlambda, dL/db)"}
+    # cfg 6: Huber fitting (§4.4) at the paper's largest size, 8000 x 16000 (512 MB in FP32)
+    P = problems.huber_outliers(16000)
+    A = torch.from_numpy(P.A.astype(np.float32)).cuda()
+    b = torch.from_numpy(P.b.astype(np.float32)).cuda()
+    lam = float(P.lam_frac * (A.T @ b).abs().max())   # lambda_1 = 0.1 ||A^T b||_inf (input set-up)
+    for name, prec in (("fp32", G.FP32), ("bf16", G.BF16)):
+        with G.Solver(precision=prec, stop_rule=G.STOP_KKT, eps_kkt=1e-4, sketch_rank=P.sketch_rank,
+                      rho=P.rho, max_iter=20000) as s:
+            s.set_data(A, b, "huber")
+            s.solve(lam)
+            el, (z, info) = tsolve(s, lambda: s.solve(lam))
+        res[f"huber_8000x16000_{name}"] = {
+            "time_s": el, "iters": info["iters"], "cg_iters": info["cg_iters_total"], "status": info["status_name"],
+            "rel_kkt": info["rel_kkt"], "nnz": info["nnz"],
+            "hv_gbs": (info["hv_bytes"] / (info["hv_ms"] / info["hv_launches"] * 1e-3) / 1e9) if info["hv_launches"] else None}
+    del A, b
     return res
 
 

@@ -50,7 +50,9 @@ typedef enum {
     GENIOS_EUNSUPPORTED = 8  /* valid request this build does not implement */
 } genios_status;
 
-typedef enum { GENIOS_LOSS_SQUARED = 0, GENIOS_LOSS_LOGISTIC = 1 } genios_loss;
+/* SQUARED l(w) = w^2/2 (§4.1); LOGISTIC l(w) = log(1 + e^w) (§4.2, rows label-signed);
+   HUBER l(w) = w^2 for |w| <= 1, 2|w| - 1 beyond (the Huber fitting loss of §4.4). */
+typedef enum { GENIOS_LOSS_SQUARED = 0, GENIOS_LOSS_LOGISTIC = 1, GENIOS_LOSS_HUBER = 2 } genios_loss;
 
 /* Precision in which A is stored and streamed by the Hessian-vector products.
  *   FP64: A and all vectors in float64.

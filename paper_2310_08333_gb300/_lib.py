@@ -15,7 +15,8 @@ LIB_PATH = os.environ.get("GENIOS_LIB") or os.path.join(_HERE, "libgenios.so")
 OK, EINVAL, ESTATE, ENOMEM, ECUDA, EMAXITER, ENUMERIC, ETIMEOUT, EUNSUPPORTED = range(9)
 STATUS_NAMES = ["OK", "EINVAL", "ESTATE", "ENOMEM", "ECUDA", "EMAXITER", "ENUMERIC", "ETIMEOUT",
                 "EUNSUPPORTED"]
-LOSS_SQUARED, LOSS_LOGISTIC = 0, 1
+LOSS_SQUARED, LOSS_LOGISTIC, LOSS_HUBER = 0, 1, 2
+LOSSES = {"squared": LOSS_SQUARED, "logistic": LOSS_LOGISTIC, "huber": LOSS_HUBER}
 FP64, FP32, BF16, FP8_E4M3 = 0, 1, 2, 3
 DT_F64, DT_F32, DT_BF16, DT_U8 = 0, 1, 2, 3
 STOP_RESID, STOP_GAP, STOP_KKT = 1, 2, 4

@@ -39,7 +39,7 @@ inline int64_t padded_lda(int P, int64_t n) {
 // ------------------------------------------------------------------------------------------
 // Loss functors (§3.3): value, first and second derivative.
 // ------------------------------------------------------------------------------------------
-enum LossKind { LOSS_SQUARED = 0, LOSS_LOGISTIC = 1 };
+enum LossKind { LOSS_SQUARED = 0, LOSS_LOGISTIC = 1, LOSS_HUBER = 2 };
 
 template <typename T> GENIOS_DEV T sigmoid_(T w);
 template <> GENIOS_DEV float sigmoid_<float>(float w) { return 1.0f / (1.0f + expf(-w)); }
@@ -51,6 +51,17 @@ GENIOS_DEV void loss_eval(int loss, T t, T& l0, T& l1, T& l2) {
         l0 = T(0.5) * t * t;
         l1 = t;
         l2 = T(1);
+    } else if (loss == LOSS_HUBER) {   // §4.4: t^2 inside |t| <= 1, 2|t| - 1 beyond
+        const T at = t < T(0) ? -t : t;
+        if (at <= T(1)) {
+            l0 = t * t;
+            l1 = T(2) * t;
+            l2 = T(2);
+        } else {
+            l0 = T(2) * at - T(1);
+            l1 = t < T(0) ? T(-2) : T(2);
+            l2 = T(0);
+        }
     } else {
         T s = sigmoid_<T>(t);
         // log(1 + e^t) = max(t, 0) + log1p(e^{-|t|})
@@ -64,6 +75,7 @@ GENIOS_DEV void loss_eval(int loss, T t, T& l0, T& l1, T& l2) {
 // Fenchel conjugate of the loss (App. A), +inf outside the domain.
 GENIOS_DEV double loss_conj(int loss, double v) {
     if (loss == LOSS_SQUARED) return 0.5 * v * v;
+    if (loss == LOSS_HUBER) return fabs(v) <= 2.0 ? 0.25 * v * v : __longlong_as_double(0x7ff0000000000000LL);
     if (v < 0.0 || v > 1.0) return __longlong_as_double(0x7ff0000000000000LL);
     double a = v > 0.0 ? v * log(v) : 0.0;
     double b = v < 1.0 ? (1.0 - v) * log1p(-v) : 0.0;

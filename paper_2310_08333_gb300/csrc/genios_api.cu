@@ -322,7 +322,8 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
                                   const void* const* A, int A_dtype, const int64_t* lda, const void* const* b) {
     if (!m || !n || !A || !lda || !b || !A[0] || !b[0]) FAIL(GENIOS_EINVAL, "NULL argument");
     if (m[0] < 1 || n[0] < 1 || lda[0] < n[0]) FAIL(GENIOS_EINVAL, "bad sizes");
-    if (loss != GENIOS_LOSS_SQUARED && loss != GENIOS_LOSS_LOGISTIC) FAIL(GENIOS_EINVAL, "bad loss");
+    if (loss != GENIOS_LOSS_SQUARED && loss != GENIOS_LOSS_LOGISTIC && loss != GENIOS_LOSS_HUBER)
+        FAIL(GENIOS_EINVAL, "bad loss");
     if (A_dtype != GENIOS_DT_F64 && A_dtype != GENIOS_DT_F32) FAIL(GENIOS_EINVAL, "A_dtype must be F64 or F32");
     CK(cudaSetDevice(ctx->device));
     const double t0 = now_ms();
@@ -1497,7 +1498,7 @@ extern "C" genios_status genios_op_gradient(int loss, int precision, int64_t m, 
                                             double* loss_sum_out, void* workspace, size_t workspace_bytes,
                                             void* stream) {
     if (!prec_valid(precision) || m < 1 || n < 1 || !A || !b || !x || !grad_out) return GENIOS_EINVAL;
-    if (loss != 0 && loss != 1) return GENIOS_EINVAL;
+    if (loss != GENIOS_LOSS_SQUARED && loss != GENIOS_LOSS_LOGISTIC && loss != GENIOS_LOSS_HUBER) return GENIOS_EINVAL;
     if (precision >= 2 && !A_lo) return GENIOS_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     OpWs w;

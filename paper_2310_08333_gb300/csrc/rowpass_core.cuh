@@ -39,7 +39,10 @@ GENIOS_DEV void rp_consume_stage(const RowpassArgs& a, const unsigned char* smem
     constexpr bool HILO = (P == P_HILO);
     constexpr bool FP8 = (P == P_FP8);
     constexpr int RB = rp_rb(P, NCH);
-    constexpr bool HOLD = (NCH * RB <= 8);
+    // the row group's chunks are held in registers between the dot and the update only while
+    // v, y and the held chunks fit in about 64 of the 96 registers a thread has (17 warps per
+    // CTA); wider rows re-read them from shared memory instead of spilling
+    constexpr bool HOLD = (NCH * RB <= 8) && (2 * NCH * VEC * (int)(sizeof(VT) / 4) + 4 * NCH * RB <= 64);
     constexpr bool PK = sizeof(VT) == 4 && !HILO;   // float32 lanes: packed f32x2 FMAs
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const VT* dvec = static_cast<const VT*>(a.d);

@@ -56,7 +56,7 @@ class Solver:
     # ------------------------------------------------------------------
     def set_data(self, A, b, loss: int | str = L.LOSS_SQUARED):
         if isinstance(loss, str):
-            loss = {"squared": L.LOSS_SQUARED, "logistic": L.LOSS_LOGISTIC}[loss]
+            loss = L.LOSSES[loss]
         if isinstance(A, np.ndarray):
             A = np.ascontiguousarray(A)
             b = np.ascontiguousarray(b, dtype=A.dtype)
@@ -74,7 +74,7 @@ class Solver:
         """Load a batch.  path_size = K: one data set (As[0], bs[0]) shared by K problems that
         differ in lambda (a regularisation path).  Otherwise: len(As) independent problems."""
         if isinstance(loss, str):
-            loss = {"squared": L.LOSS_SQUARED, "logistic": L.LOSS_LOGISTIC}[loss]
+            loss = L.LOSSES[loss]
         As = [np.ascontiguousarray(a) if isinstance(a, np.ndarray) else a for a in As]
         bs = [np.ascontiguousarray(b, dtype=a.dtype) if isinstance(b, np.ndarray) else b for a, b in zip(As, bs)]
         K = path_size if path_size is not None else len(As)

@@ -143,9 +143,34 @@ def test_elastic_net_logistic_parity(G):
     assert_parity(P, z, ref["z"], lam, 1e-3, "logistic", tol_z=tol, tol_f=max(1e-7, tol ** 2))
 
 
-@pytest.mark.parametrize("loss", ["squared", "logistic"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_huber_parity(G, prec):
+    """The Huber fitting problem of §4.4 (300 x 600, 5 % outliers of +-10, rho = 10): FP64 to
+    the 1e-5 bar; FP32 to the relative KKT residual (checked in float64 by the oracle at the
+    GPU's z) and the objective its stopping tolerance implies."""
+    P = problems.huber_outliers(n=600, seed=problems.seed_for(6, 1), sketch_rank=30)
+    A, b = rounded(P, prec)
+    lam = P.lam_frac * np.max(np.abs(A.T @ b))
+    ref = oadmm.solve(A, b, "huber", lam, rho=P.rho, tol=1e-13, check_every=5)
+    assert ref["converged"]
+    z, info, _ = gpu_solve(G, P, prec, lam, eps_kkt=1e-10 if prec == 0 else 1e-5)
+    assert info["status"] == 0, info
+    assert np.any(np.abs(A @ ref["z"] - b) > 1.0)   # outliers sit on the linear pieces
+    if prec == 0:
+        assert_parity(P, z, ref["z"], lam, 0.0, "huber")
+    else:
+        kkt = checks.rel_kkt(A, b, z, "huber", lam)
+        F = checks.objective(A, b, z, "huber", lam)
+        Fs = checks.objective(A, b, ref["z"], "huber", lam)
+        print(f"FP32 Huber: rel KKT {kkt:.2e} (GPU {info['rel_kkt']:.2e}), objective {abs(F - Fs) / Fs:.2e}")
+        assert kkt <= 3e-5
+        assert abs(F - Fs) <= 1e-5 * abs(Fs)
+
+
+@pytest.mark.parametrize("loss", ["squared", "logistic", "huber"])
 def test_lambda_above_lambda_max_gives_exact_zero(G, loss):
     P = (problems.lasso_iid(300, 800, nnz=10, seed=9) if loss == "squared"
+         else problems.huber_outliers(n=600, seed=9) if loss == "huber"
          else problems.logistic_lowrank(600, 300, nnz=10, seed=9))
     lmax = checks.lambda_max(*rounded(P, 1), loss)
     z, info, lmax_gpu = gpu_solve(G, P, 1, lmax * (1 + 1e-4))
