@@ -29,8 +29,8 @@ import numpy as np
 import scipy.linalg as sla
 
 from . import losses as _losses
-from .checks import rel_kkt, duality_gap, polish
-from .prox import soft_threshold
+from .checks import rel_kkt, rel_kkt_box, duality_gap, polish
+from .prox import project_box, soft_threshold
 
 
 class _ExactSolver:
@@ -76,7 +76,7 @@ class _ExactSolver:
 def solve(A, b, loss, lam1, lam2=0.0, rho=1.0, alpha=1.6, max_iter=20000, tol=1e-10,
           rho_update_every=25, rho_tau=2.0, rho_mu=10.0, max_rho_updates=20,
           rho_update_until=1000, check_every=1, time_limit=None, callback=None,
-          polish_below=1e-3, polish_tol=1e-11):
+          polish_below=1e-3, polish_tol=1e-11, box=None):
     """Run the reference ADMM until rel_kkt(z) <= tol (or max_iter / time_limit).
 
     Once rel_kkt <= ``polish_below`` (checked every ``check_every`` iterations), an exact
@@ -84,8 +84,17 @@ def solve(A, b, loss, lam1, lam2=0.0, rho=1.0, alpha=1.6, max_iter=20000, tol=1e
     optimality conditions to ``polish_tol`` the polished point is returned as the solution
     (z = x = polished point) and ``polished`` is True.
 
+    box = (lo, hi): g is the indicator of [lo, hi]^n instead of lam1 ||.||_1 (lam1 must be 0):
+    the z-step is the projection, the stop test the box KKT residual (rel_kkt_box), no polish,
+    no duality gap (the §4.5 bounded least squares).
+
     Returns dict(x, z, u, rho, iters, rel_kkt, gap, converged, polished, history)."""
+    if box is not None:
+        assert lam1 == 0.0, "the box replaces the l1 term"
+        polish_below = None
     L = _losses.get(loss) if isinstance(loss, str) else loss
+    kkt_of = ((lambda zz: rel_kkt_box(A, b, zz, L, box[0], box[1], lam2)) if box is not None
+              else (lambda zz: rel_kkt(A, b, zz, L, lam1, lam2)))
     m, n = A.shape
     x = np.zeros(n)
     z = np.zeros(n)
@@ -112,13 +121,13 @@ def solve(A, b, loss, lam1, lam2=0.0, rho=1.0, alpha=1.6, max_iter=20000, tol=1e
         # §2.5 over-relaxation, §3.1 prox, Eq. (5)
         xh = alpha * x + (1.0 - alpha) * z
         z_old = z
-        z = soft_threshold(xh + u, lam1 / rho)
+        z = project_box(xh + u, box[0], box[1]) if box is not None else soft_threshold(xh + u, lam1 / rho)
         u = u + xh - z
         # Eqs. (11)-(12) at the new iterate
         rp = np.linalg.norm(x - z)
         rd = np.linalg.norm(A.T @ L.d1(A @ x - b) + lam2 * x + rho * u)
         if it % check_every == 0:
-            kkt = rel_kkt(A, b, z, L, lam1, lam2)
+            kkt = kkt_of(z)
             hist.append((it, rp, rd, kkt, rho))
             if callback is not None:
                 callback(it, x, z, u, rho, kkt)
@@ -147,7 +156,7 @@ def solve(A, b, loss, lam1, lam2=0.0, rho=1.0, alpha=1.6, max_iter=20000, tol=1e
                 rho = new_rho
                 n_rho += 1
         del z_old
-    gap = duality_gap(A, b, z, L, lam1, lam2)
+    gap = duality_gap(A, b, z, L, lam1, lam2) if box is None else None
     return {"x": x, "z": z, "u": u, "rho": rho, "iters": it, "rel_kkt": kkt, "gap": gap,
             "converged": kkt <= tol or polished, "polished": polished, "history": hist,
             "seconds": time.perf_counter() - t0}

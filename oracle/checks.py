@@ -69,6 +69,26 @@ def rel_kkt(A, b, z, loss, lam1, lam2=0.0):
     return float(np.linalg.norm(d) / max(np.linalg.norm(g), lam1, 1e-30))
 
 
+def box_violation(g, z, lo, hi):
+    """Per-coordinate distance of 0 from g + N(z), N the normal cone of [lo, hi]^n at z:
+    |g_j| inside, max(-g_j, 0) at the lower bound, max(g_j, 0) at the upper bound."""
+    g = np.asarray(g, dtype=np.float64)
+    d = np.abs(g)
+    at_lo = z <= lo
+    at_hi = z >= hi
+    d[at_lo] = np.maximum(-g[at_lo], 0.0)
+    d[at_hi] = np.maximum(g[at_hi], 0.0)
+    return d
+
+
+def rel_kkt_box(A, b, z, loss, lo, hi, lam2=0.0):
+    """Relative KKT residual of  min f(x) s.t. lo <= x <= hi  at the feasible z:
+    ||dist(0, grad f(z) + N(z))|| / ||grad f(z)|| (the box counterpart of rel_kkt)."""
+    g = grad_f(A, b, z, loss, lam2)
+    d = box_violation(g, z, lo, hi)
+    return float(np.linalg.norm(d) / max(np.linalg.norm(g), 1e-30))
+
+
 def duality_gap(A, b, x, loss, lam1, lam2=0.0):
     """Returns dict(primal, dual, gap, rel_gap_min, rel_gap_max) for the point x (App. A)."""
     L = _L(loss)

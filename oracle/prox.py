@@ -19,3 +19,9 @@ def soft_threshold(v, kappa):
     out[hi] = v[hi] - kappa
     out[lo] = v[lo] + kappa
     return out
+
+
+def project_box(v, lo, hi):
+    """prox of the indicator of the box [lo, hi]^n: the Euclidean projection, i.e. the clip
+    (the z-step of the §4.5 bounded least squares, where g is that indicator)."""
+    return np.clip(np.asarray(v, dtype=np.float64), lo, hi)

@@ -174,6 +174,22 @@ def huber_outliers(n: int = 16000, m: int | None = None, density: float = 0.1, n
                    {"lam_of": "atb_inf", "outliers": np.sort(O)})
 
 
+def bls_lowrank(m: int = 20000, n: int | None = None, rank: int = 50, noise: float = 0.1,
+                seed: int | None = None, cfg: int = 7, k: int = 0, sketch_rank: int = 50) -> Problem:
+    """Bounded least squares of §4.5,  min 1/2 ||A x - b||^2  s.t.  0 <= x <= 1, with n = m / 2
+    features.  The paper's YearMSD-plus-random-features matrix is low rank and dense; this stand-in
+    is A = Z1 (m x r) Z2 (r x n) / sqrt(r) + 0.1 N(0, 1), and b = A x_true + 0.1 N(0, 1) with x_true
+    uniform on [-0.5, 1.5], so that about half of the solution's coordinates sit on a bound."""
+    rng = np.random.default_rng(seed_for(cfg, k) if seed is None else seed)
+    n = m // 2 if n is None else n
+    A = rng.standard_normal((m, rank)) @ rng.standard_normal((rank, n)) / np.sqrt(rank)
+    A += noise * rng.standard_normal((m, n))
+    x_true = rng.uniform(-0.5, 1.5, n)
+    b = A @ x_true + noise * rng.standard_normal(m)
+    return Problem(f"bls_{m}x{n}", A, b, SQUARED, 0.0, 0.0, 1.0, sketch_rank, x_true,
+                   {"box": (0.0, 1.0)})
+
+
 def lambda_path_fracs(K: int = 32, lo: float = 1e-3) -> np.ndarray:
     """K regularisation levels log-spaced from lambda_max down to lo * lambda_max."""
     return np.logspace(0.0, np.log10(lo), K)
@@ -197,4 +213,5 @@ CONFIGS = {
     4: "Batched: 32-level lambda path on a shared 5000x20000 AR(1) Lasso; 64 uneven Lasso problems",
     5: "Differentiation: 16 elastic-net logistic problems 8000x4000 (+2000 validation rows)",
     6: "Huber fitting (§4.4): 8000x16000, unit centred columns, 10% N(0,1) nonzeros, 5% +-10 outliers, lambda=0.1 ||A^T b||_inf",
+    7: "Bounded least squares (§4.5): 20000x10000 low rank (50) + 0.1 noise, 0 <= x <= 1",
 }

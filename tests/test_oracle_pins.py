@@ -61,6 +61,22 @@ def test_huber_special_values_and_conjugate_by_grid_search():
 
 
 # ----------------------------------------------------------------------------- prox
+def test_box_projection_is_the_prox_by_grid_search():
+    """prox of the indicator of [0, 1]: argmin_z 1/2 (z - v)^2 over the box, by a grid."""
+    grid = np.linspace(0.0, 1.0, 100001)
+    for v in (-0.7, 0.0, 0.31, 1.0, 2.5):
+        best = grid[np.argmin((grid - v) ** 2)]
+        assert prox.project_box(v, 0.0, 1.0) == pytest.approx(best, abs=1e-5)
+
+
+def test_box_violation_hand_values():
+    g = np.array([0.5, -0.5, 0.5, -0.5, 0.3])
+    z = np.array([0.0, 0.0, 1.0, 1.0, 0.4])
+    # at 0 a positive gradient is optimal, at 1 a negative one; inside only g = 0 is
+    np.testing.assert_array_equal(checks.box_violation(g, z, 0.0, 1.0), [0.0, 0.5, 0.5, 0.0, 0.3])
+
+
+
 def test_soft_threshold_piecewise_and_ties():
     v = np.array([3.0, 1.0, 0.5, -0.5, -1.0, -3.0, 0.0])
     out = prox.soft_threshold(v, 1.0)
@@ -269,6 +285,28 @@ def test_huber_solution_kkt_gap_and_fista():
     f = checks.fista(P.A, P.b, "huber", lam, tol=1e-15, max_iter=100000)
     F = checks.objective(P.A, P.b, r["z"], "huber", lam)
     assert checks.objective(P.A, P.b, f, "huber", lam) >= F - 1e-9 * abs(F)
+
+
+@pytest.mark.parametrize("shape", [(60, 30), (30, 60)])
+def test_bounded_least_squares_matches_scipy_bvls(shape):
+    """§4.5: the box-constrained ADMM (projection prox, box KKT stop) reaches the bounded least
+    squares solution of SciPy's BVLS (an active-set method, independent of ADMM); m < n takes the
+    Woodbury x-step."""
+    import scipy.optimize as so
+    m, n = shape
+    P = problems.bls_lowrank(m, n, rank=5, seed=23)
+    # the box KKT residual floors near 1e-11 in float64; m < n (several minimisers) converges slowly
+    tol = 1e-10 if m >= n else 1e-9
+    r = admm.solve(P.A, P.b, "squared", 0.0, rho=1.0, tol=tol, box=(0.0, 1.0), max_iter=50000)
+    assert r["converged"] and r["gap"] is None
+    ref = so.lsq_linear(P.A, P.b, bounds=(0.0, 1.0), method="bvls", tol=1e-15)
+    assert checks.rel_kkt_box(P.A, P.b, ref.x, "squared", 0.0, 1.0) <= 1e-10
+    on_bound = np.mean((ref.x <= 0.0) | (ref.x >= 1.0))
+    assert 0.1 < on_bound < 0.9                      # both pieces of the prox are exercised
+    obj = lambda x: 0.5 * np.sum((P.A @ x - P.b) ** 2)  # noqa: E731
+    assert obj(r["z"]) <= obj(ref.x) * (1 + 1e-10) + 1e-12
+    if m >= n:                                       # unique minimiser when A has full column rank
+        np.testing.assert_allclose(r["z"], ref.x, atol=1e-8)
 
 
 @pytest.mark.parametrize("loss", ["squared", "logistic", "huber"])
@@ -497,6 +535,8 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     B = Y @ np.linalg.inv(C).T
     Ub, sb, _ = np.linalg.svd(B, full_matrices=False)
     assert not np.allclose((Ub * sb ** 2) @ Ub.T, H, atol=1e-8 * ev[0])
+    # 6) a projection with the bounds swapped fails the grid-search pin of the box prox
+    assert not np.isclose(np.clip(0.31, 1.0, 0.0), 0.31)
     # 5) the Huber derivative without its factor 2 fails the finite-difference pin
     w = np.linspace(-3, 3, 61) + 0.013
     h = 1e-6
