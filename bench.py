@@ -401,8 +401,9 @@ def extra_configs(G, torch, args) -> dict:
     """The other workloads of the measurement plan, one timed pass each (rank 0, --extra):
     the 1000 x 10000 AR(1) Lasso (FP32, BF16), the 32-level lambda path on a shared 5000 x 20000
     Lasso and the 64 uneven Lasso problems (solved in one batched call each), the
-    elastic-net logistic implicit gradient (solve + adjoint) on 8000 x 4000 problems, and the
-    §4.4 Huber fit at 8000 x 16000 (FP32, BF16)."""
+    elastic-net logistic implicit gradient (solve + adjoint) on 8000 x 4000 problems, the
+    §4.5 bounded least squares at 16000 x 8000 (FP64) and the §4.4 Huber fit at 8000 x 16000 (FP32,
+    BF16)."""
     from oracle import losses
     res = {}
     sync = torch.cuda.synchronize
@@ -477,6 +478,21 @@ def extra_configs(G, torch, args) -> dict:
     res["implicit_grad_8000x4000_fp32"] = {"problems": args.cfg5_problems, "solve_s_mean": float(np.mean(ts)),
                                            "grad_s_mean": float(np.mean(tg)),
                                            "note": "grad = adjoint PCG on the support + outputs (dL/dlambda, dL/db)"}
+    # cfg 7: bounded least squares (§4.5) in FP64 (a float32 gradient of this well-fit problem
+    # floors the box KKT residual near 1e-3), 16000 x 8000 (1 GB; FP64 covers n <= 8192)
+    P = problems.bls_lowrank(16000)
+    A = torch.from_numpy(P.A).cuda()
+    b = torch.from_numpy(P.b).cuda()
+    with G.Solver(precision=G.FP64, stop_rule=G.STOP_KKT, eps_kkt=1e-4, sketch_rank=P.sketch_rank, rho=P.rho,
+                  max_iter=20000, box=1, box_lo=0.0, box_hi=1.0) as s:
+        s.set_data(A, b, "squared")
+        s.solve(0.0)
+        el, (z, info) = tsolve(s, lambda: s.solve(0.0))
+    res["bls_16000x8000_fp64"] = {
+        "time_s": el, "iters": info["iters"], "cg_iters": info["cg_iters_total"], "status": info["status_name"],
+        "rel_kkt": info["rel_kkt"], "on_bounds": float(np.mean((z <= 0.0) | (z >= 1.0))),
+        "hv_gbs": (info["hv_bytes"] / (info["hv_ms"] / info["hv_launches"] * 1e-3) / 1e9) if info["hv_launches"] else None}
+    del A, b
     # cfg 6: Huber fitting (§4.4) at the paper's largest size, 8000 x 16000 (512 MB in FP32)
     P = problems.huber_outliers(16000)
     A = torch.from_numpy(P.A.astype(np.float32)).cuda()

@@ -133,6 +133,12 @@ typedef struct genios_options {
                                 shape allows (n <= 1024 x SMs, s <= 128, not the split-BF16
                                 stream); 0: one Hv launch plus vector kernels per CG iteration
                                 (CUDA graph when use_graphs = 1) */
+    int32_t box;             /* 0 (default): g = lambda_1 ||.||_1.  1: g is the indicator of the box
+                                [box_lo, box_hi]^n (the bounded least squares of §4.5 with the
+                                squared loss): the z-step is the projection, STOP_KKT tests
+                                ||dist(0, grad f(z) + N(z))|| / ||grad f(z)|| (N the normal cone),
+                                lambda_1 must be 0, STOP_GAP and genios_grad are refused */
+    double box_lo, box_hi;   /* the bounds (default 0 and 1) */
 } genios_options;
 
 typedef struct genios_info {

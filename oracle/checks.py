@@ -81,6 +81,13 @@ def box_violation(g, z, lo, hi):
     return d
 
 
+def bls_exact(A, b, lo, hi):
+    """The bounded least squares minimiser of 1/2 ||A x - b||^2 over [lo, hi]^n by SciPy's BVLS
+    (an active-set method; the definition computed by a library routine, independent of ADMM)."""
+    import scipy.optimize as so
+    return so.lsq_linear(A, b, bounds=(lo, hi), method="bvls", tol=1e-15).x
+
+
 def rel_kkt_box(A, b, z, loss, lo, hi, lam2=0.0):
     """Relative KKT residual of  min f(x) s.t. lo <= x <= hi  at the feasible z:
     ||dist(0, grad f(z) + N(z))|| / ||grad f(z)|| (the box counterpart of rel_kkt)."""

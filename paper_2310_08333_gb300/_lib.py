@@ -39,7 +39,8 @@ class Options(C.Structure):
         ("precision", C.c_int32), ("kkt_check_every", C.c_int32), ("use_graphs", C.c_int32),
         ("seed", C.c_uint64), ("device_wait_limit_us", C.c_int64),
         ("verbose", C.c_int32), ("profile", C.c_int32), ("tensor_sketch", C.c_int32),
-        ("batch_lockstep", C.c_int32), ("persistent_cg", C.c_int32),
+        ("batch_lockstep", C.c_int32), ("persistent_cg", C.c_int32), ("box", C.c_int32),
+        ("box_lo", C.c_double), ("box_hi", C.c_double),
     ]
 
 

@@ -417,7 +417,8 @@ GENIOS_DEV bool cg_step(const CgLoopArgs& a, CglShared<VT>& sh) {
 }
 
 // The z/u update of §2.5 / Eq. (5) after the x-step, on the CTA's slice: x += delta,
-// x_hat = alpha x + (1 - alpha) z, z = S_{lambda_1 / rho}(x_hat + u), u += x_hat - z; and the norms
+// x_hat = alpha x + (1 - alpha) z, z = S_{lambda_1 / rho}(x_hat + u) (with a box: the projection of
+// x_hat + u onto it), u += x_hat - z; and the norms
 // ||x - z||^2, ||x||^2, ||z||^2, ||u||^2, ||z||_1, nnz(z) into DevState.  The CTA partials (float64)
 // are summed in a fixed order by the last CTA to finish, so no grid barrier is needed.
 template <typename VT>
@@ -434,6 +435,8 @@ GENIOS_DEV void zu_phase(const CgLoopArgs& a, CglShared<VT>& sh) {
     const VT* delta = static_cast<const VT*>(a.delta);
     const double kappa = a.zu_lam1 / a.zu_rho;
     const double alpha = a.zu_alpha;
+    const int box = a.zu_box;
+    const VT lo = (VT)a.zu_lo, hi = (VT)a.zu_hi;
     double v[6] = {0, 0, 0, 0, 0, 0};
     for (int jj = tid; jj < ns; jj += RP_CTHREADS) {
         const int64_t j = j0 + jj;
@@ -443,7 +446,8 @@ GENIOS_DEV void zu_phase(const CgLoopArgs& a, CglShared<VT>& sh) {
         const VT xh = (VT)alpha * xj + (VT)(1.0 - alpha) * zj;
         const VT vv = xh + u[j];
         VT zn;
-        if (vv > (VT)kappa) zn = vv - (VT)kappa;
+        if (box) zn = vv < lo ? lo : vv > hi ? hi : vv;   // projection onto the box
+        else if (vv > (VT)kappa) zn = vv - (VT)kappa;
         else if (vv < -(VT)kappa) zn = vv + (VT)kappa;
         else zn = VT(0);
         const VT un = u[j] + xh - zn;

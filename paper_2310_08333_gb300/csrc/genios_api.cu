@@ -181,6 +181,9 @@ extern "C" void genios_default_options(genios_options* o) {
     o->tensor_sketch = 1;
     o->batch_lockstep = 0;
     o->persistent_cg = 1;
+    o->box = 0;
+    o->box_lo = 0.0;
+    o->box_hi = 1.0;
 }
 
 extern "C" genios_status genios_create(const genios_options* opts, int device, void* stream,
@@ -562,6 +565,9 @@ static cudaError_t cg_persistent(genios_ctx* ctx, const void* d, const void* g, 
     a.zu_rho = zu_rho;
     a.zu_lam1 = zu_lam1;
     a.zu_alpha = zu_alpha;
+    a.zu_box = ctx->opt.box ? 1 : 0;
+    a.zu_lo = ctx->opt.box_lo;
+    a.zu_hi = ctx->opt.box_hi;
     a.zu_part = reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->sc.part) +
                                           cgloop_zu_offset_bytes(ctx->cgl.rp.grid));
     a.S = ctx->S;
@@ -758,6 +764,11 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
     if (!ctx->has_data) FAIL(GENIOS_ESTATE, "solve before set_data");
     if (!lambda1 || !lambda2 || !x_out) FAIL(GENIOS_EINVAL, "NULL argument");
     if (!(lambda1[0] >= 0) || !(lambda2[0] >= 0)) FAIL(GENIOS_EINVAL, "lambda must be >= 0");
+    if (ctx->opt.box) {
+        if (lambda1[0] != 0.0) FAIL(GENIOS_EINVAL, "box constraint: lambda_1 must be 0 (the box replaces the l1 term)");
+        if (ctx->opt.stop_rule & GENIOS_STOP_GAP) FAIL(GENIOS_EINVAL, "box constraint: the duality-gap stop rule is for the l1 problem");
+        if (!(ctx->opt.box_lo <= ctx->opt.box_hi)) FAIL(GENIOS_EINVAL, "box constraint: box_lo > box_hi");
+    }
     if (out_dtype != GENIOS_DT_F64 && out_dtype != GENIOS_DT_F32) FAIL(GENIOS_EINVAL, "bad out_dtype");
     CK(cudaSetDevice(ctx->device));
     const double t_start = now_ms();
@@ -868,7 +879,7 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
             if (!stop && (o.stop_rule & GENIOS_STOP_KKT) && kkt.due(k, resid_ok)) {
                 CK(grad_pass(ctx, ctx->z, nullptr, nullptr));
                 CK(kkt_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, n, ctx->z, lam2, lam1,
-                              ctx->S, ctx->sc, s));
+                              ctx->S, ctx->sc, s, o.box, o.box_lo, o.box_hi));
                 ctx->launches += 2;
                 inf.grad_launches++;
                 st = read_state(ctx);
@@ -950,7 +961,7 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
         // ---- z/u update (§2.5, §3.1, Eq. (5)); x <- x + delta (inside the persistent CG launch)
         if (!ctx->cgl.ok) {
             CK(zu_update(ctx->dbl, n, ctx->x, ctx->delta, ctx->z, ctx->u, rho, lam1, o.alpha, ctx->S, nullptr,
-                         ctx->sc, s));
+                         ctx->sc, s, o.box, o.box_lo, o.box_hi));
             ctx->launches++;
         }
     }
@@ -1173,7 +1184,7 @@ extern "C" genios_status genios_solve(genios_ctx* ctx, const double* lambda1, co
     if (!ctx->has_data) FAIL(GENIOS_ESTATE, "solve before set_data");
     if (!lambda1 || !lambda2 || !x_out) FAIL(GENIOS_EINVAL, "NULL argument");
     if (out_dtype != GENIOS_DT_F64 && out_dtype != GENIOS_DT_F32) FAIL(GENIOS_EINVAL, "bad out_dtype");
-    if (ctx->shared && ctx->opt.batch_lockstep && ctx->loss == GENIOS_LOSS_SQUARED && ctx->prec == GENIOS_FP32 &&
+    if (ctx->shared && ctx->opt.batch_lockstep && !ctx->opt.box && ctx->loss == GENIOS_LOSS_SQUARED && ctx->prec == GENIOS_FP32 &&
         ctx->sk > 0 && ctx->K <= 128)
         return solve_lockstep(ctx, lambda1, lambda2, x_out, out_dtype, info);
     const size_t es = out_dtype == GENIOS_DT_F64 ? 8 : 4;
@@ -1232,6 +1243,7 @@ extern "C" genios_status genios_grad(genios_ctx* ctx, const void* dL_dx, double*
     if (ctx->K != 1 || !ctx->subs.empty())
         FAIL(GENIOS_EUNSUPPORTED, "implicit gradient of a batch: use one K = 1 context per problem");
     if (!ctx->solved) FAIL(GENIOS_ESTATE, "grad before a solve");
+    if (ctx->opt.box) FAIL(GENIOS_EUNSUPPORTED, "implicit gradient with a box constraint");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = ctx->stream;
     const int64_t m = ctx->m, n = ctx->n;

@@ -136,6 +136,8 @@ struct CgLoopArgs {
     void* zu_x;                // x (x += delta) and z, value type
     void* zu_z;
     double zu_rho, zu_lam1, zu_alpha;
+    int zu_box;                // 1: z = the projection onto [zu_lo, zu_hi]^n instead of the soft threshold
+    double zu_lo, zu_hi;
     double* zu_part;           // grid x 6 float64 partials of the z/u norms
     DevState* S;               // cg_fault must be 0 at launch; results: cg_it, rr, rz, ...
     int timed;                 // accumulate H-phase and launch device times in S
@@ -198,16 +200,19 @@ cudaError_t rhs_init(bool dbl, int64_t n, const void* g, const void* x, const vo
 cudaError_t grad_finish(bool dbl, const void* P, int G, int64_t ldp, const double* loss_part,
                         int64_t n, const void* x, const void* u, double mu, double rho,
                         double lam1, void* g, DevState* S, Scratch sc, cudaStream_t s);
-// KKT finish at z: gz = sum_b P[b] + mu z; subgradient distance norms
+// KKT finish at z: gz = sum_b P[b] + mu z; subgradient distance norms (box = 1: the distance of
+// 0 from gz + N(z), N the normal cone of [lo, hi]^n)
 cudaError_t kkt_finish(bool dbl, const void* P, int G, int64_t ldp, int64_t n, const void* z,
-                       double mu, double lam1, DevState* S, Scratch sc, cudaStream_t s);
+                       double mu, double lam1, DevState* S, Scratch sc, cudaStream_t s, int box = 0,
+                       double lo = 0.0, double hi = 0.0);
 // duality gap pieces from W = loss'(Ax - b) (m-vector)
 cudaError_t gap_pieces(bool dbl, int loss, int64_t m, const void* W, const void* b, double mu,
                        double lam1, DevState* S, Scratch sc, cudaStream_t s);
-// z/u update (x += delta first when delta != null)
+// z/u update (x += delta first when delta != null); box = 1: z = the projection onto [lo, hi]^n
+// instead of the soft threshold
 cudaError_t zu_update(bool dbl, int64_t n, void* x, const void* delta, void* z, void* u,
                       double rho, double lam1, double alpha, DevState* S, double* norms_out,
-                      Scratch sc, cudaStream_t s);
+                      Scratch sc, cudaStream_t s, int box = 0, double lo = 0.0, double hi = 0.0);
 // conversions
 cudaError_t convert_copy(int src_dt, int dst_dt, int64_t rows, int64_t cols, const void* src,
                          int64_t lds, void* dst, int64_t ldd, cudaStream_t s);

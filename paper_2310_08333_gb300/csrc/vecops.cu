@@ -239,7 +239,8 @@ __global__ void grad_finish_kernel(const VT* P, int G, int64_t ldp, const double
 
 template <typename VT>
 __global__ void kkt_finish_kernel(const VT* P, int G, int64_t ldp, int64_t n, const VT* z,
-                                  double mu, double lam1, DevState* S, Scratch sc) {
+                                  double mu, double lam1, DevState* S, Scratch sc, int box, double lo,
+                                  double hi) {
     __shared__ double sh[8 * 33];
     const int64_t j = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
     double sum = column_sum<VT, double>(P, G, ldp, j, n, sh);
@@ -249,7 +250,11 @@ __global__ void kkt_finish_kernel(const VT* P, int G, int64_t ldp, int64_t n, co
         const double zj = (double)z[j];
         const double gj = sum + mu * zj;
         double d;
-        if (zj > 0.0) d = fabs(gj + lam1);
+        if (box) {   // distance of 0 from g + N(z), N the normal cone of the box at z
+            if (zj <= lo) d = fmax(-gj, 0.0);
+            else if (zj >= hi) d = fmax(gj, 0.0);
+            else d = fabs(gj);
+        } else if (zj > 0.0) d = fabs(gj + lam1);
         else if (zj < 0.0) d = fabs(gj - lam1);
         else d = fmax(fabs(gj) - lam1, 0.0);
         v[0] = d * d;
@@ -289,7 +294,8 @@ __global__ void gap_kernel(int loss, int64_t m, const VT* W, const VT* b, double
 
 template <typename VT>
 __global__ void zu_kernel(int64_t n, VT* x, const VT* delta, VT* z, VT* u, double rho, double lam1,
-                          double alpha, DevState* S, double* norms_out, Scratch sc) {
+                          double alpha, DevState* S, double* norms_out, Scratch sc, int box, double lo,
+                          double hi) {
     const double kappa = lam1 / rho;
     double v[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
@@ -303,7 +309,8 @@ __global__ void zu_kernel(int64_t n, VT* x, const VT* delta, VT* z, VT* u, doubl
         const VT xh = (VT)alpha * xj + (VT)(1.0 - alpha) * zj;
         const VT vv = xh + u[j];
         VT zn;
-        if (vv > (VT)kappa) zn = vv - (VT)kappa;
+        if (box) zn = vv < (VT)lo ? (VT)lo : vv > (VT)hi ? (VT)hi : vv;   // projection onto the box
+        else if (vv > (VT)kappa) zn = vv - (VT)kappa;
         else if (vv < -(VT)kappa) zn = vv + (VT)kappa;
         else zn = VT(0);
         const VT un = u[j] + xh - zn;
@@ -446,10 +453,11 @@ cudaError_t grad_finish(bool dbl, const void* P, int G, int64_t ldp, const doubl
 }
 
 cudaError_t kkt_finish(bool dbl, const void* P, int G, int64_t ldp, int64_t n, const void* z,
-                       double mu, double lam1, DevState* S, Scratch sc, cudaStream_t s) {
+                       double mu, double lam1, DevState* S, Scratch sc, cudaStream_t s, int box, double lo,
+                       double hi) {
     const int grid = nblocks(n, 32);
-    if (dbl) kkt_finish_kernel<double><<<grid, VT_THREADS, 0, s>>>(CC<double>(P), G, ldp, n, CC<double>(z), mu, lam1, S, sc);
-    else kkt_finish_kernel<float><<<grid, VT_THREADS, 0, s>>>(CC<float>(P), G, ldp, n, CC<float>(z), mu, lam1, S, sc);
+    if (dbl) kkt_finish_kernel<double><<<grid, VT_THREADS, 0, s>>>(CC<double>(P), G, ldp, n, CC<double>(z), mu, lam1, S, sc, box, lo, hi);
+    else kkt_finish_kernel<float><<<grid, VT_THREADS, 0, s>>>(CC<float>(P), G, ldp, n, CC<float>(z), mu, lam1, S, sc, box, lo, hi);
     return cudaGetLastError();
 }
 
@@ -463,10 +471,10 @@ cudaError_t gap_pieces(bool dbl, int loss, int64_t m, const void* W, const void*
 
 cudaError_t zu_update(bool dbl, int64_t n, void* x, const void* delta, void* z, void* u,
                       double rho, double lam1, double alpha, DevState* S, double* norms_out,
-                      Scratch sc, cudaStream_t s) {
+                      Scratch sc, cudaStream_t s, int box, double lo, double hi) {
     const int grid = grid_for(n, VT_THREADS, 512);
-    if (dbl) zu_kernel<double><<<grid, VT_THREADS, 0, s>>>(n, C<double>(x), CC<double>(delta), C<double>(z), C<double>(u), rho, lam1, alpha, S, norms_out, sc);
-    else zu_kernel<float><<<grid, VT_THREADS, 0, s>>>(n, C<float>(x), CC<float>(delta), C<float>(z), C<float>(u), rho, lam1, alpha, S, norms_out, sc);
+    if (dbl) zu_kernel<double><<<grid, VT_THREADS, 0, s>>>(n, C<double>(x), CC<double>(delta), C<double>(z), C<double>(u), rho, lam1, alpha, S, norms_out, sc, box, lo, hi);
+    else zu_kernel<float><<<grid, VT_THREADS, 0, s>>>(n, C<float>(x), CC<float>(delta), C<float>(z), C<float>(u), rho, lam1, alpha, S, norms_out, sc, box, lo, hi);
     return cudaGetLastError();
 }
 

@@ -175,18 +175,22 @@ def huber_outliers(n: int = 16000, m: int | None = None, density: float = 0.1, n
 
 
 def bls_lowrank(m: int = 20000, n: int | None = None, rank: int = 50, noise: float = 0.1,
-                seed: int | None = None, cfg: int = 7, k: int = 0, sketch_rank: int = 50) -> Problem:
+                seed: int | None = None, cfg: int = 7, k: int = 0, sketch_rank: int = 100) -> Problem:
     """Bounded least squares of §4.5,  min 1/2 ||A x - b||^2  s.t.  0 <= x <= 1, with n = m / 2
     features.  The paper's YearMSD-plus-random-features matrix is low rank and dense; this stand-in
     is A = Z1 (m x r) Z2 (r x n) / sqrt(r) + 0.1 N(0, 1), and b = A x_true + 0.1 N(0, 1) with x_true
-    uniform on [-0.5, 1.5], so that about half of the solution's coordinates sit on a bound."""
+    uniform on [-0.5, 1.5], so that about half of the solution's coordinates sit on a bound.
+    Penalty rho = noise^2 m, the scale of the noise bulk of A^T A's spectrum (ADMM on this problem
+    converges in tens of iterations there and in hundreds at rho = 1).  Sketch rank 100 > rank:
+    with s = rank the Nystrom eigenvalue lam_s stays at the top of the spectrum and Eq. (10)
+    leaves a condition number of about lam_s / (nu + bulk)."""
     rng = np.random.default_rng(seed_for(cfg, k) if seed is None else seed)
     n = m // 2 if n is None else n
     A = rng.standard_normal((m, rank)) @ rng.standard_normal((rank, n)) / np.sqrt(rank)
     A += noise * rng.standard_normal((m, n))
     x_true = rng.uniform(-0.5, 1.5, n)
     b = A @ x_true + noise * rng.standard_normal(m)
-    return Problem(f"bls_{m}x{n}", A, b, SQUARED, 0.0, 0.0, 1.0, sketch_rank, x_true,
+    return Problem(f"bls_{m}x{n}", A, b, SQUARED, 0.0, 0.0, noise * noise * m, sketch_rank, x_true,
                    {"box": (0.0, 1.0)})
 
 

@@ -167,6 +167,52 @@ def test_huber_parity(G, prec):
         assert abs(F - Fs) <= 1e-5 * abs(Fs)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_bounded_least_squares_parity(G, prec):
+    """§4.5 bounded least squares (600 x 300, 0 <= x <= 1, about half the coordinates on a
+    bound): the z iterate is feasible exactly; FP64 matches the BVLS solution.  In FP32 the
+    residual A x - b of this well-fit problem is ~175x smaller than A x, so a float32 gradient
+    carries ~1e-4 relative error and the box KKT residual floors near 1e-3 (the FP64 oracle and
+    the FP64 GPU path reach 1e-8 in 34 iterations): FP32 is run to 3e-3 and checked there."""
+    P = problems.bls_lowrank(600, 300, rank=10, seed=problems.seed_for(7, 1), sketch_rank=30)
+    A, b = rounded(P, prec)
+    ref = checks.bls_exact(A, b, 0.0, 1.0)        # BVLS; the oracle's ADMM is pinned to it
+    z, info, _ = gpu_solve(G, P, prec, 0.0, box=1, box_lo=0.0, box_hi=1.0,
+                           eps_kkt=1e-8 if prec == 0 else 3e-3, rho_update_every=25 if prec == 0 else 0)
+    assert info["status"] == 0, info
+    assert np.all(z >= 0.0) and np.all(z <= 1.0)
+    on = np.mean((ref <= 0.0) | (ref >= 1.0))
+    assert 0.1 < on < 0.9
+    kkt = checks.rel_kkt_box(A, b, z, "squared", 0.0, 1.0)
+    obj = lambda x: 0.5 * np.sum((A @ x - b) ** 2)  # noqa: E731
+    if prec == 0:
+        # lambda_min(A^T A) = 0.52 here: the error the 1e-8 KKT residual allows is ~1e-7
+        np.testing.assert_allclose(z, ref, atol=1e-6)
+        assert kkt <= 2e-8
+    else:
+        print(f"FP32 BLS: box KKT {kkt:.2e} (GPU {info['rel_kkt']:.2e})")
+        assert kkt <= 5e-3, (kkt, info["rel_kkt"], info["iters"])
+        assert abs(obj(z) - obj(ref)) <= 1e-4 * obj(ref), (obj(z), obj(ref), kkt)
+
+
+def test_box_constraint_refusals(G):
+    P = problems.bls_lowrank(200, 100, rank=5, seed=7)
+    A = torch.from_numpy(P.A).cuda()
+    b = torch.from_numpy(P.b).cuda()
+    with G.Solver(precision=0, box=1, sketch_rank=10) as s:
+        s.set_data(A, b, "squared")
+        with pytest.raises(G.GeniosError):
+            s.solve(0.1)                     # the box replaces the l1 term
+        z, info = s.solve(0.0)
+        assert info["status"] == 0
+        with pytest.raises(G.GeniosError):
+            s.grad(np.ones(100))
+    with G.Solver(precision=0, box=1, stop_rule=G.STOP_GAP, sketch_rank=10) as s:
+        s.set_data(A, b, "squared")
+        with pytest.raises(G.GeniosError):
+            s.solve(0.0)
+
+
 @pytest.mark.parametrize("loss", ["squared", "logistic", "huber"])
 def test_lambda_above_lambda_max_gives_exact_zero(G, loss):
     P = (problems.lasso_iid(300, 800, nnz=10, seed=9) if loss == "squared"
