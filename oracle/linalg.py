@@ -151,3 +151,40 @@ def nystrom_precond_apply(U, lam, nu, v):
 def gaussian_test_matrix(n, s, seed):
     """Standard normal test matrix Omega (n x s) (§2.2 uses a standard normal Omega)."""
     return np.random.default_rng(seed).standard_normal((n, s))
+
+
+def nystrom_error_norm(apply_H, U, lam, iters=30, v0=None):
+    """||E||_2 for E = H_data - U diag(lam) U^T, which is PSD for a Nystrom approximation of the
+    PSD H_data (§2.2, adaptive sketch size): the randomized power method, each step one product
+    with H_data; returns the Rayleigh quotient v^T E v of the last iterate (a lower estimate that
+    approaches ||E|| as the iterations grow).  v0: the unit start vector (default: a seeded
+    standard normal)."""
+    n = U.shape[0]
+    v = np.random.default_rng(0).standard_normal(n) if v0 is None else np.asarray(v0, dtype=np.float64)
+    v = v / np.linalg.norm(v)
+    est = 0.0
+    for _ in range(iters):
+        w = apply_H(v) - U @ (lam * (U.T @ v))
+        est = float(v @ w)
+        nw = np.linalg.norm(w)
+        if nw == 0.0:
+            return 0.0
+        v = w / nw
+    return max(est, 0.0)
+
+
+def adaptive_nystrom(apply_H_block, apply_H, n, s0, s_max, nu, theta=10.0, seed=0, power_iters=30):
+    """The adaptive sketch size of §2.2: starting from s0, double s (up to s_max) until the bound
+    kappa(L^{-1/2} (H + nu I) L^{-1/2}) <= 1 + (lam_s + ||E||) / nu on the preconditioned
+    condition number (the bound the paper cites) is at most 1 + theta.  apply_H_block(Omega)
+    returns H_data Omega; apply_H(v) returns H_data v.  Returns (U, lam, s, err, bound) with
+    bound = (lam_s + err) / nu."""
+    s = s0
+    while True:
+        Om = orthonormal_test_matrix(gaussian_test_matrix(n, s, seed))
+        U, lam, _ = nystrom_from_sketch(apply_H_block(Om), Om)
+        err = nystrom_error_norm(apply_H, U, lam, power_iters)
+        bound = (lam[-1] + err) / nu
+        if bound <= theta or s >= s_max:
+            return U, lam, s, err, bound
+        s = min(2 * s, s_max)

@@ -87,6 +87,26 @@ def test_config1_lasso_parity(G, prec):
     assert_parity(P, z, ref["z"], lam, 0.0, "squared")
 
 
+@pytest.mark.parametrize("persistent", [1, 0])
+@pytest.mark.parametrize("graphs", [1, 0])
+def test_cg_paths_agree_with_oracle(G, persistent, graphs):
+    """Both CG paths, on a logistic problem (re-sketches, D changing every iteration): the
+    persistent cooperative kernel (persistent_cg = 1) and the per-iteration kernels
+    (persistent_cg = 0: CUDA graph with a device-side loop when use_graphs = 1, host-driven
+    otherwise) reach the oracle's solution."""
+    if persistent and not graphs:
+        pytest.skip("use_graphs only selects between the per-iteration launch modes")
+    P = problems.logistic_lowrank(1000, 400, nnz=20, sketch_rank=40, seed=problems.seed_for(3, 7))
+    A, b = rounded(P, 0)
+    lam = P.lam_frac * checks.lambda_max(A, b, "logistic")
+    ref = oadmm.solve(A, b, "logistic", lam, rho=30.0, tol=1e-13, check_every=5)
+    assert ref["converged"]
+    z, info, _ = gpu_solve(G, P, 0, lam, rho=30.0, persistent_cg=persistent, use_graphs=graphs)
+    assert info["status"] == 0, info
+    assert (info["cg_launches"] > 0) == bool(persistent)
+    assert_parity(P, z, ref["z"], lam, 0.0, "logistic")
+
+
 def test_config2_lasso_fp32_parity(G):
     P = problems.lasso_ar1()
     A, b = rounded(P, 1)

@@ -221,6 +221,43 @@ def test_preconditioned_operator_has_two_eigenvalues_and_pcg_stops_in_two():
         np.testing.assert_allclose(x, np.linalg.solve(H + nu * np.eye(n), rhs), rtol=1e-8)
 
 
+def test_nystrom_error_power_method_and_condition_bound():
+    """E = H - U Lam U^T is PSD; the power estimate of ||E|| approaches the exact value from below;
+    and the preconditioned condition number obeys kappa <= 1 + (lam_s + ||E||) / nu (the bound of
+    §2.2), checked with dense eigenvalues of L^{-1} (H + nu I)."""
+    n, s, nu = 120, 12, 0.5
+    rng = np.random.default_rng(40)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.concatenate([np.logspace(3, 1, 20), np.linspace(1.0, 0.01, n - 20)])
+    H = (Q * ev) @ Q.T
+    Om = linalg.orthonormal_test_matrix(linalg.gaussian_test_matrix(n, s, 41))
+    U, lam, _ = linalg.nystrom_from_sketch(H @ Om, Om)
+    E = H - (U * lam) @ U.T
+    eE = np.linalg.eigvalsh(0.5 * (E + E.T))
+    assert eE[0] >= -1e-9 * ev[0]
+    est = linalg.nystrom_error_norm(lambda v: H @ v, U, lam, iters=200)
+    assert est <= eE[-1] * (1 + 1e-9) and est >= 0.95 * eE[-1]
+    Linv = np.column_stack([linalg.nystrom_precond_apply(U, lam, nu, e) for e in np.eye(n)])
+    mu = np.sort(np.linalg.eigvals(Linv @ (H + nu * np.eye(n))).real)
+    assert mu[-1] / mu[0] <= 1 + (lam[-1] + eE[-1]) / nu + 1e-8
+
+
+def test_adaptive_sketch_grows_until_the_bound_holds():
+    """A PSD matrix with 40 dominant directions: from s = 8 the sketch doubles until
+    (lam_s + ||E||) / nu <= theta; a cap below that stops at the cap with the bound unmet."""
+    n, nu, theta = 200, 1.0, 10.0
+    rng = np.random.default_rng(42)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.concatenate([np.logspace(4, 2, 40), 0.5 * rng.uniform(size=n - 40)])
+    H = (Q * ev) @ Q.T
+    U, lam, s, err, bound = linalg.adaptive_nystrom(lambda O: H @ O, lambda v: H @ v, n, 8, 128, nu, theta)
+    assert s in (64, 128) and bound <= theta
+    exact = np.linalg.eigvalsh(H - (U * lam) @ U.T)[-1]
+    assert err <= exact * (1 + 1e-9) + 1e-12
+    _, _, s2, _, b2 = linalg.adaptive_nystrom(lambda O: H @ O, lambda v: H @ v, n, 8, 16, nu, theta)
+    assert s2 == 16 and b2 > theta
+
+
 def test_sketch_is_data_hessian_times_omega():
     A, b = _small_logistic()
     D = linalg.gradient_pass(A, b, np.zeros(A.shape[1]), "logistic")["D"]
