@@ -139,6 +139,14 @@ typedef struct genios_options {
                                 ||dist(0, grad f(z) + N(z))|| / ||grad f(z)|| (N the normal cone),
                                 lambda_1 must be 0, STOP_GAP and genios_grad are refused */
     double box_lo, box_hi;   /* the bounds (default 0 and 1) */
+    int32_t sketch_adaptive; /* 0 (default): the constant sketch rank.  1: the adaptive size of
+                                §2.2 at the first sketch of a data set: from sketch_rank, double s
+                                (up to sketch_rank_max) until (lam_s + ||E||) / nu <= sketch_theta,
+                                with ||E|| = ||H - U Lam U^T|| from 20 randomized power steps (one
+                                pass over A each) and nu = rho + lambda_2 + sigma at k = 1; the
+                                rank found is kept for the re-sketches and later solves */
+    int32_t sketch_rank_max; /* cap of the adaptive rank (default 128, at most 128) */
+    double sketch_theta;     /* target of the bound kappa <= 1 + theta (default 10) */
 } genios_options;
 
 typedef struct genios_info {
@@ -164,6 +172,9 @@ typedef struct genios_info {
     int64_t grad_launches;   /* gradient rowpass launches */
     double grad_ms;          /* their total device time (profile = 1), else 0 */
     double hv_bytes;         /* algorithmic bytes of one Hv launch (A once + vectors) */
+    int32_t sketch_rank_used;/* the sketch rank s in use (after the adaptive choice) */
+    int32_t pad0;
+    double sketch_bound;     /* (lam_s + ||E||) / nu of the adaptive choice, NaN when not adaptive */
     int64_t cg_launches;     /* persistent CG launches (persistent_cg = 1), else 0 */
     double cg_ms;            /* their total time: CUDA events around each launch on its stream
                                 (profile = 1), else the device's globaltimer (CTA 0, start to end) */

@@ -40,7 +40,8 @@ class Options(C.Structure):
         ("seed", C.c_uint64), ("device_wait_limit_us", C.c_int64),
         ("verbose", C.c_int32), ("profile", C.c_int32), ("tensor_sketch", C.c_int32),
         ("batch_lockstep", C.c_int32), ("persistent_cg", C.c_int32), ("box", C.c_int32),
-        ("box_lo", C.c_double), ("box_hi", C.c_double),
+        ("box_lo", C.c_double), ("box_hi", C.c_double), ("sketch_adaptive", C.c_int32),
+        ("sketch_rank_max", C.c_int32), ("sketch_theta", C.c_double),
     ]
 
 
@@ -53,7 +54,8 @@ class Info(C.Structure):
         ("objective", C.c_double), ("t_setup_ms", C.c_double), ("t_sketch_ms", C.c_double),
         ("t_solve_ms", C.c_double), ("kernel_launches", C.c_int64), ("hv_launches", C.c_int64),
         ("hv_ms", C.c_double), ("grad_launches", C.c_int64), ("grad_ms", C.c_double),
-        ("hv_bytes", C.c_double), ("cg_launches", C.c_int64), ("cg_ms", C.c_double),
+        ("hv_bytes", C.c_double), ("sketch_rank_used", C.c_int32), ("pad0", C.c_int32),
+        ("sketch_bound", C.c_double), ("cg_launches", C.c_int64), ("cg_ms", C.c_double),
         ("cg_phase_ms", C.c_double * 6),
     ]
 

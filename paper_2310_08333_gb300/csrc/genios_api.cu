@@ -109,6 +109,9 @@ struct genios_ctx {
     bool have_precond = false;
     bool omega_ready = false;   // Om drawn and its orthonormal basis in nw.Oq
     bool eig_warm = false;      // nw holds the eigenvectors of the last successful core
+    int sk_alloc = 0;           // sketch buffers are sized for this rank (>= sk; adaptive: the cap)
+    bool sketch_adapted = false;// the adaptive rank has been chosen for this data set
+    double sketch_bound = NAN;  // its (lam_s + ||E||) / nu
     int n_sketch_total = 0;
     int grad_cg_iters = 0;      // adjoint CG iterations of the last genios_grad
     // device scalars
@@ -184,6 +187,9 @@ extern "C" void genios_default_options(genios_options* o) {
     o->box = 0;
     o->box_lo = 0.0;
     o->box_hi = 1.0;
+    o->sketch_adaptive = 0;
+    o->sketch_rank_max = 128;
+    o->sketch_theta = 10.0;
 }
 
 extern "C" genios_status genios_create(const genios_options* opts, int device, void* stream,
@@ -301,19 +307,31 @@ static genios_status load_matrix_f32(genios_ctx* ctx, const void* A, int dt, int
 
 // Tensor-core sketch operands: the blocked bf16 copies of A and A^T, packed once per data set
 // from the float32 (or stored) matrix.  Only for float value types with a sketch.
+// The sketch rank of the options (-1: min(50, n / 20), Table 2) and the rank its buffers are
+// sized for (the adaptive cap when the rank is chosen by §2.2's rule).
+static void sketch_ranks(const genios_options& o, int64_t N, int* s0, int* s_alloc) {
+    int sk = o.sketch_rank;
+    if (sk < 0) sk = (int)std::min<int64_t>(50, N / 20);
+    sk = std::max(0, (int)std::min<int64_t>(sk, N));
+    int sa = sk;
+    if (o.sketch_adaptive && sk > 0)
+        sa = std::max(sk, (int)std::min<int64_t>(std::min(128, std::max(1, o.sketch_rank_max)), N));
+    *s0 = sk;
+    *s_alloc = sa;
+}
+
 static cudaError_t tc_setup(genios_ctx* ctx, int src_prec, const void* A, int64_t lda,
                             const float* row_scale, int64_t M, int64_t N) {
     ctx->use_tc = false;
-    int sk = ctx->opt.sketch_rank;
-    if (sk < 0) sk = (int)std::min<int64_t>(50, N / 20);
-    sk = (int)std::min<int64_t>(sk, N);
+    int sk = 0, sa = 0;
+    sketch_ranks(ctx->opt, N, &sk, &sa);
     if (sk < 1 || ctx->prec == GENIOS_FP64 || !ctx->opt.tensor_sketch) return cudaSuccess;
-    TcPlan p = tc_plan(M, N, sk);
+    TcPlan p = tc_plan(M, N, sa);   // buffers for the largest rank; the packed A does not depend on s
     if (!p.ok) return cudaSuccess;
     cudaError_t e = ctx->mem.get(&ctx->tcbuf, tc_bytes(p));
     if (e != cudaSuccess) return e;
-    ctx->tc.plan = p;
-    ctx->tc.work = tc_carve(ctx->tcbuf, p);
+    ctx->tc.plan = tc_plan(M, N, sk);
+    ctx->tc.work = tc_carve(ctx->tcbuf, ctx->tc.plan);
     ctx->tc.wait_limit = (long long)ctx->opt.device_wait_limit_us * 2100LL;
     e = tc_pack_a(p, ctx->tc.work, src_prec, A, lda, row_scale, ctx->stream);
     if (e != cudaSuccess) return e;
@@ -420,11 +438,13 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
     if (!ctx->plan_hv.ok || !ctx->plan_g.ok)
         FAIL(GENIOS_EUNSUPPORTED, "n too large for the fused rowpass in this precision");
     ctx->ldp = std::max(ctx->lda, ctx->lda_g);
-    int sk = ctx->opt.sketch_rank;
-    if (sk < 0) sk = (int)std::min<int64_t>(50, N / 20);
-    sk = (int)std::min<int64_t>(sk, N);
-    ctx->sk = std::max(0, sk);
-    ctx->cgl = ctx->opt.persistent_cg ? cgloop_plan(hvp, M, N, ctx->lda, ctx->sk) : CgLoopPlan{};
+    int sk = 0, sk_alloc = 0;
+    sketch_ranks(ctx->opt, N, &sk, &sk_alloc);
+    ctx->sk = sk;
+    ctx->sk_alloc = sk_alloc;
+    ctx->sketch_adapted = false;
+    ctx->sketch_bound = NAN;
+    ctx->cgl = ctx->opt.persistent_cg ? cgloop_plan(hvp, M, N, ctx->lda, ctx->sk_alloc) : CgLoopPlan{};
     const int G = std::max(std::max(ctx->plan_hv.grid, ctx->plan_g.grid), ctx->cgl.ok ? ctx->cgl.rp.grid : 0);
     CK(ctx->mem.get(&ctx->Pbuf, (size_t)G * ctx->ldp * vt));
     CK(ctx->mem.get((void**)&ctx->loss_part, (size_t)G * 8));
@@ -436,13 +456,13 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
     CK(ctx->mem.get(&ctx->D, (size_t)M * vt));
     CK(ctx->mem.get(&ctx->W, (size_t)M * vt));
     // Nystrom
-    ctx->cgv = cgv_plan(ctx->dbl, N, ctx->sk);
+    ctx->cgv = cgv_plan(ctx->dbl, N, ctx->sk_alloc);
     if (!ctx->cgv.ok) FAIL(GENIOS_EUNSUPPORTED, "no thread-block cluster configuration for the CG vector kernel");
     if (ctx->sk > 0) {
-        CK(ctx->mem.get(&ctx->Om, (size_t)N * ctx->sk * vt));
-        CK(ctx->mem.get(&ctx->U, (size_t)N * ctx->sk * vt));
-        CK(ctx->mem.get((void**)&ctx->lam, (size_t)ctx->sk * 8));
-        const size_t wb = nystrom_work_bytes(hvp, M, N, ctx->sk);
+        CK(ctx->mem.get(&ctx->Om, (size_t)N * ctx->sk_alloc * vt));
+        CK(ctx->mem.get(&ctx->U, (size_t)N * ctx->sk_alloc * vt));
+        CK(ctx->mem.get((void**)&ctx->lam, (size_t)ctx->sk_alloc * 8));
+        const size_t wb = nystrom_work_bytes(hvp, M, N, ctx->sk_alloc);
         CK(ctx->mem.get(&ctx->nyswork, wb));
         ctx->nw = nystrom_carve(ctx->nyswork, hvp, M, N, ctx->sk);
     } else {
@@ -608,6 +628,61 @@ static genios_status build_precond(genios_ctx* ctx, const void* d, double* ms) {
     ctx->n_sketch_total++;
     CK(cudaStreamSynchronize(s));
     *ms += now_ms() - t0;
+    return GENIOS_OK;
+}
+
+// Switch the sketch rank to s <= sk_alloc: the workspaces are re-carved for s (the packed
+// tensor-core copies of A keep their place), and the next sketch starts from a fresh test matrix.
+static void set_sketch_rank(genios_ctx* ctx, int s) {
+    ctx->sk = s;
+    ctx->nw = nystrom_carve(ctx->nyswork, hv_prec(ctx), ctx->m, ctx->n, s);
+    if (ctx->use_tc) {
+        ctx->tc.plan = tc_plan(ctx->m, ctx->n, s);
+        ctx->tc.work = tc_carve(ctx->tcbuf, ctx->tc.plan);
+    }
+    ctx->omega_ready = false;
+    ctx->eig_warm = false;
+    ctx->have_precond = false;
+}
+
+// The adaptive sketch size of §2.2: from the current rank, sketch, estimate ||E|| for
+// E = H_data - U Lam U^T by randomized power steps (each one pass over A, then the rank-s
+// correction), and double s (up to sk_alloc) until (lam_s + ||E||) / nu <= sketch_theta.
+static genios_status adapt_sketch(genios_ctx* ctx, const void* d, double nu, double* ms) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = ctx->n;
+    const int G = ctx->plan_hv.grid;
+    for (;;) {
+        genios_status st = build_precond(ctx, d, ms);
+        if (st != GENIOS_OK) return st;
+        const double t0 = now_ms();
+        // v0 = a standard normal vector (its own Philox stream), then 20 power steps
+        CK(omega_fill(ctx->dbl, n, 1, ctx->opt.seed, 0x5e7u, ctx->r, s));
+        double est = 0.0;
+        for (int it = 0; it < 20; ++it) {
+            CK(hv_pass(ctx, ctx->r, nullptr, d, nullptr));
+            CK(hv_finish(ctx->dbl, ctx->Pbuf, G, ctx->ldp, n, 0.0, ctx->r, ctx->q, s));
+            CK(nys_error_step(ctx->dbl, n, ctx->sk, ctx->U, ctx->lam, ctx->r, ctx->q, ctx->S->nys_dots, ctx->sc, s));
+            ctx->launches += 5;
+            st = read_state(ctx);
+            if (st != GENIOS_OK) return st;
+            const double vy = ctx->Sh->nys_dots[0], yy = ctx->Sh->nys_dots[1], vv = ctx->Sh->nys_dots[2];
+            if (!(vv > 0.0) || !(yy > 0.0)) {
+                est = 0.0;
+                break;
+            }
+            est = std::max(0.0, vy / vv);
+            CK(nys_scale(ctx->dbl, n, ctx->q, 1.0 / std::sqrt(yy), ctx->r, s));
+        }
+        double lam_s = 0.0;
+        CK(cudaMemcpyAsync(&lam_s, ctx->lam + ctx->sk - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *ms += now_ms() - t0;
+        ctx->sketch_bound = (lam_s + est) / nu;
+        if (ctx->sketch_bound <= ctx->opt.sketch_theta || ctx->sk >= ctx->sk_alloc) break;
+        set_sketch_rank(ctx, std::min(2 * ctx->sk, ctx->sk_alloc));
+    }
+    ctx->sketch_adapted = true;
     return GENIOS_OK;
 }
 
@@ -916,7 +991,10 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
             const bool first = !ctx->have_precond;
             const bool resk = !quadratic && o.resketch_every > 0 && k > 1 && (k - 1) % o.resketch_every == 0;
             if (first || resk) {
-                st = build_precond(ctx, dvec, &inf.t_sketch_ms);
+                if (first && o.sketch_adaptive && !ctx->sketch_adapted && ctx->sk_alloc > ctx->sk)
+                    st = adapt_sketch(ctx, dvec, nu, &inf.t_sketch_ms);
+                else
+                    st = build_precond(ctx, dvec, &inf.t_sketch_ms);
                 if (st != GENIOS_OK) return st;
                 inf.sketches++;
             }
@@ -1007,6 +1085,8 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
         inf.hv_ms = ctx->Sh->hv_ns * 1e-6;   // device-timed Hv passes (graph launches or CG phases)
         inf.hv_launches = ctx->Sh->hv_count;
     }
+    inf.sketch_rank_used = ctx->sk;
+    inf.sketch_bound = ctx->sketch_bound;
     inf.cg_launches = ctx->Sh->cgl_count;
     inf.cg_ms = o.profile ? cg_ev_ms : ctx->Sh->cgl_ns * 1e-6;
     for (int k = 0; k < 6; ++k) inf.cg_phase_ms[k] = ctx->Sh->cgl_phase_ns[k] * 1e-6;

@@ -54,6 +54,7 @@ struct DevState {
     double hv_ns;     // accumulated device time of the timed Hv launches
     double cgl_ns;    // accumulated device time of the persistent CG launches (timed)
     int32_t cgl_count, cgl_iters;   // those launches and their CG iterations
+    double nys_dots[4];             // adaptive sketch: [v^T E v, ||E v||^2, v^T v] of a power step
     double cgl_phase_ns[6];         // CTA 0's time by phase: Hv, barrier, update, barrier,
                                     // direction, barrier
     double w[256];    // U^T r (Nystrom preconditioner), s <= 256 (op-level preconditioner)
@@ -305,6 +306,13 @@ cudaError_t nystrom_build(int prec, int64_t m, int64_t n, int sk, const void* A,
                           const float* row_scale, const void* d, const void* Om, void* U,
                           double* lam, double* eta_out, NysWork w, int* chol_ok, int flags,
                           const TcSketch* tc, cudaStream_t s);
+
+// Adaptive sketch size (§2.2): y holds H_data v on entry; y -= U diag(lam) U^T v, and out3 (device)
+// = [v^T y, y^T y, v^T v] (one power-method step on E = H_data - U diag(lam) U^T).  s <= 128.
+cudaError_t nys_error_step(bool dbl, int64_t n, int sk, const void* U, const double* lam, const void* v, void* y,
+                           double* out3, Scratch sc, cudaStream_t s);
+// v = scale * y
+cudaError_t nys_scale(bool dbl, int64_t n, const void* y, double scale, void* v, cudaStream_t s);
 
 // implicit gradient: r = g on the support of z (z_j != 0), 0 elsewhere
 cudaError_t adj_rhs(bool dbl, int64_t n, const double* g, const void* z, void* r, cudaStream_t s);

@@ -941,3 +941,98 @@ cudaError_t quantize_fp8_rows(int64_t m, int64_t n, const float* A, int64_t lda_
 }
 
 }  // namespace genios
+
+// ------------------------------------------------------------------------------------------
+// Adaptive sketch size (§2.2): power-method steps on E = H_data - U diag(lam) U^T
+// ------------------------------------------------------------------------------------------
+namespace genios {
+
+constexpr int NYS_ROWS = 64;   // rows of U per block of the U^T v partials
+
+// block partials of U^T v over NYS_ROWS rows: part[b][c], c < 128 (threads: c = t % 128, two halves)
+template <typename VT>
+__global__ void nys_utv_part_kernel(int64_t n, int sk, const VT* U, const VT* v, double* part) {
+    __shared__ double sh[256];
+    const int t = threadIdx.x, c = t & 127, h = t >> 7;
+    const int64_t r0 = (int64_t)blockIdx.x * NYS_ROWS;
+    double acc = 0.0;
+    if (c < sk)
+        for (int r = h; r < NYS_ROWS; r += 2) {
+            const int64_t j = r0 + r;
+            if (j < n) acc += (double)U[j * sk + c] * (double)v[j];
+        }
+    sh[t] = acc;
+    __syncthreads();
+    if (t < 128) part[(size_t)blockIdx.x * 128 + t] = c < sk ? sh[t] + sh[t + 128] : 0.0;
+}
+
+// w_c = lam_c sum_b part[b][c], in block order
+__global__ void nys_utv_reduce_kernel(int nb, int sk, const double* part, const double* lam, double* w) {
+    const int c = threadIdx.x;
+    if (c >= 128) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(size_t)b * 128 + c];
+    w[c] = c < sk ? lam[c] * s : 0.0;
+}
+
+// y -= U w, and out = [v^T y, y^T y, v^T v]
+template <typename VT>
+__global__ void nys_err_apply_kernel(int64_t n, int sk, const VT* U, const double* w, const VT* v, VT* y,
+                                     Scratch sc, double* out) {
+    __shared__ double wsh[128];
+    for (int c = threadIdx.x; c < 128; c += blockDim.x) wsh[c] = w[c];
+    __syncthreads();
+    double d[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < sk; ++c) acc += (double)U[j * sk + c] * wsh[c];
+        const double yj = (double)y[j] - acc;
+        y[j] = (VT)yj;
+        const double vj = (double)v[j];
+        d[0] += vj * yj;
+        d[1] += yj * yj;
+        d[2] += vj * vj;
+    }
+    double o[3];
+    if (grid_sum<3>(d, sc.part, sc.counter, o) && threadIdx.x == 0) {
+        out[0] = o[0];
+        out[1] = o[1];
+        out[2] = o[2];
+    }
+}
+
+template <typename VT>
+__global__ void nys_scale_kernel(int64_t n, const VT* y, double scale, VT* v) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        v[j] = (VT)((double)y[j] * scale);
+}
+
+template <typename VT>
+static cudaError_t err_step_vt(int64_t n, int sk, const void* U, const double* lam, const void* v, void* y,
+                               double* out3, Scratch sc, cudaStream_t s) {
+    const int nb = (int)((n + NYS_ROWS - 1) / NYS_ROWS);
+    double* part = sc.part + 65536;
+    double* w = part + (size_t)nb * 128;
+    nys_utv_part_kernel<VT><<<nb, 256, 0, s>>>(n, sk, static_cast<const VT*>(U), static_cast<const VT*>(v), part);
+    nys_utv_reduce_kernel<<<1, 128, 0, s>>>(nb, sk, part, lam, w);
+    const int g = (int)std::min<int64_t>(256, (n + 255) / 256);
+    nys_err_apply_kernel<VT><<<g, 256, 0, s>>>(n, sk, static_cast<const VT*>(U), w, static_cast<const VT*>(v),
+                                               static_cast<VT*>(y), sc, out3);
+    return cudaGetLastError();
+}
+
+cudaError_t nys_error_step(bool dbl, int64_t n, int sk, const void* U, const double* lam, const void* v, void* y,
+                           double* out3, Scratch sc, cudaStream_t s) {
+    if (sk < 0 || sk > 128 || (size_t)((n + NYS_ROWS - 1) / NYS_ROWS) * 128 + 128 > 196608) return cudaErrorInvalidValue;
+    return dbl ? err_step_vt<double>(n, sk, U, lam, v, y, out3, sc, s)
+               : err_step_vt<float>(n, sk, U, lam, v, y, out3, sc, s);
+}
+
+cudaError_t nys_scale(bool dbl, int64_t n, const void* y, double scale, void* v, cudaStream_t s) {
+    const int g = (int)std::min<int64_t>(512, (n + 255) / 256);
+    if (dbl) nys_scale_kernel<double><<<g, 256, 0, s>>>(n, static_cast<const double*>(y), scale, static_cast<double*>(v));
+    else nys_scale_kernel<float><<<g, 256, 0, s>>>(n, static_cast<const float*>(y), scale, static_cast<float*>(v));
+    return cudaGetLastError();
+}
+
+}  // namespace genios

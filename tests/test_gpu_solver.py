@@ -215,6 +215,30 @@ def test_bounded_least_squares_parity(G, prec):
         assert abs(obj(z) - obj(ref)) <= 1e-4 * obj(ref), (obj(z), obj(ref), kkt)
 
 
+def test_adaptive_sketch_size(G):
+    """§2.2's adaptive sketch size from s = 4 on a rank-10-plus-noise problem (the BLS instance,
+    FP64): the rank grows by doubling until (lam_s + ||E||) / nu <= theta; the oracle's rule
+    (its own test matrix) lands within one doubling; fewer CG iterations than the fixed s = 4;
+    and the solution still matches BVLS."""
+    from oracle import linalg as olin
+    P = problems.bls_lowrank(600, 300, rank=10, seed=problems.seed_for(7, 1))
+    A, b = rounded(P, 0)
+    kw = dict(box=1, eps_kkt=1e-8, rho=P.rho, rho_update_every=0)
+    # theta = 40: the oracle's rule stops at s = 32 here (bound 29.7; 12.4 at s = 64)
+    z, info, _ = gpu_solve(G, P, 0, 0.0, sketch_rank=4, sketch_adaptive=1, sketch_rank_max=64,
+                           sketch_theta=40.0, **kw)
+    assert info["status"] == 0, info
+    s_used, bound = info["sketch_rank_used"], info["sketch_bound"]
+    assert s_used in (8, 16, 32, 64) and (bound <= 40.0 or s_used == 64), (s_used, bound)
+    H = A.T @ A
+    _, _, s_or, _, b_or = olin.adaptive_nystrom(lambda O: H @ O, lambda v: H @ v, A.shape[1], 4, 64, P.rho, 40.0)
+    assert abs(np.log2(s_used / s_or)) <= 1, (s_used, s_or, bound, b_or)
+    z4, info4, _ = gpu_solve(G, P, 0, 0.0, sketch_rank=4, **kw)
+    assert info4["sketch_rank_used"] == 4 and np.isnan(info4["sketch_bound"])
+    assert info["cg_iters_total"] < info4["cg_iters_total"], (info["cg_iters_total"], info4["cg_iters_total"])
+    np.testing.assert_allclose(z, checks.bls_exact(A, b, 0.0, 1.0), atol=1e-6)
+
+
 def test_box_constraint_refusals(G):
     P = problems.bls_lowrank(200, 100, rank=5, seed=7)
     A = torch.from_numpy(P.A).cuda()
