@@ -513,7 +513,7 @@ static cudaError_t grad_pass(genios_ctx* ctx, const void* xv, void* Wout, void* 
     return rowpass_launch(a, ctx->plan_g, ctx->stream);
 }
 
-static cudaError_t hv_pass(genios_ctx* ctx, const void* v, const void* v_aux, const void* d,
+static cudaError_t hv_pass(genios_ctx* ctx, const void* v, const void* d,
                            const int* skip, bool timed = false) {
     RowpassArgs a{};
     a.prec = hv_prec(ctx);
@@ -524,8 +524,6 @@ static cudaError_t hv_pass(genios_ctx* ctx, const void* v, const void* v_aux, co
     a.A = ctx->A_hv;
     a.row_scale = ctx->A_scale;
     a.v = v;
-    a.v_aux = v_aux;
-    a.beta = &ctx->S->beta;
     a.d = d;
     a.partial = ctx->Pbuf;
     a.ldp = ctx->ldp;
@@ -660,7 +658,7 @@ static genios_status adapt_sketch(genios_ctx* ctx, const void* d, double nu, dou
         CK(omega_fill(ctx->dbl, n, 1, ctx->opt.seed, 0x5e7u, ctx->r, s));
         double est = 0.0;
         for (int it = 0; it < 20; ++it) {
-            CK(hv_pass(ctx, ctx->r, nullptr, d, nullptr));
+            CK(hv_pass(ctx, ctx->r, d, nullptr));
             CK(hv_finish(ctx->dbl, ctx->Pbuf, G, ctx->ldp, n, 0.0, ctx->r, ctx->q, s));
             CK(nys_error_step(ctx->dbl, n, ctx->sk, ctx->U, ctx->lam, ctx->r, ctx->q, ctx->S->nys_dots, ctx->sc, s));
             ctx->launches += 5;
@@ -713,7 +711,7 @@ static genios_status build_cg_graph(genios_ctx* ctx, const void* d, bool pc) {
     const int sk = pc ? ctx->sk : 0;
     cudaError_t e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = hv_pass(ctx, ctx->p, nullptr, d, &ctx->S->cg_done, true);
+    if (e == cudaSuccess) e = hv_pass(ctx, ctx->p, d, &ctx->S->cg_done, true);
     if (e == cudaSuccess)
         e = cgv_q(ctx->dbl, ctx->Pbuf, ctx->plan_hv.grid, ctx->ldp, ctx->n, ctx->p, ctx->q, ctx->U, sk,
                   ctx->sc.part, ctx->S, nullptr, ctx->cap_stream);
@@ -779,7 +777,7 @@ static genios_status cg_loop(genios_ctx* ctx, const void* d, int* iters, std::ve
             }
             CK(cudaEventRecord(ctx->evs[0], s));
         }
-        CK(hv_pass(ctx, ctx->p, nullptr, d, &ctx->S->cg_done));
+        CK(hv_pass(ctx, ctx->p, d, &ctx->S->cg_done));
         if (prof) CK(cudaEventRecord(ctx->evs[1], s));
         CK(cgv_q(ctx->dbl, ctx->Pbuf, G, ctx->ldp, ctx->n, ctx->p, ctx->q, ctx->U, sk, ctx->sc.part, ctx->S,
                  nullptr, s));
@@ -1413,7 +1411,7 @@ extern "C" genios_status genios_grad(genios_ctx* ctx, const void* dL_dx, double*
             const int G = ctx->plan_hv.grid;
             int it = 0;
             while (!ctx->Sh->cg_done && it < max_it + 2) {
-                if (hv_pass(ctx, ctx->p, nullptr, ctx->D, &ctx->S->cg_done) != cudaSuccess ||
+                if (hv_pass(ctx, ctx->p, ctx->D, &ctx->S->cg_done) != cudaSuccess ||
                     cgv_q(ctx->dbl, ctx->Pbuf, G, ctx->ldp, n, ctx->p, ctx->q, ctx->U, sk, ctx->sc.part, ctx->S,
                           ctx->z, s) != cudaSuccess ||
                     cgv_iter(ctx->dbl, ctx->cgv, n, ctx->q, ctx->r, ctx->delta, ctx->p, ctx->U, sk, ctx->lam, ctx->S,

@@ -58,7 +58,6 @@ struct DevState {
     double cgl_phase_ns[6];         // CTA 0's time by phase: Hv, barrier, update, barrier,
                                     // direction, barrier
     double w[256];    // U^T r (Nystrom preconditioner), s <= 256 (op-level preconditioner)
-    double cgw[128];  // U^T r of the current CG residual (cluster CG path, s <= 128)
     double cgc[128];  // preconditioner coefficients c_i w_i for the next direction
 };
 
@@ -76,8 +75,6 @@ struct RowpassArgs {
     const void* A_lo;           // P_HILO: low part
     const float* row_scale;     // P_FP8
     const void* v;              // input vector (value type)
-    const void* v_aux;          // if non-null: v := v_aux + beta * v  (fused CG direction update)
-    const double* beta;         // device scalar for the fused update
     const void* d;              // RP_HV: row weights or null (= 1)
     const void* b;              // RP_GRAD: offsets
     void* W_out;                // RP_GRAD: loss'(t) (may be null)

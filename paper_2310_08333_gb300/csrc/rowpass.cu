@@ -98,8 +98,6 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
     // ------------------------------------------------------------------ consumers
     const int lane = tid & 31, wid = tid >> 5;
     const VT* vin = static_cast<const VT*>(a.v);
-    const VT* vaux = static_cast<const VT*>(a.v_aux);
-    const VT beta = (vaux != nullptr) ? (VT)(*a.beta) : VT(0);
     VT vr[NCH][VEC];
     VT yr[NCH][VEC];
 #pragma unroll
@@ -110,10 +108,7 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
             const int64_t j = (int64_t)c * VEC + e;
             VT val = VT(0);
             if (c < nchunk_row && j < a.n) {
-                if (GCHK(a.dbg, j, a.n)) {
-                    val = vin[j];
-                    if (vaux != nullptr) val = vaux[j] + beta * val;
-                }
+                if (GCHK(a.dbg, j, a.n)) val = vin[j];
             }
             vr[k][e] = val;
             yr[k][e] = VT(0);
