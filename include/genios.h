@@ -94,8 +94,8 @@ typedef struct genios_options {
     double eps_gap;          /* duality-gap tolerance (default 1e-4) */
     double eps_kkt;          /* relative KKT tolerance (default 1e-4) */
     double gamma;            /* CG tolerance exponent (default 1.2, Table 2) */
-    double cg_tol_floor;     /* lower bound of the CG relative tolerance; < 0 (default): 10x the
-                                tightest stop tolerance, at most 1e-3, at least 1e-12 / 1e-6 /
+    double cg_tol_floor;     /* lower bound of the CG relative tolerance; < 0 (default): 100x the
+                                tightest stop tolerance, at most 1e-2, at least 1e-12 / 1e-6 /
                                 1e-4 for FP64 / FP32 / BF16-FP8 */
     double cg_tol_first;     /* CG relative tolerance at k = 1 (default 0.1) */
     int32_t sketch_rank;     /* Nystrom rank s; -1 = min(50, n/20) (Table 2); 0 = no preconditioner */
