@@ -108,6 +108,13 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample)
 # ------------------------------------------------------------------------------------------
+def reduced_problem(P, k: int):
+    """A 1/8-scale instance (m/8 x n/8) of the workload's generator, seeded by k."""
+    if P.loss == "logistic":
+        return problems.logistic_lowrank(P.m // 8, P.n // 8, nnz=50, seed=problems.seed_for(3, k))
+    return problems.lasso_ar1(P.m // 8, P.n // 8, nnz=25, seed=problems.seed_for(2, k))
+
+
 def oracle_baseline(P, lam: float, rho: float, budget_s: float = 25.0, iters: int | None = None) -> dict:
     """Estimate the float64 oracle's time to a 1e-4 relative KKT residual on this workload:
     (seconds per exact-solve ADMM iteration, timed at full size) x (iteration count).  With
@@ -130,10 +137,7 @@ def oracle_baseline(P, lam: float, rho: float, budget_s: float = 25.0, iters: in
                            f"iteration count this ADMM takes to 1e-4 rel-KKT on this workload)"),
                 "per_iter_s": per_iter, "iters": iters}
     # iteration count on a reduced instance of the same structure
-    if P.loss == "logistic":
-        Ps = problems.logistic_lowrank(P.m // 8, P.n // 8, nnz=50, seed=problems.seed_for(3, 77))
-    else:
-        Ps = problems.lasso_ar1(P.m // 8, P.n // 8, nnz=25, seed=problems.seed_for(2, 77))
+    Ps = reduced_problem(P, 77)
     lam_s = Ps.lam_frac * checks.lambda_max(Ps.A, Ps.b, Ps.loss)
     t1 = time.perf_counter()
     rs = admm.solve(Ps.A, Ps.b, Ps.loss, lam_s, Ps.mu, rho=rho, tol=1e-4, max_iter=3000,
@@ -517,12 +521,19 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    from oracle import checks
+    from oracle import admm, checks
     _, rho, desc = WORKLOADS[args.workload]
     P = make_problem(args.workload)
     A = P.A.astype(np.float32).astype(np.float64)
     P.A = A
     lam = P.lam_frac * checks.lambda_max(A, P.b, P.loss)
+    # untimed warm-up: one oracle ADMM iteration per step on a 1/8-scale instance of the same
+    # generator (thread pools and BLAS pages in, a second or so each)
+    Pw = reduced_problem(P, 78)
+    lam_w = Pw.lam_frac * checks.lambda_max(Pw.A, Pw.b, Pw.loss)
+    for _ in range(args.warmup):
+        admm.solve(Pw.A, Pw.b, Pw.loss, lam_w, Pw.mu, rho=rho, max_iter=1, check_every=10 ** 9,
+                   polish_below=None, rho_update_every=0)
     vals = []
     t0 = time.perf_counter()
     for _ in range(max(1, args.steps)):
@@ -533,7 +544,7 @@ def run_reference(args):
     v = float(np.mean(vals))
     cpu["value"] = v
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
-           "steps": len(vals), "warmup": 0, "ms_per_step": v * 1e3, "higher_is_better": False,
+           "steps": len(vals), "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded generator; the paper's datasets are not available)",
            "config": {"workload": args.workload, "description": desc, "m": P.m, "n": P.n,
