@@ -95,3 +95,27 @@ def test_create_without_gpu_fails_loudly(L):
     assert lib.genios_op_lda(L.FP8_E4M3, 1000) == 1024
     assert lib.genios_op_lda(L.FP64, 1000) == 1000
     assert lib.genios_op_lda(7, 1000) == 0
+
+
+def _sources(top, exts):
+    for d, _, files in os.walk(os.path.join(ROOT, top)):
+        if "__pycache__" in d or "_build" in d:
+            continue
+        for f in files:
+            if f.endswith(exts):
+                yield os.path.join(d, f)
+
+
+def test_oracle_and_cuda_path_share_no_code():
+    """The oracle and the product path are independent: the package (its Python and its CUDA
+    sources) never names the oracle, and neither the oracle nor the input generators name the
+    package, its sources or the C ABI header."""
+    pkg = list(_sources("paper_2310_08333_gb300", (".py", ".cu", ".cuh", ".h", ".cpp")))
+    assert len(pkg) >= 10
+    for p in pkg:
+        assert not re.search(r"\boracle\b", open(p).read()), p
+    for top in ("oracle", "problems"):
+        for p in _sources(top, (".py", ".c", ".h")):
+            src = open(p).read()
+            for name in ("paper_2310_08333_gb300", "csrc", "genios.h", "libgenios"):
+                assert name not in src, (p, name)
