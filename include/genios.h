@@ -6,11 +6,13 @@
  *     minimize  sum_i loss(a_i^T x - b_i) + lambda_1 ||x||_1 + (lambda_2 / 2) ||x||_2^2
  *
  * written as f(x) + g(z) subject to x - z = 0 (§1.1, Eq. (1) with M = I, c = 0), with
- * loss = squared (1/2 w^2) or logistic (log(1 + e^w)).  Each ADMM iteration (§2, Eqs. (3)-(6))
- * solves the linear system of Eq. (7) inexactly by conjugate gradients preconditioned with a
- * randomized Nystrom approximation (§2.1, §2.2, Eq. (10)); Hessian-vector products are
- * A^T (D (A v)) with D = diag(loss''(A x^k - b)) (§3.1, §3.3).  The z-update is the
- * soft-threshold prox with over-relaxation (§2.5), termination follows §2.3 (residuals of
+ * loss = squared (1/2 w^2), logistic (log(1 + e^w)) or the Huber loss of §4.4 (w^2 on |w| <= 1,
+ * 2|w| - 1 beyond).  With the `box` option g is instead the indicator of a box (the bounded
+ * least squares of §4.5).  Each ADMM iteration (§2, Eqs. (3)-(6)) solves the linear system of
+ * Eq. (7) inexactly by conjugate gradients preconditioned with a randomized Nystrom
+ * approximation (§2.1, §2.2, Eq. (10)); Hessian-vector products are A^T (D (A v)) with
+ * D = diag(loss''(A x^k - b)) (§3.1, §3.3).  The z-update is the soft-threshold prox (or the
+ * projection onto the box) with over-relaxation (§2.5), termination follows §2.3 (residuals of
  * Eqs. (11)-(12)) and App. A (duality gap), or a relative KKT residual.
  *
  * Conventions for every entry point:
@@ -199,7 +201,12 @@ genios_status genios_create(const genios_options* opts, int device, void* stream
  *   shared_A: 1: one data set (m[0], n[0], A[0], b[0], lda[0]) shared by the K problems, which
  *             differ only in (lambda_1, lambda_2): a regularisation path.  0: K independent data
  *             sets of their own sizes (arrays of K entries).
- * Builds the precision copies of A requested by opts.precision (per data set). */
+ * Builds the precision copies of A requested by opts.precision (per data set).
+ * Size limits: each thread of the fused row pass keeps its slice of an n-vector in registers,
+ * and a CTA's shared-memory ring holds at least two stages of rows, so n <= 8192 in
+ * GENIOS_FP64, n <= 20480 in GENIOS_FP32 and n <= 28096 in GENIOS_BF16 and GENIOS_FP8_E4M3
+ * (their gradient pass streams a row's bf16 hi and lo planes together); a larger n returns
+ * GENIOS_EUNSUPPORTED.  m is limited only by device memory. */
 genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const int64_t* m, const int64_t* n,
                               const void* const* A, int A_dtype, const int64_t* lda,
                               const void* const* b, int shared_A);
