@@ -6,7 +6,7 @@ context for torch tensors / NumPy arrays.  PyTorch is used only for device memor
 """
 from . import _lib  # noqa: F401
 from ._lib import (  # noqa: F401
-    FP64, FP32, BF16, FP8_E4M3, LOSS_SQUARED, LOSS_LOGISTIC, STOP_RESID, STOP_GAP, STOP_KKT,
+    FP64, FP32, BF16, FP8_E4M3, LOSS_SQUARED, LOSS_LOGISTIC, LOSS_HUBER, STOP_RESID, STOP_GAP, STOP_KKT,
     GeniosError, Info, Options, default_options, lib,
 )
 from .solver import Solver, ops  # noqa: F401
