@@ -1,11 +1,18 @@
 // Randomized Nystrom approximation of A^T diag(d) A (§2.2, §3.3) and the test matrix (sm_103a).
 //
-//   Omega   : Philox4x32-10 (Salmon et al. 2011) + Box-Muller standard normals.
-//   sketch  : W = A Omega (m x s), W <- diag(d) W, Y = A^T W (n x s)    [tiled CUDA-core GEMMs]
+//   Omega   : Philox4x32-10 (Salmon et al. 2011) + Box-Muller standard normals, made orthonormal
+//             by CholeskyQR2 once per data set.
+//   sketch  : W = A Omega (m x s), W <- diag(d) W, Y = A^T W (n x s): tensor-core GEMMs
+//             (umma.cu) for float value types, the tiled CUDA-core GEMMs below for float64.
 //   core    : eta = sqrt(n) eps ||Y||_F; Y_eta = Y + eta Omega; G = Omega^T Y_eta (FP64 sums);
-//             G = C^T C (FP64 Cholesky, one CTA); B = Y_eta C^{-1}; B^T B = V Sigma^2 V^T
-//             (cyclic Jacobi with round-robin parallel ordering, Golub & Van Loan §8.5, FP64,
-//             one CTA); U = B V Sigma^{-1}; lam = max(Sigma^2 - eta, 0), sorted descending.
+//             G = C^T C (FP64 Cholesky, one CTA, eta x 10 and retry on failure);
+//             B = Y_eta C^{-1}; B^T B = V Sigma^2 V^T by cyclic Jacobi with round-robin parallel
+//             ordering (Golub & Van Loan §8.5) in the value type, one CTA, warm-started from
+//             the previous sketch's V when the test matrix is reused; one Newton-Schulz step
+//             re-orthogonalises V; in float32 the eigenvalues are refined by float64 Rayleigh
+//             quotients; U = B V Sigma^{-1}; lam = max(Sigma^2 - eta, 0), sorted descending.
+//   adaptive: the power steps that estimate ||A^T diag(d) A - U diag(lam) U^T|| for the
+//             adaptive sketch size (nys_error_step, nys_scale).
 // The shift uses the machine epsilon of the value type (float64 or float32).
 #include "common.cuh"
 #include "internal.h"
