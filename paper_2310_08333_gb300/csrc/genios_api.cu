@@ -4,11 +4,15 @@
 // c = 0, in the step form of Eq. (7): (A^T D A + nu I) delta = -(grad f(x^k) + rho (x^k - z^k
 // + u^k)), nu = rho + lambda_2 + sigma, which has the same solution x^{k+1} = x^k + delta.
 // Per iteration: one gradient rowpass over A (§3.3), the inexact PCG solve (§2.1) whose
-// Hessian-vector products are fused rowpasses, the Nystrom preconditioner of Eq. (10)
+// Hessian-vector products are fused rowpasses (the whole solve and the z/u update after it in
+// one persistent cooperative launch, cgloop.cu; or, with persistent_cg = 0, per-iteration
+// launches captured in a CUDA graph), the Nystrom preconditioner of Eq. (10)
 // (re-sketched every `resketch_every` iterations for a non-constant loss'', once for the
-// squared loss, §3.3 / Table 2), the fused z/u update (§2.5, §3.1, Eq. (5)), residuals
-// (Eqs. (11)-(12)), the §2.3 stopping test / App. A duality gap / relative KKT, and the
-// penalty update of §2.5.
+// squared loss, §3.3 / Table 2; its rank optionally chosen by the adaptive rule of §2.2), the
+// fused z/u update (§2.5, §3.1, Eq. (5); the soft threshold, or the projection onto a box for
+// the bounded least squares of §4.5), residuals (Eqs. (11)-(12)), the §2.3 stopping test /
+// App. A duality gap / relative KKT (checked on a schedule, KktSchedule), and the penalty
+// update of §2.5.
 #include "common.cuh"
 #include "internal.h"
 #include "genios.h"
