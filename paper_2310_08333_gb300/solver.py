@@ -34,6 +34,30 @@ def _ptr(a):
     raise TypeError(type(a))
 
 
+def _rows(A):
+    """A with unit stride along its rows (the C ABI reads row-major with a leading dimension):
+    NumPy arrays and torch tensors laid out otherwise (a transpose, a column slice) are copied
+    into row-major order."""
+    if torch is not None and isinstance(A, torch.Tensor):
+        if A.dim() != 2:
+            raise ValueError("A must be a matrix")
+        if A.stride(1) != 1 or A.stride(0) < A.shape[1]:
+            A = A.contiguous()
+        return A
+    return np.ascontiguousarray(A)
+
+
+def _vec(v, like=None):
+    """A contiguous vector (of like's dtype for NumPy input when given)."""
+    if torch is not None and isinstance(v, torch.Tensor):
+        return v.contiguous()
+    return np.ascontiguousarray(v, dtype=None if like is None else like.dtype)
+
+
+def _lda(A) -> int:
+    return A.stride(0) if torch is not None and isinstance(A, torch.Tensor) else A.strides[0] // A.itemsize
+
+
 def _dt(a) -> int:
     if torch is not None and isinstance(a, torch.Tensor):
         return {torch.float64: L.DT_F64, torch.float32: L.DT_F32}[a.dtype]
@@ -57,12 +81,12 @@ class Solver:
     def set_data(self, A, b, loss: int | str = L.LOSS_SQUARED):
         if isinstance(loss, str):
             loss = L.LOSSES[loss]
-        if isinstance(A, np.ndarray):
-            A = np.ascontiguousarray(A)
-            b = np.ascontiguousarray(b, dtype=A.dtype)
+        A = _rows(A)
+        b = _vec(b, A if isinstance(A, np.ndarray) else None)
         m, n = A.shape
-        lda = A.stride(0) if torch is not None and isinstance(A, torch.Tensor) else A.strides[0] // A.itemsize
-        mm, nn, ll = (C.c_int64 * 1)(m), (C.c_int64 * 1)(n), (C.c_int64 * 1)(lda)
+        if b.shape != (m,):
+            raise ValueError("b must be a vector of m entries")
+        mm, nn, ll = (C.c_int64 * 1)(m), (C.c_int64 * 1)(n), (C.c_int64 * 1)(_lda(A))
         Ap = (C.c_void_p * 1)(_ptr(A).value)
         bp = (C.c_void_p * 1)(_ptr(b).value)
         st = self._lib.genios_set_data(self._ctx, loss, 1, mm, nn, Ap, _dt(A), ll, bp, 0)
@@ -75,14 +99,15 @@ class Solver:
         differ in lambda (a regularisation path).  Otherwise: len(As) independent problems."""
         if isinstance(loss, str):
             loss = L.LOSSES[loss]
-        As = [np.ascontiguousarray(a) if isinstance(a, np.ndarray) else a for a in As]
-        bs = [np.ascontiguousarray(b, dtype=a.dtype) if isinstance(b, np.ndarray) else b for a, b in zip(As, bs)]
+        As = [_rows(a) for a in As]
+        bs = [_vec(b, a if isinstance(a, np.ndarray) else None) for a, b in zip(As, bs)]
+        if any(b.shape != (a.shape[0],) for a, b in zip(As, bs)):
+            raise ValueError("each b must be a vector of its matrix's m entries")
         K = path_size if path_size is not None else len(As)
         cnt = len(As)
         ms = (C.c_int64 * cnt)(*[a.shape[0] for a in As])
         ns = (C.c_int64 * cnt)(*[a.shape[1] for a in As])
-        lds = (C.c_int64 * cnt)(*[(a.stride(0) if torch is not None and isinstance(a, torch.Tensor)
-                                   else a.strides[0] // a.itemsize) for a in As])
+        lds = (C.c_int64 * cnt)(*[_lda(a) for a in As])
         Ap = (C.c_void_p * cnt)(*[_ptr(a).value for a in As])
         bp = (C.c_void_p * cnt)(*[_ptr(b).value for b in bs])
         st = self._lib.genios_set_data(self._ctx, loss, K, ms, ns, Ap, _dt(As[0]), lds, bp,
@@ -130,6 +155,9 @@ class Solver:
         """Returns (z, info dict).  ``out`` (host ndarray or torch tensor) receives z if given."""
         if out is None:
             out = np.empty(self.n, dtype=out_dtype)
+        elif tuple(out.shape) != (self.n,) or not (out.is_contiguous() if torch is not None and
+                                                   isinstance(out, torch.Tensor) else out.flags.c_contiguous):
+            raise ValueError("out must be a contiguous vector of n entries")
         info = L.Info()
         l1, l2 = (C.c_double * 1)(lam1), (C.c_double * 1)(lam2)
         st = self._lib.genios_solve(self._ctx, l1, l2, _ptr(out), _dt(out), C.byref(info),

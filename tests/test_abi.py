@@ -119,3 +119,20 @@ def test_oracle_and_cuda_path_share_no_code():
             src = open(p).read()
             for name in ("paper_2310_08333_gb300", "csrc", "genios.h", "libgenios"):
                 assert name not in src, (p, name)
+
+
+def test_binding_passes_row_major_matrices():
+    """The binding hands the C ABI row-major data with a leading dimension: a transposed or
+    column-major matrix is copied into row-major order, a row-padded one keeps its stride."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    from paper_2310_08333_gb300 import solver as S
+    A = torch.arange(35.0).reshape(5, 7)
+    At = S._rows(A.T)
+    assert At.is_contiguous() and S._lda(At) == 5 and torch.equal(At, A.T)
+    padded = torch.zeros(5, 9)[:, :7]
+    assert S._rows(padded).data_ptr() == padded.data_ptr() and S._lda(S._rows(padded)) == 9
+    F = np.asfortranarray(np.arange(12.0).reshape(4, 3))
+    assert S._rows(F).flags.c_contiguous and S._lda(S._rows(F)) == 3
+    assert S._vec(np.arange(3), np.zeros((2, 2), np.float32)).dtype == np.float32
+    assert S._vec(torch.arange(6.0)[::2]).is_contiguous()
