@@ -47,11 +47,17 @@ def _rows(A):
     return np.ascontiguousarray(A)
 
 
-def _vec(v, like=None):
-    """A contiguous vector (of like's dtype for NumPy input when given)."""
+def _vec(v, like):
+    """v as a contiguous vector in the dtype of the matrix `like` (the C ABI reads b with A's
+    dtype), on like's device when both are torch tensors.  A NumPy vector given with a torch
+    matrix becomes a tensor on that matrix's device, and the reverse a NumPy array."""
+    if torch is not None and isinstance(like, torch.Tensor):
+        if not isinstance(v, torch.Tensor):
+            v = torch.from_numpy(np.ascontiguousarray(v))
+        return v.to(device=like.device, dtype=like.dtype).contiguous()
     if torch is not None and isinstance(v, torch.Tensor):
-        return v.contiguous()
-    return np.ascontiguousarray(v, dtype=None if like is None else like.dtype)
+        v = v.detach().cpu().numpy()
+    return np.ascontiguousarray(v, dtype=like.dtype)
 
 
 def _lda(A) -> int:
@@ -82,9 +88,9 @@ class Solver:
         if isinstance(loss, str):
             loss = L.LOSSES[loss]
         A = _rows(A)
-        b = _vec(b, A if isinstance(A, np.ndarray) else None)
+        b = _vec(b, A)
         m, n = A.shape
-        if b.shape != (m,):
+        if tuple(b.shape) != (m,):
             raise ValueError("b must be a vector of m entries")
         mm, nn, ll = (C.c_int64 * 1)(m), (C.c_int64 * 1)(n), (C.c_int64 * 1)(_lda(A))
         Ap = (C.c_void_p * 1)(_ptr(A).value)
@@ -100,8 +106,10 @@ class Solver:
         if isinstance(loss, str):
             loss = L.LOSSES[loss]
         As = [_rows(a) for a in As]
-        bs = [_vec(b, a if isinstance(a, np.ndarray) else None) for a, b in zip(As, bs)]
-        if any(b.shape != (a.shape[0],) for a, b in zip(As, bs)):
+        if any(_dt(a) != _dt(As[0]) for a in As):
+            raise ValueError("every matrix of a batch must have the same dtype (float64 or float32)")
+        bs = [_vec(b, a) for a, b in zip(As, bs)]
+        if any(tuple(b.shape) != (a.shape[0],) for a, b in zip(As, bs)):
             raise ValueError("each b must be a vector of its matrix's m entries")
         K = path_size if path_size is not None else len(As)
         cnt = len(As)
@@ -251,6 +259,12 @@ def hv_noalloc(prec, A, n, d, nu, v, row_scale=None):
     return y
 
 
+def status():
+    """Raises GeniosError(ETIMEOUT) if an op-level row pass on the current device ran out of its
+    wait bound since the last check (synchronises the current stream)."""
+    _chk(L.lib().genios_op_status(_stream_ptr()))
+
+
 def gradient(loss, prec, A, A_lo, n, b, x, lam2):
     m = A.shape[0]
     g = torch.empty(n, dtype=_vt(prec), device="cuda")
@@ -355,7 +369,7 @@ def pcg(prec, A, n, d, nu, r, U=None, lam=None, rtol=1e-6, max_iter=100, row_sca
     return delta, it.value, rel.value
 
 
-ops = SimpleNamespace(lda=lda, pad=pad, hv=hv, hv_noalloc=hv_noalloc, gradient=gradient, zu_update=zu_update, nystrom=nystrom,
+ops = SimpleNamespace(lda=lda, pad=pad, hv=hv, hv_noalloc=hv_noalloc, status=status, gradient=gradient, zu_update=zu_update, nystrom=nystrom,
                       nystrom_workspace=nystrom_workspace, sketch=sketch,
                       precond=precond, omega=omega, philox=philox, quantize=quantize, pcg=pcg)
 

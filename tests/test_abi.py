@@ -135,4 +135,28 @@ def test_binding_passes_row_major_matrices():
     F = np.asfortranarray(np.arange(12.0).reshape(4, 3))
     assert S._rows(F).flags.c_contiguous and S._lda(S._rows(F)) == 3
     assert S._vec(np.arange(3), np.zeros((2, 2), np.float32)).dtype == np.float32
-    assert S._vec(torch.arange(6.0)[::2]).is_contiguous()
+    assert S._vec(torch.arange(6.0)[::2], torch.zeros(3, 3)).is_contiguous()
+
+
+def test_binding_gives_b_the_dtype_of_A():
+    """The C ABI reads b with A's dtype (one A_dtype argument): the binding converts b, whatever
+    its own dtype or container, to A's dtype (and, for a torch A, to A's device) before the
+    call, so float32 A with a float64 b never hands the library a buffer of the wrong width."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    from paper_2310_08333_gb300 import solver as S
+    b64 = np.linspace(-1.0, 1.0, 5)
+    A32n, A64n = np.zeros((5, 3), np.float32), np.zeros((5, 3), np.float64)
+    A32t, A64t = torch.zeros(5, 3, dtype=torch.float32), torch.zeros(5, 3, dtype=torch.float64)
+    for A, b in ((A32n, b64), (A32n, torch.from_numpy(b64)), (A64n, b64.astype(np.float32)),
+                 (A64n, torch.from_numpy(b64.astype(np.float32)))):
+        v = S._vec(b, A)
+        assert isinstance(v, np.ndarray) and v.dtype == A.dtype and v.flags.c_contiguous
+        assert v.nbytes == A.shape[0] * A.itemsize
+        np.testing.assert_allclose(v, b64, rtol=1e-7)
+    for A, b in ((A32t, b64), (A32t, torch.from_numpy(b64)), (A64t, b64.astype(np.float32)),
+                 (A64t, torch.from_numpy(b64)[::1])):
+        v = S._vec(b, A)
+        assert isinstance(v, torch.Tensor) and v.dtype == A.dtype and v.is_contiguous()
+        assert v.device == A.device
+        np.testing.assert_allclose(v.double().numpy(), b64, rtol=1e-7)
