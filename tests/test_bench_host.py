@@ -1,6 +1,6 @@
 """Host logic of bench.py that needs no GPU: the clock summary taken during the timed region,
-the validity check of the committed ncu traffic record, and the reduced problem used for the
-oracle's iteration count."""
+the validity check of the committed ncu traffic record, the iteration count the oracle legs take
+from the committed bench record, and the oracle leg itself on a small problem."""
 import json
 import os
 
@@ -48,8 +48,37 @@ def test_traffic_record_is_tied_to_the_kernel_sources(tmp_path, monkeypatch):
     assert bench.traffic_record("cgloop_fp32", "other") is None
 
 
-def test_reduced_problem_keeps_the_generator_and_scales_by_eight():
-    P = bench.make_problem("lasso_1000x10000")
-    R = bench.reduced_problem(P, 77)
-    assert (R.m, R.n, R.loss) == (P.m // 8, P.n // 8, P.loss)
-    assert np.all(np.isfinite(R.A)) and R.A.shape == (R.m, R.n)
+def test_recorded_iteration_count_comes_from_the_committed_bench_record(tmp_path, monkeypatch):
+    its, rec = bench.recorded_iterations("logistic_20000x8000")
+    assert rec == os.path.join("profiles", "bench_logistic_20000x8000.json")
+    committed = json.load(open(os.path.join(bench.ROOT, rec)))["solve"]["iters"]
+    assert its == int(np.median(committed)) and its > 0
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "bench_w.json").write_text(json.dumps({"solve": {"iters": [10, 30, 20]}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.recorded_iterations("w")[0] == 20
+    assert bench.recorded_iterations("missing")[0] is None
+
+
+def test_blas_threads_follow_the_environment(monkeypatch):
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        monkeypatch.delenv(k, raising=False)
+    assert bench.blas_threads() == os.cpu_count()
+    monkeypatch.setenv("OMP_NUM_THREADS", "3")
+    assert bench.blas_threads() == 3
+
+
+def test_oracle_leg_certifies_z_and_times_an_iteration():
+    """The cpu_baseline leg on a small Lasso: the oracle's float64 rel-KKT of a given z, and a
+    value equal to the timed seconds per exact iteration times the count passed in."""
+    import problems
+    from oracle import admm, checks
+    P = problems.lasso_iid(60, 120, nnz=6, seed=3)
+    lam = 0.1 * checks.lambda_max(P.A, P.b, "squared")
+    ref = admm.solve(P.A, P.b, "squared", lam, tol=1e-10)
+    leg = bench.oracle_leg(P, lam, 1.0, ref["z"], iters=50, sample_iters=2)
+    assert leg["rel_kkt_oracle"] <= 1e-10
+    assert leg["value"] == leg["per_iter_s"] * 50 and leg["per_iter_s"] > 0
+    assert leg["kind"] == "oracle" and leg["cores"] >= 1 and "x 50 iterations" in leg["sample"]
+    bad = bench.oracle_leg(P, lam, 1.0, np.zeros(P.n), iters=1, sample_iters=1)
+    assert bad["rel_kkt_oracle"] > 1e-3     # z = 0 is not the solution below lambda_max
