@@ -80,7 +80,8 @@ typedef enum {
 /* Stop rules (bitmask; any satisfied rule stops). */
 enum {
     GENIOS_STOP_RESID = 1, /* §2.3 absolute + relative residual test */
-    GENIOS_STOP_GAP = 2,   /* App. A relative duality gap (min-denominator form) <= eps_gap */
+    GENIOS_STOP_GAP = 2,   /* App. A relative duality gap (min-denominator form) <= eps_gap,
+                              at the iterate x^k and then at z^k, the vector returned */
     GENIOS_STOP_KKT = 4    /* relative KKT residual at z, ||dist(0, dF(z))|| / max(||grad f(z)||,
                               lambda_1) <= eps_kkt (one extra pass over A per check; checked
                               when the residual test first passes, then at intervals of 1 to
@@ -116,7 +117,11 @@ typedef struct genios_options {
                                 (default 10) */
     int32_t use_graphs;      /* capture the CG loop in a CUDA graph (default 1) */
     uint64_t seed;           /* seed of the Gaussian test matrix (Philox4x32-10) */
-    int64_t device_wait_limit_us; /* bound on any device-side wait (default 2e6 us) */
+    int64_t device_wait_limit_us; /* bound on a device-side wait for another thread or CTA
+                                (default 2e6 us, at most 3.6e9; 0: give up at the first
+                                unsuccessful poll); a wait that runs out ends the call with
+                                GENIOS_ETIMEOUT.  A CTA's wait for its own copies and MMAs to
+                                land before it exits is bounded by max(this, ~1 s) */
     int32_t verbose;         /* 0 silent; N > 0: log every N-th iteration to stderr */
     int32_t profile;         /* 1: time the gradient passes and the CG launches with CUDA events
                                 (info.grad_ms, info.cg_ms; per Hv launch on the per-kernel path) */
@@ -149,6 +154,13 @@ typedef struct genios_options {
                                 rank found is kept for the re-sketches and later solves */
     int32_t sketch_rank_max; /* cap of the adaptive rank (default 128, at most 128) */
     double sketch_theta;     /* target of the bound kappa <= 1 + theta (default 10) */
+    int32_t device_loop;     /* 1 (default): with the persistent CG kernel, the STOP_KKT / STOP_RESID
+                                rules, profile = 0 and verbose = 0, the per-iteration decisions of
+                                §2.1-§2.5 (stop tests, KKT schedule, penalty update, CG tolerance)
+                                run on the device between the iteration's kernels, and the host
+                                syncs only at re-sketches and every few iterations; 0: the host
+                                reads the device state and decides after every gradient pass.
+                                Both take the same steps */
 } genios_options;
 
 typedef struct genios_info {
@@ -161,10 +173,12 @@ typedef struct genios_info {
     double rho;              /* final penalty */
     double lambda1, lambda2;
     double r_p, r_d;         /* ||x - z||, ||grad f(x) + rho u|| at the last check */
-    double rel_gap;          /* relative duality gap at the last evaluation (NaN if never) */
+    double rel_gap;          /* relative duality gap at the last evaluation (NaN if never); on
+                                a STOP_GAP stop, the gap at the returned z */
     double rel_kkt;          /* ||dist(0, dF(z))|| / max(||grad f(z)||, lambda_1) at the last
                                 evaluation (NaN if never) */
-    double objective;        /* loss + lambda_1||x||_1 + lambda_2/2||x||^2 at x (last gradient pass) */
+    double objective;        /* loss + lambda_1||x||_1 + lambda_2/2||x||^2 at x (last gradient
+                                pass); at z on a STOP_GAP stop */
     double t_setup_ms;       /* quantisation / data preparation (set_data) */
     double t_sketch_ms;      /* Nystrom sketch + core, total */
     double t_solve_ms;       /* wall time of genios_solve */
@@ -251,7 +265,17 @@ void genios_destroy(genios_ctx* ctx);
  * float64 for GENIOS_FP64 and float32 for the other precisions ("value type").  `workspace`
  * is caller-owned device scratch of at least genios_op_workspace_bytes(...) bytes, 256-byte
  * aligned.
+ * The row passes of genios_op_hv, genios_op_hv_noalloc and genios_op_gradient wait on their
+ * own copy stream with a bound of about 2 s; a bound that runs out leaves that call's outputs
+ * incomplete and is recorded in a per-device fault word, which these asynchronous calls
+ * cannot return.  genios_op_status reports it.
  * ------------------------------------------------------------------------------------------ */
+
+/* Synchronises `stream`, then reads and clears the current device's op-level fault word:
+ * GENIOS_ETIMEOUT (reason in genios_last_error(NULL)) if a row pass of an op-level call on this
+ * device ran out of its wait bound since the last genios_op_status, else GENIOS_OK.  Not a
+ * step of the paper's method: the status channel of the asynchronous op-level calls. */
+genios_status genios_op_status(void* stream);
 
 /* Device scratch needed by genios_op_hv / genios_op_gradient for an m x n problem. */
 size_t genios_op_workspace_bytes(int precision, int64_t m, int64_t n);
@@ -382,7 +406,10 @@ genios_status genios_op_pcg(int precision, int64_t m, int64_t n, const void* A, 
  *   - The first call on a device looks up the array's device address on that device (once);
  *     make that first call before any stream capture.
  *   - All calls share the scratch.  Calls whose kernels may overlap on the GPU (different
- *     streams, or unordered host threads on one device) race on it; order them. */
+ *     streams, or unordered host threads on one device) race on it; order them.
+ *   - The device address is cached for the process: after cudaDeviceReset on a device, do not
+ *     call this entry point on that device again.
+ *   - A bounded wait that runs out is reported by genios_op_status, as for genios_op_hv. */
 genios_status genios_op_hv_noalloc(int precision, int64_t m, int64_t n, const void* A, int64_t lda,
                                    const float* row_scale, const void* d, double nu, const void* v,
                                    void* y, void* stream);

@@ -41,7 +41,7 @@ class Options(C.Structure):
         ("verbose", C.c_int32), ("profile", C.c_int32), ("tensor_sketch", C.c_int32),
         ("batch_lockstep", C.c_int32), ("persistent_cg", C.c_int32), ("box", C.c_int32),
         ("box_lo", C.c_double), ("box_hi", C.c_double), ("sketch_adaptive", C.c_int32),
-        ("sketch_rank_max", C.c_int32), ("sketch_theta", C.c_double),
+        ("sketch_rank_max", C.c_int32), ("sketch_theta", C.c_double), ("device_loop", C.c_int32),
     ]
 
 
@@ -103,6 +103,7 @@ SIGNATURES = {
     "genios_op_pcg": (_i32, [_i32, _i64, _i64, _vp, _i64, _vp, _vp, _d, _vp, _i32, _vp, _vp, _d, _i32,
                              _vp, C.POINTER(_i32), C.POINTER(_d), _vp]),
     "genios_op_hv_noalloc": (_i32, [_i32, _i64, _i64, _vp, _i64, _vp, _vp, _d, _vp, _vp, _vp]),
+    "genios_op_status": (_i32, [_vp]),
 }
 
 _lib = None

@@ -63,6 +63,7 @@ struct CglShared {
     int ns, nstage_work, it, start;
     unsigned epoch;             // grid barriers passed (thread 0)
     int32_t stop;               // set by the consumers when they leave; read by the producer
+    double rho, u_scale, nu, tol, zu_rho;   // this x-step's parameters (arguments, or DevLoop)
 };
 
 // Grid barrier among the consumer threads of all CTAs (co-resident: cooperative launch).  The
@@ -175,9 +176,9 @@ GENIOS_DEV void cg_start(const CgLoopArgs& a, CglShared<VT>& sh) {
     VT rr = VT(0);
     for (int jj = tid; jj < ns; jj += RP_CTHREADS) {
         const int64_t j = j0 + jj;
-        const VT uj = u[j] * (VT)a.u_scale;
+        const VT uj = u[j] * (VT)sh.u_scale;
         u[j] = uj;
-        const VT rj = -(g[j] + (VT)a.rho * (x[j] - z[j] + uj));
+        const VT rj = -(g[j] + (VT)sh.rho * (x[j] - z[j] + uj));
         r[j] = rj;
         delta[j] = VT(0);
         sh.vsl[jj] = rj;
@@ -217,7 +218,7 @@ template <typename VT>
 GENIOS_DEV bool cg_direction(const CgLoopArgs& a, CglShared<VT>& sh) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int G = gridDim.x, sk = a.sk;
-    const VT nu = (VT)a.nu;
+    const VT nu = (VT)sh.nu;
     const VT* partW = static_cast<const VT*>(a.part);
     const int64_t j0 = sh.j0;
     const int ns = sh.ns;
@@ -277,7 +278,7 @@ GENIOS_DEV bool cg_direction(const CgLoopArgs& a, CglShared<VT>& sh) {
         done = !(rr > VT(0));
     } else {
         ++it;
-        done = rr <= (VT)a.tol * (VT)a.tol * rhs2 || it >= a.cg_max;
+        done = rr <= (VT)sh.tol * (VT)sh.tol * rhs2 || it >= a.cg_max;
     }
     const VT beta = (!start && rz_old > VT(0)) ? rz / rz_old : VT(0);
     if (!done) {
@@ -335,7 +336,7 @@ template <typename VT>
 GENIOS_DEV bool cg_step(const CgLoopArgs& a, CglShared<VT>& sh) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int G = gridDim.x;
-    const VT nu = (VT)a.nu;
+    const VT nu = (VT)sh.nu;
     VT* partW = static_cast<VT*>(a.part);
     const VT* partH = partW + (size_t)G * CGL_ST;
     const VT* partPP = partH + G;
@@ -433,7 +434,7 @@ GENIOS_DEV void zu_phase(const CgLoopArgs& a, CglShared<VT>& sh) {
     VT* z = static_cast<VT*>(a.zu_z);
     VT* u = static_cast<VT*>(a.u);
     const VT* delta = static_cast<const VT*>(a.delta);
-    const double kappa = a.zu_lam1 / a.zu_rho;
+    const double kappa = a.zu_lam1 / sh.zu_rho;
     const double alpha = a.zu_alpha;
     const int box = a.zu_box;
     const VT lo = (VT)a.zu_lo, hi = (VT)a.zu_hi;
@@ -525,7 +526,23 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nst_cap * stage_bytes);
     uint64_t* empty = full + nst_cap;
 
+    // device-side ADMM loop: nothing to do once the solve has stopped (the flag was written by an
+    // earlier kernel in the stream, so every CTA reads the same value)
+    if (a.loop != nullptr && a.loop->stop != 0) return;
     if (tid == 0) {
+        if (a.loop != nullptr) {
+            sh.rho = a.loop->rho;
+            sh.u_scale = a.loop->u_scale;
+            sh.nu = a.loop->nu;
+            sh.tol = a.loop->tol;
+            sh.zu_rho = a.loop->rho;
+        } else {
+            sh.rho = a.rho;
+            sh.u_scale = a.u_scale;
+            sh.nu = a.nu;
+            sh.tol = a.tol;
+            sh.zu_rho = a.zu_rho;
+        }
         for (int s = 0; s < nst_cap; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], RP_CWARPS);
@@ -594,7 +611,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
             }
             // every copy issued must land before the CTA's shared memory is released
             for (long long st = std::max(0LL, issued - nst_cap); st < issued; ++st)
-                mbar_wait_bounded(&full[st % nst_cap], (uint32_t)((st / nst_cap) & 1), rp.wait_limit);
+                mbar_wait_bounded(&full[st % nst_cap], (uint32_t)((st / nst_cap) & 1), drain_limit(rp.wait_limit));
         }
         return;
     }
@@ -706,8 +723,8 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
         S->pq = sh.pq;
         S->alpha = sh.alpha;
         S->beta = sh.beta;
-        S->nu = a.nu;
-        S->tol = a.tol;
+        S->nu = sh.nu;
+        S->tol = sh.tol;
         S->cg_max = a.cg_max;
         if (a.timed) {
             S->cgl_ns += (double)(gtimer() - sh.t_start);

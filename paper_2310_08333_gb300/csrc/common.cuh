@@ -166,6 +166,15 @@ GENIOS_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Floor of the limit on the waits with which a CTA drains its own asynchronous work before it
+// releases the memory that work writes: bulk copies landing in its shared memory, MMAs writing
+// its tensor memory.  About one second at the SM clock.  A caller's short device wait limit ends
+// the waits on other threads and CTAs early, never these: that work always completes (each copy
+// and MMA was issued against memory the CTA still holds), and only its completion makes the
+// release safe.
+constexpr long long DRAIN_MIN_CYCLES = 1LL << 31;
+GENIOS_DEV long long drain_limit(long long limit) { return limit > DRAIN_MIN_CYCLES ? limit : DRAIN_MIN_CYCLES; }
+
 // Bounded wait: returns false when `limit` clock cycles pass without completion.
 GENIOS_DEV bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
     if (mbar_try_wait(bar, parity)) return true;

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -194,6 +195,7 @@ extern "C" void genios_default_options(genios_options* o) {
     o->sketch_adaptive = 0;
     o->sketch_rank_max = 128;
     o->sketch_theta = 10.0;
+    o->device_loop = 1;
 }
 
 extern "C" genios_status genios_create(const genios_options* opts, int device, void* stream,
@@ -215,7 +217,8 @@ extern "C" genios_status genios_create(const genios_options* opts, int device, v
     else genios_default_options(&ctx->opt);
     const genios_options& o = ctx->opt;
     if (o.precision < 0 || o.precision > 3 || o.max_iter < 1 || o.max_cg_iter < 1 || o.rho <= 0 ||
-        o.alpha <= 0 || o.alpha >= 2 || o.sketch_rank > 128 || o.sketch_rank < -1) {
+        o.alpha <= 0 || o.alpha >= 2 || o.sketch_rank > 128 || o.sketch_rank < -1 ||
+        o.device_wait_limit_us < 0 || o.device_wait_limit_us > 3600LL * 1000000LL) {
         g_create_error = "invalid options";
         delete ctx;
         return GENIOS_EINVAL;
@@ -491,7 +494,9 @@ static long long wait_cycles(const genios_ctx* ctx) {
     return (long long)ctx->opt.device_wait_limit_us * 2100LL;
 }
 
-static cudaError_t grad_pass(genios_ctx* ctx, const void* xv, void* Wout, void* Dout) {
+// skip: when non-null, the pass returns at once if *skip != 0 (device-side loop)
+static cudaError_t grad_pass(genios_ctx* ctx, const void* xv, void* Wout, void* Dout,
+                             const int* skip = nullptr) {
     RowpassArgs a{};
     a.prec = ctx->gprec;
     a.mode = RP_GRAD;
@@ -508,7 +513,8 @@ static cudaError_t grad_pass(genios_ctx* ctx, const void* xv, void* Wout, void* 
     a.partial = ctx->Pbuf;
     a.ldp = ctx->ldp;
     a.loss_part = ctx->loss_part;
-    a.err = nullptr;
+    a.skip = skip;
+    a.err = &ctx->S->rp_fault;
     a.wait_limit = wait_cycles(ctx);
     a.dbg = ctx->dbg;
     a.smem_bytes = (long long)ctx->plan_g.smem;
@@ -532,7 +538,7 @@ static cudaError_t hv_pass(genios_ctx* ctx, const void* v, const void* d,
     a.partial = ctx->Pbuf;
     a.ldp = ctx->ldp;
     a.skip = skip;
-    a.err = nullptr;
+    a.err = &ctx->S->rp_fault;
     a.wait_limit = wait_cycles(ctx);
     a.dbg = ctx->dbg;
     a.timer = timed ? &ctx->S->hv_t0 : nullptr;
@@ -549,7 +555,7 @@ static cudaError_t hv_pass(genios_ctx* ctx, const void* v, const void* d,
 static cudaError_t cg_persistent(genios_ctx* ctx, const void* d, const void* g, const void* x, const void* z,
                                  void* u, double rho, double u_scale, double nu, double tol, int cg_max, int sk,
                                  const void* mask, bool zu = false, double zu_rho = 1.0, double zu_lam1 = 0.0,
-                                 double zu_alpha = 1.0) {
+                                 double zu_alpha = 1.0, const DevLoop* loop = nullptr) {
     CgLoopArgs a{};
     a.rp.prec = hv_prec(ctx);
     a.rp.mode = RP_HV;
@@ -594,13 +600,25 @@ static cudaError_t cg_persistent(genios_ctx* ctx, const void* d, const void* g, 
                                           cgloop_zu_offset_bytes(ctx->cgl.rp.grid));
     a.S = ctx->S;
     a.timed = 1;
+    a.loop = loop;
     ctx->launches++;
     return cgloop_launch(ctx->cgl, a, ctx->stream);
 }
 
+// Copies DevState to the host.  A row pass whose bounded wait ran out since the last read ends
+// the call with GENIOS_ETIMEOUT (its partial sums are incomplete); the word is cleared so that
+// the context stays usable.
 static genios_status read_state(genios_ctx* ctx) {
     CK(cudaMemcpyAsync(ctx->Sh, ctx->S, offsetof(DevState, w), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->Sh->rp_fault != 0) {
+        const int code = ctx->Sh->rp_fault;
+        CK(cudaMemsetAsync(&ctx->S->rp_fault, 0, sizeof(int32_t), ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        FAIL(GENIOS_ETIMEOUT, std::string("row pass over A: a bounded device wait ran out (") +
+                                  (code == DERR_TIMEOUT_EMPTY ? "copy stream waiting for a free stage"
+                                                              : "consumers waiting for a stage") + ")");
+    }
     return GENIOS_OK;
 }
 
@@ -623,6 +641,7 @@ static genios_status build_precond(genios_ctx* ctx, const void* d, double* ms) {
     ctx->launches += ((flags & NYS_REUSE_BASIS) ? 14 : 21) + (ctx->use_tc ? 2 : 0);
     ctx->omega_ready = true;
     ctx->eig_warm = false;
+    if (ok == -2) FAIL(GENIOS_ETIMEOUT, "tensor-core sketch: a bounded device wait ran out");
     if (ok == -1) FAIL(GENIOS_ENUMERIC, "Nystrom sketch is not finite (NaN/Inf in A^T D A Omega)");
     if (!ok) FAIL(GENIOS_ENUMERIC, "Nystrom core: Cholesky failed after raising the shift");
     ctx->eig_warm = ok == 1;
@@ -886,8 +905,117 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
     KktSchedule kkt(o.kkt_check_every, 1);
     const double sqn = std::sqrt((double)n);
     const double floor = cg_floor(ctx);
+    // Device-side loop: the same iteration, its decisions taken on the device (loop_decide) so
+    // that the host enqueues iterations back to back; it syncs at re-sketches (which read the
+    // state) and after chunks of 4, 8, ..., 64 iterations, and the kernels queued after a stop
+    // return at once.
+    const bool dev_loop = o.device_loop && ctx->cgl.ok && !(o.stop_rule & GENIOS_STOP_GAP) && !o.profile &&
+                          o.verbose == 0;
+    if (dev_loop) {
+        DevLoop L{};
+        L.max_iter = o.max_iter;
+        L.stop_resid = (o.stop_rule & GENIOS_STOP_RESID) ? 1 : 0;
+        L.stop_kkt = (o.stop_rule & GENIOS_STOP_KKT) ? 1 : 0;
+        L.kkt_every = std::max(1, o.kkt_check_every);
+        L.rho_every = o.rho_update_every;
+        L.rho_max = o.rho_update_max;
+        L.rho_until = o.rho_update_until;
+        L.eps_abs = o.eps_abs;
+        L.eps_rel = o.eps_rel;
+        L.eps_kkt = o.eps_kkt;
+        L.gamma = o.gamma;
+        L.cg_first = o.cg_tol_first;
+        L.cg_floor = floor;
+        L.rho_tau = o.rho_tau;
+        L.rho_mu = o.rho_mu;
+        L.sigma = o.sigma;
+        L.lam1 = lam1;
+        L.lam2 = lam2;
+        L.sqn = sqn;
+        L.status = GENIOS_OK;
+        L.kkt_last = 1;
+        L.kkt_gap = L.kkt_every;
+        L.kkt_vlast = -1.0;
+        L.rho = rho;
+        L.u_scale = 1.0;
+        L.rel_kkt = NAN;
+        CK(cudaMemcpyAsync(&ctx->S->loop, &L, sizeof(DevLoop), cudaMemcpyHostToDevice, s));
+        DevLoop* Ld = &ctx->S->loop;
+        const bool kkt_rule = (o.stop_rule & GENIOS_STOP_KKT) != 0;
+        int chunk = 4, since = 0;
+        for (int k = 1; k <= o.max_iter; ++k) {
+            // gradient pass at x^k (§3.3), then the residual and KKT-schedule decisions
+            CK(grad_pass(ctx, ctx->x, ctx->W, ctx->D, &Ld->stop));
+            CK(grad_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, ctx->loss_part, n, ctx->x,
+                           ctx->u, lam2, rho, lam1, ctx->g, ctx->S, ctx->sc, s, &Ld->stop, &Ld->rho));
+            CK(loop_decide(0, ctx->S, s));
+            ctx->launches += 2;
+            if (kkt_rule) {   // relative KKT at z, run only when due (reading R21)
+                CK(grad_pass(ctx, ctx->z, nullptr, nullptr, &Ld->skip_kkt));
+                CK(kkt_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, n, ctx->z, lam2, lam1,
+                              ctx->S, ctx->sc, s, o.box, o.box_lo, o.box_hi, &Ld->skip_kkt));
+                ctx->launches++;
+            }
+            CK(loop_decide(1, ctx->S, s));   // KKT stop, penalty update, CG tolerance
+            ctx->launches++;
+            // (re-)sketch (§2.2, §3.3) with D at x^k: the host reads the decisions first
+            if (use_pc) {
+                const bool first = !ctx->have_precond;
+                const bool resk = !quadratic && o.resketch_every > 0 && k > 1 && (k - 1) % o.resketch_every == 0;
+                if (first || resk) {
+                    genios_status st = read_state(ctx);
+                    if (st != GENIOS_OK) return st;
+                    if (ctx->Sh->loop.stop) break;
+                    if (first && o.sketch_adaptive && !ctx->sketch_adapted && ctx->sk_alloc > ctx->sk)
+                        st = adapt_sketch(ctx, dvec, ctx->Sh->loop.nu, &inf.t_sketch_ms);
+                    else
+                        st = build_precond(ctx, dvec, &inf.t_sketch_ms);
+                    if (st != GENIOS_OK) return st;
+                    inf.sketches++;
+                    since = 0;
+                }
+            }
+            // x-step (§2.1) and z/u update (Eq. (5)) in one persistent launch, parameters from Ld
+            const int sk_now = use_pc && ctx->have_precond ? ctx->sk : 0;
+            CK(cg_persistent(ctx, dvec, ctx->g, ctx->x, ctx->z, ctx->u, rho, 1.0, rho + lam2 + o.sigma, floor,
+                             o.max_cg_iter, sk_now, nullptr, /*zu=*/true, rho, lam1, o.alpha, Ld));
+            if (++since >= chunk && k < o.max_iter) {
+                genios_status st = read_state(ctx);
+                if (st != GENIOS_OK) return st;
+                if (ctx->Sh->loop.stop) break;
+                since = 0;
+                chunk = std::min(2 * chunk, 64);
+            }
+        }
+        genios_status st = read_state(ctx);
+        if (st != GENIOS_OK) return st;
+        const DevLoop& Lh = ctx->Sh->loop;
+        if (Lh.stop && Lh.status == GENIOS_ETIMEOUT)
+            FAIL(GENIOS_ETIMEOUT, "persistent CG: a bounded device wait ran out");
+        if (Lh.stop) {
+            iters = Lh.iters;
+            converged = Lh.status == GENIOS_OK;
+            if (Lh.status == GENIOS_ENUMERIC) {
+                inf.status = GENIOS_ENUMERIC;
+                ctx->err = "non-finite gradient or loss";
+            }
+            inf.cg_iters_total = (int)Lh.cg_iters;
+        } else {   // max_iter iterations, the last x-step included
+            iters = o.max_iter;
+            converged = false;
+            inf.cg_iters_total = (int)(Lh.cg_iters + ctx->Sh->cg_it);
+        }
+        inf.hv_launches = inf.cg_iters_total;
+        inf.grad_launches = Lh.grad_passes;
+        inf.r_p = Lh.r_p;
+        inf.r_d = Lh.r_d;
+        inf.rel_kkt = Lh.rel_kkt;
+        inf.objective = Lh.objective;
+        rho = Lh.rho;
+        n_rho = Lh.n_rho;
+    }
 
-    for (int k = 1; k <= o.max_iter; ++k) {
+    for (int k = 1; k <= o.max_iter && !dev_loop; ++k) {
         iters = k;
         // ---- gradient pass at x^k (§3.3): grad f, D = loss'', loss sum
         if (o.profile) {
@@ -943,16 +1071,34 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
             bool stop = false;
             if ((o.stop_rule & GENIOS_STOP_RESID) && resid_ok) stop = true;
             if (!stop && (o.stop_rule & GENIOS_STOP_GAP)) {
-                CK(gap_pieces(ctx->dbl, ctx->loss, ctx->m, ctx->W, ctx->b, lam2, lam1, ctx->S, ctx->sc, s));
-                ctx->launches++;
-                st = read_state(ctx);
-                if (st != GENIOS_OK) return st;
-                const double P = H.loss_sum + lam1 * H.gx1 + 0.5 * lam2 * H.gx2;
-                double Dv = -H.conj_sum - H.btnu;
-                if (lam2 > 0) Dv -= H.excess2 / (2.0 * lam2);
-                const double den = std::min(P, std::fabs(Dv));
-                inf.rel_gap = den > 0 ? (P - Dv) / den : INFINITY;
-                if (inf.rel_gap <= o.eps_gap) stop = true;
+                // App. A, Eq. (24) at the gradient pass's iterate x^k; when it passes, once more at
+                // z^k, the vector returned (one extra pass over A: loss'(A z - b), ||A^T loss'||_inf
+                // and the loss sum at z; grad_finish's gradient output goes to scratch so that
+                // grad f(x^k) for this iteration's x-step is kept), and the solve stops only if
+                // the gap at z meets the tolerance too.  rel_gap reports the last one evaluated.
+                for (int at_z = 0; at_z < 2 && !stop; ++at_z) {
+                    if (at_z) {
+                        CK(grad_pass(ctx, ctx->z, ctx->W, nullptr));
+                        CK(grad_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, ctx->loss_part, n, ctx->z,
+                                       ctx->u, lam2, rho, lam1, ctx->q, ctx->S, ctx->sc, s));
+                        ctx->launches++;
+                        inf.grad_launches++;
+                    }
+                    CK(gap_pieces(ctx->dbl, ctx->loss, ctx->m, ctx->W, ctx->b, lam2, lam1, ctx->S, ctx->sc, s));
+                    ctx->launches++;
+                    st = read_state(ctx);
+                    if (st != GENIOS_OK) return st;
+                    const double P = H.loss_sum + lam1 * H.gx1 + 0.5 * lam2 * H.gx2;
+                    double Dv = -H.conj_sum - H.btnu;
+                    if (lam2 > 0) Dv -= H.excess2 / (2.0 * lam2);
+                    const double den = std::min(P, std::fabs(Dv));
+                    inf.rel_gap = den > 0 ? (P - Dv) / den : INFINITY;
+                    if (inf.rel_gap > o.eps_gap) break;
+                    if (at_z) {
+                        stop = true;
+                        inf.objective = P;   // F(z), the objective of the vector returned
+                    }
+                }
             }
             // relative KKT at z: one extra pass over A, on the schedule of KktSchedule
             if (!stop && (o.stop_rule & GENIOS_STOP_KKT) && kkt.due(k, resid_ok)) {
@@ -1549,7 +1695,55 @@ genios_status op_err(cudaError_t e) {
     g_create_error = cudaGetErrorString(e);
     return GENIOS_ECUDA;
 }
+
+// Where the op-level row passes (genios_op_hv, genios_op_hv_noalloc, genios_op_gradient) record a
+// bounded wait that ran out: a __device__ variable exists once on every device that loads the
+// library.  Its address is looked up once per device and cached.
+__device__ int g_op_fault;
+std::mutex g_op_fault_mu;
+constexpr int kOpFaultDevices = 64;
+void* g_op_fault_addr[kOpFaultDevices] = {};
 }  // namespace
+
+namespace genios {
+cudaError_t op_fault_address(int** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kOpFaultDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_op_fault_mu);
+    if (g_op_fault_addr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_op_fault);
+        if (e != cudaSuccess) return e;
+        g_op_fault_addr[dev] = p;
+    }
+    *out = static_cast<int*>(g_op_fault_addr[dev]);
+    return cudaSuccess;
+}
+}  // namespace genios
+
+extern "C" genios_status genios_op_status(void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int* w = nullptr;
+    cudaError_t e = op_fault_address(&w);
+    int code = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&code, w, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && code != 0) {
+        e = cudaMemsetAsync(w, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) return op_err(e);
+    if (code != 0) {
+        g_create_error = std::string("op-level row pass: a bounded device wait ran out (") +
+                         (code == DERR_TIMEOUT_EMPTY ? "copy stream waiting for a free stage"
+                                                     : "consumers waiting for a stage") +
+                         "); the outputs of that call are incomplete";
+        return GENIOS_ETIMEOUT;
+    }
+    return GENIOS_OK;
+}
 
 extern "C" size_t genios_op_workspace_bytes(int precision, int64_t m, int64_t n) {
     if (!prec_valid(precision) || m < 1 || n < 1) return 0;
@@ -1583,7 +1777,8 @@ extern "C" genios_status genios_op_hv(int precision, int64_t m, int64_t n, const
     a.partial = w.P;
     a.ldp = lda;
     a.wait_limit = 2000000LL * 2100LL;
-    cudaError_t e = rowpass_launch(a, plan, s);
+    cudaError_t e = op_fault_address(&a.err);
+    if (e == cudaSuccess) e = rowpass_launch(a, plan, s);
     if (e == cudaSuccess) e = hv_finish(precision == 0, w.P, plan.grid, lda, n, nu, v, y, s);
     return op_err(e);
 }
@@ -1617,7 +1812,8 @@ extern "C" genios_status genios_op_gradient(int loss, int precision, int64_t m, 
     a.ldp = lda;
     a.loss_part = w.loss_part;
     a.wait_limit = 2000000LL * 2100LL;
-    cudaError_t e = rowpass_launch(a, plan, s);
+    cudaError_t e = op_fault_address(&a.err);
+    if (e == cudaSuccess) e = rowpass_launch(a, plan, s);
     if (e == cudaSuccess)
         e = grad_finish(precision == 0, w.P, plan.grid, lda, w.loss_part, n, x, x, lambda2, 0.0, 0.0,
                         grad_out, w.S, w.sc, s);
@@ -1684,6 +1880,10 @@ extern "C" genios_status genios_op_nystrom(int precision, int64_t m, int64_t n, 
     cudaError_t e = nystrom_build(P, m, n, s, A, lda, row_scale, d, Omega, U_out, lam_out, eta_out, w,
                                   &ok, flags, tp, st);
     if (e != cudaSuccess) return op_err(e);
+    if (ok == -2) {
+        g_create_error = "tensor-core sketch: a bounded device wait ran out";
+        return GENIOS_ETIMEOUT;
+    }
     return ok >= 1 ? GENIOS_OK : GENIOS_ENUMERIC;
 }
 

@@ -14,6 +14,13 @@
 // any stream capture.  All calls share the array: two calls whose kernels overlap on the GPU
 // (different streams, or different host threads on one device without ordering) race on it.
 // Nothing in the array needs to start at zero: every CTA overwrites its whole partial row.
+//
+// The cached addresses belong to the device's current (primary) context.  A device reset after
+// the first call (cudaDeviceReset) unloads the library's device image, and the cache then holds
+// stale addresses: a process that resets a device must not call this entry point on it again.
+//
+// A bounded wait of the row pass that runs out (about 2 s without progress) is recorded in the
+// device's op-level fault word, like genios_op_hv's: genios_op_status(stream) reports it.
 #include "common.cuh"
 #include "internal.h"
 #include "genios.h"
@@ -88,6 +95,11 @@ extern "C" genios_status genios_op_hv_noalloc(int precision, int64_t m, int64_t 
     a.wait_limit = 2000000LL * 2100LL;
     a.smem_bytes = (long long)plan.smem;
     a.partial_len = (long long)(kScratchBytes / vt);
+    e = op_fault_address(&a.err);   // a bounded wait that runs out is reported by genios_op_status
+    if (e != cudaSuccess) {
+        set_last_error(std::string("genios_op_hv_noalloc: fault word: ") + cudaGetErrorString(e));
+        return GENIOS_ECUDA;
+    }
     e = rowpass_launch(a, plan, s);
     if (e == cudaSuccess) e = hv_finish(precision == 0, scratch, plan.grid, lda, n, nu, v, y, s);
     if (e != cudaSuccess) {

@@ -14,6 +14,31 @@ namespace genios {
 
 // Scalars that kernels produce and consume on the device.  One instance per context,
 // in device memory; the host reads it with an async copy when it needs a decision.
+// State of the ADMM loop when its per-iteration decisions run on the device (loop_decide): the
+// host enqueues iterations without reading back and syncs only at re-sketches and chunk ends.
+// The configuration fields are written by the host at solve start.
+struct DevLoop {
+    // configuration
+    int32_t max_iter, stop_resid, stop_kkt, kkt_every;
+    int32_t rho_every, rho_max, rho_until, pad0;
+    double eps_abs, eps_rel, eps_kkt, gamma, cg_first, cg_floor;
+    double rho_tau, rho_mu, sigma, lam1, lam2, sqn;
+    // state
+    int32_t k;           // iteration whose decisions were taken last (0 before the first)
+    int32_t stop;        // 1 once the solve stopped: the kernels that follow return at once
+    int32_t skip_kkt;    // 1 unless iteration k evaluates the relative KKT residual at z
+    int32_t status;      // genios_status once stopped (GENIOS_OK: converged)
+    int32_t iters;       // iterations of the solve once stopped
+    int32_t n_rho;       // penalty changes
+    int32_t kkt_last, kkt_gap, resid_seen, pad1;
+    double kkt_vlast;
+    double rho, u_scale, nu, tol;   // the x-step of iteration k (§2.1, §2.5)
+    double last_rp, last_rd;
+    // results
+    double r_p, r_d, rel_kkt, objective;
+    int64_t cg_iters, grad_passes;
+};
+
 struct DevState {
     // preconditioned CG (§2.1)
     double rz;        // r^T P^{-1} r of the current iterate
@@ -29,6 +54,7 @@ struct DevState {
     int32_t cg_max;
     int32_t cg_first; // 1 before the first preconditioner application of a solve
     int32_t cg_fault; // non-zero if a bounded device wait of the CG vector kernel ran out
+    int32_t rp_fault; // non-zero (DERR_*) if a bounded wait of a row pass (gradient, Hv) ran out
     // gradient pass at x (§3.3) and residual norms (Eqs. (11)-(12))
     double loss_sum;  // sum_i loss(a_i^T x - b_i)
     double g2;        // ||grad f(x)||^2
@@ -57,6 +83,7 @@ struct DevState {
     double nys_dots[4];             // adaptive sketch: [v^T E v, ||E v||^2, v^T v] of a power step
     double cgl_phase_ns[6];         // CTA 0's time by phase: Hv, barrier, update, barrier,
                                     // direction, barrier
+    DevLoop loop;                   // device-side ADMM loop (device_loop = 1)
     double w[256];    // U^T r (Nystrom preconditioner), s <= 256 (op-level preconditioner)
     double cgc[128];  // preconditioner coefficients c_i w_i for the next direction
 };
@@ -98,6 +125,9 @@ struct RowpassPlan {
 };
 
 int device_sm_count();
+// Device address (current device) of the word where op-level row passes record a bounded wait
+// that ran out; genios_op_status reads and clears it.  Looked up once per device, allocates nothing.
+cudaError_t op_fault_address(int** out);
 // Message returned by genios_last_error(NULL) on this thread.
 void set_last_error(const std::string& msg);
 // smem_budget: bytes of dynamic shared memory for the stage ring (0: the rowpass default)
@@ -139,6 +169,8 @@ struct CgLoopArgs {
     double* zu_part;           // grid x 6 float64 partials of the z/u norms
     DevState* S;               // cg_fault must be 0 at launch; results: cg_it, rr, rz, ...
     int timed;                 // accumulate H-phase and launch device times in S
+    const DevLoop* loop;       // non-null: rho, u_scale, nu, tol (and zu_rho = rho) are read from
+                               // it at launch, and the kernel returns at once once it has stopped
 };
 // ok = false when the shape does not fit (n > 1024 per SM, s > 128, the split-BF16 stream, or a
 // ring that does not fit one CTA per SM); the caller then uses the per-kernel CG path.
@@ -195,14 +227,23 @@ cudaError_t rhs_init(bool dbl, int64_t n, const void* g, const void* x, const vo
                      void* delta, void* p, void* zc, const void* U, int sk, DevState* S,
                      Scratch sc, cudaStream_t s);
 // gradient finish: g = sum_b P[b] + mu x; norms for r_d, objective, gap; loss sum
+// skip: when non-null and *skip != 0 the kernel returns at once; rho_dev: when non-null the
+// penalty is read from it instead of `rho` (the device-side loop)
 cudaError_t grad_finish(bool dbl, const void* P, int G, int64_t ldp, const double* loss_part,
                         int64_t n, const void* x, const void* u, double mu, double rho,
-                        double lam1, void* g, DevState* S, Scratch sc, cudaStream_t s);
+                        double lam1, void* g, DevState* S, Scratch sc, cudaStream_t s,
+                        const int* skip = nullptr, const double* rho_dev = nullptr);
 // KKT finish at z: gz = sum_b P[b] + mu z; subgradient distance norms (box = 1: the distance of
 // 0 from gz + N(z), N the normal cone of [lo, hi]^n)
 cudaError_t kkt_finish(bool dbl, const void* P, int G, int64_t ldp, int64_t n, const void* z,
                        double mu, double lam1, DevState* S, Scratch sc, cudaStream_t s, int box = 0,
-                       double lo = 0.0, double hi = 0.0);
+                       double lo = 0.0, double hi = 0.0, const int* skip = nullptr);
+// Device-side ADMM loop (DevLoop): the decisions of one iteration, one thread.
+//   phase 0 (after the gradient pass at x^k): count the previous x-step's CG iterations, faults,
+//     non-finite values, the residual test of §2.3 and whether a KKT check is due (skip_kkt);
+//   phase 1 (after the KKT pass, which returns at once when skip_kkt): the KKT stop test, the
+//     penalty update of §2.5 and the CG tolerance of §2.1 for the x-step.
+cudaError_t loop_decide(int phase, DevState* S, cudaStream_t s);
 // duality gap pieces from W = loss'(Ax - b) (m-vector)
 cudaError_t gap_pieces(bool dbl, int loss, int64_t m, const void* W, const void* b, double mu,
                        double lam1, DevState* S, Scratch sc, cudaStream_t s);
@@ -299,6 +340,9 @@ cudaError_t tc_sketch(const TcPlan& p, TcWork w, const float* d, float* Y, long 
                       cudaStream_t s);   // = GENIOS_NYS_REUSE_BASIS, GENIOS_NYS_WARM
 // tc: when non-NULL (value type float), the sketch runs on the tensor cores with the packed
 // operands of tc (A already packed); otherwise on the CUDA cores in `prec`.
+// chol_ok on return: 1 done; 2 done without eigenvectors (all-zero sketch); 0 the Cholesky
+// failed after raising the shift; -1 non-finite sketch; -2 a bounded wait of the tensor-core
+// sketch ran out (nothing computed after it).
 cudaError_t nystrom_build(int prec, int64_t m, int64_t n, int sk, const void* A, int64_t lda,
                           const float* row_scale, const void* d, const void* Om, void* U,
                           double* lam, double* eta_out, NysWork w, int* chol_ok, int flags,

@@ -869,9 +869,9 @@ cudaError_t nystrom_build(int prec, int64_t m, int64_t n, int sk, const void* A,
         if (e == cudaSuccess) e = cudaMemcpyAsync(&err, tc->work.err, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
-        if (err != 0) {
-            std::fprintf(stderr, "[genios] tensor-core sketch: a bounded wait ran out (code %d)\n", err);
-            return cudaErrorLaunchTimeout;
+        if (err != 0) {   // a bounded wait of the tensor-core products ran out: Y is incomplete
+            *chol_ok = -2;
+            return cudaSuccess;
         }
         return core<float>(n, sk, Of, Yf, w, static_cast<float*>(U), lam, eta_out, chol_ok, warm, s);
     }

@@ -72,6 +72,7 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
             const char* Ab = static_cast<const char*>(a.A);
             const char* Al = static_cast<const char*>(a.A_lo);
             const uint64_t pol = l2_evict_first_policy();
+            int issued = 0;
             for (int st = 0; st < nstage_work; ++st) {
                 const int s = st % nst_cap;
                 const int use = st / nst_cap;
@@ -90,7 +91,12 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
                 mbar_arrive_expect_tx(&full[s], bytes * SPLIT);
                 bulk_g2s_hint(dst, Ab + off, bytes, &full[s], pol);
                 if (HILO) bulk_g2s_hint(dst + (size_t)rps * row_bytes, Al + off, bytes, &full[s], pol);
+                issued = st + 1;
             }
+            // Every copy issued lands before the CTA's shared memory is released: after a wait
+            // ran out the consumers may have left without waiting for the last stages.
+            for (int st = issued > nst_cap ? issued - nst_cap : 0; st < issued; ++st)
+                mbar_wait_bounded(&full[st % nst_cap], (uint32_t)((st / nst_cap) & 1), drain_limit(a.wait_limit));
         }
         return;
     }

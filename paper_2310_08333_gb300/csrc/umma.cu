@@ -170,11 +170,12 @@ __global__ void __launch_bounds__(UM_THREADS, 1) umma_gemm_kernel(UmmaArgs a) {
                 tc_commit(&empty[s]);   // frees the stage when these MMAs have read it
             }
             tc_commit(&accum);          // all MMAs of this CTA
-            if (!mbar_wait_bounded(&accum, 0, a.wait_limit)) set_err(a.err, DERR_TIMEOUT_FULL);
+            // every MMA issued has written TMEM before it is released (drain limit: see common.cuh)
+            if (!mbar_wait_bounded(&accum, 0, drain_limit(a.wait_limit))) set_err(a.err, DERR_TIMEOUT_FULL);
             // the last release of every stage has landed before the CTA can exit
             for (int s = 0; s < a.stages && s < c; ++s) {
                 const int last = s + ((c - 1 - s) / a.stages) * a.stages;
-                if (!mbar_wait_bounded(&empty[s], (uint32_t)((last / a.stages) & 1), a.wait_limit))
+                if (!mbar_wait_bounded(&empty[s], (uint32_t)((last / a.stages) & 1), drain_limit(a.wait_limit)))
                     set_err(a.err, DERR_TIMEOUT_EMPTY);
             }
         }
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) umma_gemm_kernel(UmmaArgs a) {
         const int f = issued;
         for (int s = 0; s < a.stages && s < f; ++s) {
             const int last = s + ((f - 1 - s) / a.stages) * a.stages;
-            if (!mbar_wait_bounded(&full[s], (uint32_t)((last / a.stages) & 1), a.wait_limit))
+            if (!mbar_wait_bounded(&full[s], (uint32_t)((last / a.stages) & 1), drain_limit(a.wait_limit)))
                 set_err(a.err, DERR_TIMEOUT_FULL);
         }
     }

@@ -54,12 +54,10 @@ def assert_parity(P, z, ref_z, lam, mu, loss, tol_z=1e-5, tol_f=1e-7):
     Fs = checks.objective(P.A, P.b, ref_z, loss, lam, mu)
     assert err <= tol_z, f"rel solution error {err:.3e}"
     assert abs(F - Fs) <= tol_f * abs(Fs), f"rel objective error {abs(F - Fs) / abs(Fs):.3e}"
+    # identical support apart from entries below 1e-8 in magnitude
     big = lambda v: set(np.flatnonzero(np.abs(v) > 1e-8))  # noqa: E731
-    sz, sr = big(z), big(ref_z)
-    diff = sz ^ sr
-    # entries that differ in support must be tiny on the side that has them
-    for j in diff:
-        assert abs(z[j]) < 1e-6 and abs(ref_z[j]) < 1e-6, (j, z[j], ref_z[j])
+    diff = sorted(big(z) ^ big(ref_z))
+    assert not diff, [(j, z[j], ref_z[j]) for j in diff[:5]]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -118,39 +116,27 @@ def test_config2_lasso_fp32_parity(G):
     assert_parity(P, z, ref["z"], lam, 0.0, "squared")
 
 
-def derived_tol(A, b, ref_z, loss, lam, mu, kkt):
-    """Relative solution error implied by a relative KKT residual `kkt` at a point with the
-    same support: ||z - z*|| <= ||d|| / lambda_min(H_SS), ||d|| = kkt * max(||grad f||, lam)."""
-    from oracle import losses
-    S = checks.support(ref_z)
-    D = losses.get(loss).d2(A @ ref_z - b)
-    H = A[:, S].T @ (D[:, None] * A[:, S]) + mu * np.eye(S.size)
-    lmin = np.linalg.eigvalsh(H)[0]
-    g = checks.grad_f(A, b, ref_z, loss, mu)
-    return 2.0 * kkt * max(np.linalg.norm(g), lam) / lmin / np.linalg.norm(ref_z)
-
-
 @pytest.mark.parametrize("prec", [0, 1])
 def test_config3_logistic_reduced_parity(G, prec):
-    """FP64: the 1e-5 bar.  FP32: float32 rounding of a_i^T x floors the relative KKT near
-    2e-7 on this instance and lambda_min(H_SS) = 0.38, so the bar is the derived bound."""
+    """The parity bar in both modes.  FP32 stops at a 2e-6 relative KKT residual: float32
+    evaluation of the gradient keeps the residual of this instance fluctuating near 2e-6 to
+    7e-6 once the iterate is accurate (FP32 solves asked for 1e-6 run to max_iter with the
+    solution error below 1e-6), and a stop at 5e-6 leaves a 1.7e-5 solution error, above the
+    bar; at 2e-6 the error is about 3e-6."""
     P = problems.logistic_lowrank(1000, 400, nnz=20, sketch_rank=40)
     A, b = rounded(P, prec)
     lam = P.lam_frac * checks.lambda_max(A, b, "logistic")
     ref = oadmm.solve(A, b, "logistic", lam, rho=30.0, tol=1e-13, check_every=5)
     assert ref["converged"]
-    # float32 evaluation of a_i^T x floors the reachable relative KKT near 2e-6 here
-    z, info, _ = gpu_solve(G, P, prec, lam, rho=30.0, eps_kkt=1e-10 if prec == 0 else 5e-6)
+    z, info, _ = gpu_solve(G, P, prec, lam, rho=30.0, eps_kkt=1e-10 if prec == 0 else 2e-6)
     assert info["status"] == 0, info
-    if prec == 0:
-        assert_parity(P, z, ref["z"], lam, 0.0, "logistic")
-    else:
-        tol = max(1e-5, derived_tol(A, b, ref["z"], "logistic", lam, 0.0, info["rel_kkt"]))
-        print(f"FP32 logistic: rel KKT {info['rel_kkt']:.2e}, derived tol {tol:.2e}")
-        assert_parity(P, z, ref["z"], lam, 0.0, "logistic", tol_z=tol, tol_f=max(1e-7, tol ** 2))
+    print(f"prec {prec}: rel KKT {info['rel_kkt']:.2e}, rel err {np.linalg.norm(z - ref['z']) / np.linalg.norm(ref['z']):.2e}")
+    assert_parity(P, z, ref["z"], lam, 0.0, "logistic")
 
 
 def test_elastic_net_logistic_parity(G):
+    """FP32 elastic-net logistic at the parity bar (stop at a 5e-6 relative KKT residual: a
+    solution error of about 2e-6 on this instance)."""
     P = problems.logistic_lowrank(800, 300, nnz=15, mu=1e-3, seed=41, sketch_rank=30)
     A, b = rounded(P, 1)
     lam = 0.01 * checks.lambda_max(A, b, "logistic")
@@ -158,33 +144,25 @@ def test_elastic_net_logistic_parity(G):
     assert ref["converged"]
     z, info, _ = gpu_solve(G, P, 1, lam, 1e-3, rho=20.0, eps_kkt=5e-6)
     assert info["status"] == 0, info
-    tol = max(1e-5, derived_tol(A, b, ref["z"], "logistic", lam, 1e-3, info["rel_kkt"]))
-    print(f"FP32 elastic-net logistic: rel KKT {info['rel_kkt']:.2e}, derived tol {tol:.2e}")
-    assert_parity(P, z, ref["z"], lam, 1e-3, "logistic", tol_z=tol, tol_f=max(1e-7, tol ** 2))
+    print(f"FP32 elastic-net logistic: rel KKT {info['rel_kkt']:.2e}")
+    assert_parity(P, z, ref["z"], lam, 1e-3, "logistic")
 
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_huber_parity(G, prec):
-    """The Huber fitting problem of §4.4 (300 x 600, 5 % outliers of +-10, rho = 10): FP64 to
-    the 1e-5 bar; FP32 to the relative KKT residual (checked in float64 by the oracle at the
-    GPU's z) and the objective its stopping tolerance implies."""
+    """The Huber fitting problem of §4.4 (300 x 600, 5 % outliers of +-10, rho = 10) at the
+    parity bar in both modes; FP32 stops at a 1e-6 relative KKT residual (a solution error of
+    about 7e-6 on this instance; 1e-5 leaves 6e-5)."""
     P = problems.huber_outliers(n=600, seed=problems.seed_for(6, 1), sketch_rank=30)
     A, b = rounded(P, prec)
     lam = P.lam_frac * np.max(np.abs(A.T @ b))
     ref = oadmm.solve(A, b, "huber", lam, rho=P.rho, tol=1e-13, check_every=5)
     assert ref["converged"]
-    z, info, _ = gpu_solve(G, P, prec, lam, eps_kkt=1e-10 if prec == 0 else 1e-5)
+    z, info, _ = gpu_solve(G, P, prec, lam, eps_kkt=1e-10 if prec == 0 else 1e-6)
     assert info["status"] == 0, info
     assert np.any(np.abs(A @ ref["z"] - b) > 1.0)   # outliers sit on the linear pieces
-    if prec == 0:
-        assert_parity(P, z, ref["z"], lam, 0.0, "huber")
-    else:
-        kkt = checks.rel_kkt(A, b, z, "huber", lam)
-        F = checks.objective(A, b, z, "huber", lam)
-        Fs = checks.objective(A, b, ref["z"], "huber", lam)
-        print(f"FP32 Huber: rel KKT {kkt:.2e} (GPU {info['rel_kkt']:.2e}), objective {abs(F - Fs) / Fs:.2e}")
-        assert kkt <= 3e-5
-        assert abs(F - Fs) <= 1e-5 * abs(Fs)
+    assert_parity(P, z, ref["z"], lam, 0.0, "huber")
+    assert checks.rel_kkt(A, b, z, "huber", lam) <= (1e-10 if prec == 0 else 1e-6) * 1.05
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -269,17 +247,38 @@ def test_lambda_above_lambda_max_gives_exact_zero(G, loss):
     assert info["nnz"] == 0
 
 
-def test_stop_rules_residual_and_gap(G):
-    P = problems.lasso_iid(300, 800, nnz=10, seed=10)
-    A, b = rounded(P, 1)
-    lam = 0.1 * checks.lambda_max(A, b, "squared")
-    for rule in (G.STOP_RESID, G.STOP_GAP):
-        z, info, _ = gpu_solve(G, P, 1, lam, stop_rule=rule, eps_gap=1e-5)
-        assert info["status"] == 0
-        gap = checks.duality_gap(A, b, z, "squared", lam)["rel_gap_min"]
-        if rule == G.STOP_GAP:
-            assert info["rel_gap"] <= 1e-5
-            assert gap <= 1e-3          # at z (the GPU evaluates the gap at x)
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("loss", ["squared", "logistic"])
+def test_stop_rules_residual_and_gap(G, prec, loss):
+    """§2.3 residual rule, and the App. A duality gap rule, which the GPU certifies at the z it
+    returns: the oracle's relative gap (min denominator, reading R4) at that z is the gap the
+    GPU reports, to float32 rounding of the loss sums, and meets the tolerance."""
+    P = (problems.lasso_iid(300, 800, nnz=10, seed=10) if loss == "squared"
+         else problems.logistic_lowrank(1000, 400, nnz=20, sketch_rank=40, seed=problems.seed_for(3, 21)))
+    A, b = rounded(P, prec)
+    lam = (0.1 if loss == "squared" else P.lam_frac) * checks.lambda_max(A, b, loss)
+    eps_gap = 1e-5
+    rho = P.rho if loss == "squared" else 30.0
+    z, info, _ = gpu_solve(G, P, prec, lam, stop_rule=G.STOP_RESID, rho=rho)
+    assert info["status"] == 0
+    assert info["r_p"] > 0 and info["r_d"] > 0
+    z, info, _ = gpu_solve(G, P, prec, lam, stop_rule=G.STOP_GAP, eps_gap=eps_gap, rho=rho)
+    assert info["status"] == 0, info
+    gap = checks.duality_gap(A, b, z, loss, lam)["rel_gap_min"]
+    print(f"{loss} prec {prec}: GPU gap {info['rel_gap']:.3e}, oracle gap at z {gap:.3e}")
+    assert info["rel_gap"] <= eps_gap
+    # The GPU's gap and the oracle's at the same z differ by the rounding of t = A z - b in the
+    # value type: to first order each of the primal and dual sums moves by at most
+    # sum_i |l'(t_i)| |dt_i| with |dt_i| <= eps (|a_i|^T |z| + |b_i|), relative to min(P, |D|).
+    from oracle import losses
+    eps = np.finfo(np.float64 if prec == 0 else np.float32).eps
+    t = A @ z - b
+    dt = eps * (np.abs(A) @ np.abs(z) + np.abs(b))
+    dg = checks.duality_gap(A, b, z, loss, lam)
+    slack = 4.0 * np.sum(np.abs(losses.get(loss).d1(t)) * dt) / min(dg["primal"], abs(dg["dual"]))
+    print(f"  rounding slack {slack:.2e}")
+    assert abs(info["rel_gap"] - gap) <= 0.05 * gap + slack, (info["rel_gap"], gap, slack)
+    assert gap <= eps_gap + slack, (gap, slack)
 
 
 def test_warm_start_reuses_state(G):
@@ -326,8 +325,11 @@ def test_mixed_precision_reaches_kkt_and_reports_error(G, prec):
 
 
 def test_config3_full_size_kkt_property(G):
-    """Full 20000 x 8000 logistic workload: the oracle cannot run its exact solve here, so the
-    float64 optimality conditions are checked at the GPU's z instead (they hold at any size)."""
+    """Full 20000 x 8000 logistic workload in the benchmark's configuration (FP32, rho = 30,
+    rank 100, stop at a 1e-4 relative KKT residual): the oracle cannot run its exact solve here
+    in seconds, so it certifies the GPU's z by the float64 optimality conditions, which hold at
+    any size: its relative KKT residual at z meets the tolerance the GPU stopped on (to float32
+    rounding of the GPU's own evaluation) and equals the value the GPU reported."""
     P = problems.logistic_lowrank()
     A32 = P.A.astype(np.float32)
     z, info, lmax = gpu_solve(G, P, 1, P.lam_frac * checks.lambda_max(A32.astype(np.float64), P.b, "logistic"),
@@ -335,11 +337,109 @@ def test_config3_full_size_kkt_property(G):
     A = A32.astype(np.float64)
     lam = info["lambda1"]
     kkt = checks.rel_kkt(A, P.b, z, "logistic", lam)
+    print(f"full size: GPU rel KKT {info['rel_kkt']:.6e}, oracle {kkt:.6e}, iters {info['iters']}")
     assert info["status"] == 0, info
-    assert kkt <= 2e-4, kkt
+    assert info["rel_kkt"] <= 1e-4
+    assert kkt <= 1.05e-4, kkt
+    assert abs(info["rel_kkt"] - kkt) <= 0.05 * kkt, (info["rel_kkt"], kkt)
     S = checks.support(z)
     g = checks.grad_f(A, P.b, z, "logistic")
     assert np.max(np.abs(np.delete(g, S))) <= lam * (1 + 1e-3)
     # the rank-100 Nystrom preconditioner keeps the CG solves short (about 7 iterations per
     # x-update here); a broken preconditioner runs into the 50-iteration cap instead
     assert info["cg_iters_total"] <= 12 * info["iters"], (info["cg_iters_total"], info["iters"])
+
+
+def test_b_is_read_with_the_dtype_of_A(G):
+    """float32 A with a float64 (NumPy or torch) b: the binding converts b to A's dtype before
+    the call, so the solve equals the one with a float32 b; a batch of mixed dtypes is refused."""
+    P = problems.lasso_iid(200, 500, nnz=10, seed=13)
+    A32 = torch.from_numpy(P.A.astype(np.float32)).cuda()
+    lam = 0.1 * checks.lambda_max(*rounded(P, 1), "squared")
+    outs = []
+    for b in (P.b.astype(np.float32), P.b, torch.from_numpy(P.b).cuda(), torch.from_numpy(P.b)):
+        with G.Solver(precision=1, stop_rule=G.STOP_KKT, eps_kkt=1e-6, sketch_rank=20) as s:
+            s.set_data(A32, b, "squared")
+            z, info = s.solve(lam)
+        assert info["status"] == 0
+        outs.append(z)
+    for z in outs[1:]:
+        np.testing.assert_array_equal(z, outs[0])
+    with G.Solver(precision=1) as s:
+        with pytest.raises(ValueError):
+            s.set_batch([A32, A32.double()], [P.b, P.b], "squared")
+
+
+def test_device_wait_timeout_reports_etimeout_and_context_recovers(G):
+    """A bounded device wait that runs out returns GENIOS_ETIMEOUT (the status of the C ABI) and
+    leaves the device usable.  With device_wait_limit_us = 0 every wait for another thread or
+    for the copy engine gives up at its first unsuccessful poll.  Which wait that is depends on
+    timing: the gradient pass's ring waits usually complete within the hardware's own suspension
+    in mbarrier.try_wait, while the first tensor-core sketch (m = 20000, rank 20) waits for MMA
+    chains and gives up.  The CTA that gave up still drains its own copies and MMAs (bounded by
+    about 1 s) and frees its tensor memory before it exits; the host reads the fault word and
+    fails the solve with a message.  A context with the default bound then solves the same data
+    to the oracle's solution."""
+    P = problems.lasso_iid(20000, 2000, nnz=40, seed=problems.seed_for(1, 31))
+    A, b = rounded(P, 1)
+    lam = 0.1 * checks.lambda_max(A, b, "squared")
+    Ad = torch.from_numpy(P.A.astype(np.float32)).cuda()
+    bd = torch.from_numpy(P.b.astype(np.float32)).cuda()
+    with G.Solver(precision=1, stop_rule=G.STOP_KKT, eps_kkt=1e-5, sketch_rank=20,
+                  device_wait_limit_us=0) as s:
+        s.set_data(Ad, bd, "squared")
+        with pytest.raises(G.GeniosError) as e:
+            s.solve(lam)
+        assert e.value.status == 7, (e.value.status, s.last_error())      # GENIOS_ETIMEOUT
+        assert "bounded device wait" in s.last_error()
+    torch.cuda.synchronize()          # the device answers after the timeout
+    with pytest.raises(G.GeniosError):
+        G.Solver(device_wait_limit_us=-1)
+    with G.Solver(precision=1, stop_rule=G.STOP_KKT, eps_kkt=1e-5, sketch_rank=20) as s:
+        s.set_data(Ad, bd, "squared")
+        z, info = s.solve(lam)
+    assert info["status"] == 0, info
+    assert checks.rel_kkt(A, b, z, "squared", lam) <= 2e-5
+    G.ops.status()                    # no op-level fault recorded on the device
+
+
+@pytest.mark.parametrize("case", ["logistic_fp64", "logistic_fp32", "lasso_resid", "huber_maxiter", "lasso_zero"])
+def test_device_loop_takes_the_host_loops_steps(G, case):
+    """The device-side ADMM loop (decisions of §2.1-§2.5 taken on the device between the
+    iteration's kernels, the host syncing at re-sketches and chunk ends) and the host loop
+    (device state read after every gradient pass) take the same iterations: same iteration and
+    CG counts, penalty changes, stop status and z, for the KKT and residual stop rules, a
+    re-sketching loss, a quadratic one (no re-sketch: chunk syncs only), a solve cut off by
+    max_iter (EMAXITER, last x-step included) and lambda >= lambda_max (z = 0 at the first
+    check)."""
+    if case.startswith("logistic"):
+        P = problems.logistic_lowrank(1000, 400, nnz=20, sketch_rank=40, seed=problems.seed_for(3, 9))
+        prec = 0 if case.endswith("fp64") else 1
+        lam = P.lam_frac * checks.lambda_max(*rounded(P, prec), "logistic")
+        kw = dict(rho=30.0, eps_kkt=1e-9 if prec == 0 else 1e-5, rho_update_every=10)
+    elif case == "huber_maxiter":
+        P = problems.huber_outliers(n=600, seed=problems.seed_for(6, 3), sketch_rank=30)
+        prec = 1
+        A, b = rounded(P, prec)
+        lam = P.lam_frac * np.max(np.abs(A.T @ b))
+        kw = dict(max_iter=23)
+    else:
+        P = problems.lasso_iid(400, 1000, nnz=40, seed=problems.seed_for(1, 33))
+        prec = 1
+        lmax = checks.lambda_max(*rounded(P, prec), "squared")
+        lam = 1.01 * lmax if case == "lasso_zero" else 0.1 * lmax
+        kw = dict(stop_rule=G.STOP_RESID | G.STOP_KKT, eps_rel=1e-6, eps_abs=1e-8) if case == "lasso_resid" else {}
+    zd, idev, _ = gpu_solve(G, P, prec, lam, device_loop=1, **kw)
+    zh, ihost, _ = gpu_solve(G, P, prec, lam, device_loop=0, **kw)
+    print(case, {k: (idev[k], ihost[k]) for k in ("iters", "cg_iters_total", "rho_updates", "status", "grad_launches")})
+    for k in ("status", "iters", "cg_iters_total", "rho_updates", "sketches", "grad_launches", "nnz"):
+        assert idev[k] == ihost[k], (k, idev[k], ihost[k])
+    assert idev["rho"] == ihost["rho"]
+    np.testing.assert_allclose(zd, zh, rtol=0, atol=1e-12 * max(1.0, np.max(np.abs(zh))))
+    for k in ("rel_kkt", "r_p", "r_d", "objective"):
+        a, b_ = idev[k], ihost[k]
+        assert (np.isnan(a) and np.isnan(b_)) or a == pytest.approx(b_, rel=1e-12, abs=1e-300), (k, a, b_)
+    if case == "huber_maxiter":
+        assert idev["status"] == 5 and idev["iters"] == 23        # GENIOS_EMAXITER
+    if case == "lasso_zero":
+        assert np.all(zd == 0.0)

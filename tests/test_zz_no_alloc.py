@@ -18,7 +18,7 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-11, 1: 2e-5}   # the kernel tests' tolerances for float64 / float32
+TOL = {0: 1e-11, 1: 2e-5, 2: 2e-5, 3: 2e-5}   # the kernel tests' tolerances per precision
 
 
 @pytest.fixture(scope="module")
@@ -30,18 +30,33 @@ def G():
     return pkg
 
 
-@pytest.mark.parametrize("prec", [1, 0])
-def test_noalloc_matches_workspace_entry_point_on_two_calls(G, prec):
+def _stored(G, prec, A):
+    """A in the storage of `prec` (BF16: the library's bf16 copy; FP8: E4M3 codes with per-row
+    scales) and the row scales (FP8 only)."""
+    if prec in (0, 1):
+        return G.ops.pad(A, prec), None
+    if prec == 2:
+        hi, _ = G.ops.quantize(2, A.to("cuda", torch.float32))
+        return hi, None
+    return G.ops.quantize(3, A.to("cuda", torch.float32))
+
+
+@pytest.mark.parametrize("with_d", [True, False])
+@pytest.mark.parametrize("prec", [1, 0, 2, 3])
+def test_noalloc_matches_workspace_entry_point_on_two_calls(G, prec, with_d):
+    """Every storage precision (FP8 with its per-row scales), with and without row weights: the
+    product of the entry point without allocation equals genios_op_hv's on two calls in a row of
+    different shapes, and no row pass of either ran out of its wait bound."""
     dt = torch.float64 if prec == 0 else torch.float32
     for call, (m, n) in enumerate([(1237, 3001), (4000, 2000)]):
         gen = torch.Generator().manual_seed(100 + call)
         A = torch.randn(m, n, generator=gen, dtype=torch.float64)
-        d = torch.rand(m, generator=gen, dtype=torch.float64).to("cuda", dt)
+        d = torch.rand(m, generator=gen, dtype=torch.float64).to("cuda", dt) if with_d else None
         v = torch.randn(n, generator=gen, dtype=torch.float64).to("cuda", dt)
-        Ad = G.ops.pad(A, prec)
-        y_ws = G.ops.hv(prec, Ad, n, d, 0.3, v)
-        y_na = G.ops.hv_noalloc(prec, Ad, n, d, 0.3, v)
-        torch.cuda.synchronize()
+        Ad, sc = _stored(G, prec, A)
+        y_ws = G.ops.hv(prec, Ad, n, d, 0.3, v, row_scale=sc)
+        y_na = G.ops.hv_noalloc(prec, Ad, n, d, 0.3, v, row_scale=sc)
+        G.ops.status()
         ref = y_ws.double().cpu().numpy()
         err = np.max(np.abs(y_na.double().cpu().numpy() - ref)) / np.max(np.abs(ref))
         assert err <= TOL[prec], (call, err)
