@@ -161,6 +161,10 @@ typedef struct genios_options {
                                 syncs only at re-sketches and every few iterations; 0: the host
                                 reads the device state and decides after every gradient pass.
                                 Both take the same steps */
+    int32_t batch_streams;   /* K independent problems (genios_set_data with shared_A = 0): solved on
+                                up to this many concurrent streams, each lane's launch plans made
+                                for SMs / lanes of the device, largest problems first; 1 (default):
+                                in turn on the context's stream */
 } genios_options;
 
 typedef struct genios_info {

@@ -42,6 +42,7 @@ class Options(C.Structure):
         ("batch_lockstep", C.c_int32), ("persistent_cg", C.c_int32), ("box", C.c_int32),
         ("box_lo", C.c_double), ("box_hi", C.c_double), ("sketch_adaptive", C.c_int32),
         ("sketch_rank_max", C.c_int32), ("sketch_theta", C.c_double), ("device_loop", C.c_int32),
+        ("batch_streams", C.c_int32),
     ]
 
 

@@ -63,7 +63,7 @@ struct CglShared {
     int ns, nstage_work, it, start;
     unsigned epoch;             // grid barriers passed (thread 0)
     int32_t stop;               // set by the consumers when they leave; read by the producer
-    double rho, u_scale, nu, tol, zu_rho;   // this x-step's parameters (arguments, or DevLoop)
+    double rho, u_scale, nu, tol, zu_rho, zu_lam1;   // this x-step's parameters (arguments, or DevLoop)
 };
 
 // Grid barrier among the consumer threads of all CTAs (co-resident: cooperative launch).  The
@@ -434,7 +434,7 @@ GENIOS_DEV void zu_phase(const CgLoopArgs& a, CglShared<VT>& sh) {
     VT* z = static_cast<VT*>(a.zu_z);
     VT* u = static_cast<VT*>(a.u);
     const VT* delta = static_cast<const VT*>(a.delta);
-    const double kappa = a.zu_lam1 / sh.zu_rho;
+    const double kappa = sh.zu_lam1 / sh.zu_rho;
     const double alpha = a.zu_alpha;
     const int box = a.zu_box;
     const VT lo = (VT)a.zu_lo, hi = (VT)a.zu_hi;
@@ -526,6 +526,9 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nst_cap * stage_bytes);
     uint64_t* empty = full + nst_cap;
 
+    // graph-form loop: the WHILE condition is cleared here and set again by the iteration's
+    // last finishing kernel when the loop is to go on
+    if (a.use_cond && b == 0 && tid == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)a.loop_cond, 0u);
     // device-side ADMM loop: nothing to do once the solve has stopped (the flag was written by an
     // earlier kernel in the stream, so every CTA reads the same value)
     if (a.loop != nullptr && a.loop->stop != 0) return;
@@ -536,12 +539,15 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
             sh.nu = a.loop->nu;
             sh.tol = a.loop->tol;
             sh.zu_rho = a.loop->rho;
+            sh.zu_lam1 = a.loop->lam1;
+            if (b == 0) a.loop->last_cg = a.loop->k;
         } else {
             sh.rho = a.rho;
             sh.u_scale = a.u_scale;
             sh.nu = a.nu;
             sh.tol = a.tol;
             sh.zu_rho = a.zu_rho;
+            sh.zu_lam1 = a.zu_lam1;
         }
         for (int s = 0; s < nst_cap; ++s) {
             mbar_init(&full[s], 1);

@@ -20,9 +20,12 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace genios;
@@ -77,6 +80,7 @@ struct genios_ctx {
     int K = 1;
     bool shared = false;
     std::vector<genios_ctx*> subs;
+    std::vector<cudaStream_t> lanes;   // concurrent streams of an independent-problem batch
     std::string err = "no error";
     Alloc mem;
     // problem
@@ -134,6 +138,12 @@ struct genios_ctx {
     long long* dbg = nullptr;  // bounds-check record of checked builds
     // device-side CG loop (CUDA graph with a conditional WHILE node), built on first use
     cudaStream_t cap_stream = nullptr;
+    // graph form of the device-side ADMM loop (WHILE over x-step, gradient pass, IF(KKT))
+    cudaGraph_t loop_graph = nullptr;
+    cudaGraphExec_t loop_exec = nullptr;
+    int loop_graph_sk = -1;
+    const void* loop_graph_d = nullptr;
+    bool loop_graph_failed = false;   // the graph could not be built: stream launches instead
     cudaGraph_t cg_graph = nullptr;
     cudaGraphExec_t cg_exec = nullptr;
     bool cg_graph_pc = false;
@@ -196,6 +206,7 @@ extern "C" void genios_default_options(genios_options* o) {
     o->sketch_rank_max = 128;
     o->sketch_theta = 10.0;
     o->device_loop = 1;
+    o->batch_streams = 1;
 }
 
 extern "C" genios_status genios_create(const genios_options* opts, int device, void* stream,
@@ -258,10 +269,17 @@ extern "C" void genios_destroy(genios_ctx* ctx) {
     for (genios_ctx* c : ctx->subs) genios_destroy(c);
     ctx->subs.clear();
     cudaSetDevice(ctx->device);
+    for (cudaStream_t l : ctx->lanes) {
+        cudaStreamSynchronize(l);
+        cudaStreamDestroy(l);
+    }
+    ctx->lanes.clear();
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     if (ctx->cg_exec) cudaGraphExecDestroy(ctx->cg_exec);
     if (ctx->cg_graph) cudaGraphDestroy(ctx->cg_graph);
+    if (ctx->loop_exec) cudaGraphExecDestroy(ctx->loop_exec);
+    if (ctx->loop_graph) cudaGraphDestroy(ctx->loop_graph);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     ctx->mem.free_all();
     for (auto ev : ctx->evs) cudaEventDestroy(ev);
@@ -362,6 +380,11 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
     if (ctx->cg_graph) cudaGraphDestroy(ctx->cg_graph);
     ctx->cg_exec = nullptr;
     ctx->cg_graph = nullptr;
+    if (ctx->loop_exec) cudaGraphExecDestroy(ctx->loop_exec);
+    if (ctx->loop_graph) cudaGraphDestroy(ctx->loop_graph);
+    ctx->loop_exec = nullptr;
+    ctx->loop_graph = nullptr;
+    ctx->loop_graph_sk = -1;
     ctx->mem.free_all();
     ctx->has_data = false;
     ctx->solved = false;
@@ -555,7 +578,8 @@ static cudaError_t hv_pass(genios_ctx* ctx, const void* v, const void* d,
 static cudaError_t cg_persistent(genios_ctx* ctx, const void* d, const void* g, const void* x, const void* z,
                                  void* u, double rho, double u_scale, double nu, double tol, int cg_max, int sk,
                                  const void* mask, bool zu = false, double zu_rho = 1.0, double zu_lam1 = 0.0,
-                                 double zu_alpha = 1.0, const DevLoop* loop = nullptr) {
+                                 double zu_alpha = 1.0, DevLoop* loop = nullptr, unsigned long long loop_cond = 0,
+                                 int use_cond = 0) {
     CgLoopArgs a{};
     a.rp.prec = hv_prec(ctx);
     a.rp.mode = RP_HV;
@@ -601,6 +625,8 @@ static cudaError_t cg_persistent(genios_ctx* ctx, const void* d, const void* g, 
     a.S = ctx->S;
     a.timed = 1;
     a.loop = loop;
+    a.loop_cond = loop_cond;
+    a.use_cond = use_cond;
     ctx->launches++;
     return cgloop_launch(ctx->cgl, a, ctx->stream);
 }
@@ -758,6 +784,97 @@ static genios_status build_cg_graph(genios_ctx* ctx, const void* d, bool pc) {
     return GENIOS_OK;
 }
 
+// Graph form of the device-side ADMM loop: a WHILE node whose body runs the x-step of iteration k
+// (persistent CG with the z/u update), the gradient pass at x^(k+1) with the iteration's decisions,
+// and an IF node holding the KKT pass at z when one is due.  The persistent CG kernel clears the
+// WHILE condition and the iteration's last finishing kernel sets it to DevLoop::cont, so the loop
+// leaves before an x-step whose re-sketch the host runs, after the last x-step, and at a stop.
+// All pointers are fixed for the data set and lambda, rho and the CG tolerance are read from
+// DevLoop, so one instantiation serves every solve until the data, the preconditioner rank or
+// the presence of D changes.
+static genios_status build_loop_graph(genios_ctx* ctx, const void* dvec, int sk_now) {
+    if (ctx->loop_exec) cudaGraphExecDestroy(ctx->loop_exec);
+    if (ctx->loop_graph) cudaGraphDestroy(ctx->loop_graph);
+    ctx->loop_exec = nullptr;
+    ctx->loop_graph = nullptr;
+    ctx->loop_graph_sk = -1;
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    const genios_options& o = ctx->opt;
+    DevLoop* Ld = &ctx->S->loop;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle hl = 0, hk = 0;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&hl, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams wp{};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hl;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp);
+    cudaGraph_t body = e == cudaSuccess ? wp.conditional.phGraph_out[0] : nullptr;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hk, body, 0, 0);
+    cudaStream_t saved = ctx->stream;
+    const int64_t saved_launches = ctx->launches;
+    ctx->stream = ctx->cap_stream;
+    cudaStream_t cs = ctx->cap_stream;
+    cudaGraph_t ifbody = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t c = cg_persistent(ctx, dvec, ctx->g, ctx->x, ctx->z, ctx->u, 1.0, 1.0, 1.0, 1.0, o.max_cg_iter,
+                                      sk_now, nullptr, /*zu=*/true, 1.0, 0.0, o.alpha, Ld, (unsigned long long)hl, 1);
+        if (c == cudaSuccess) c = grad_pass(ctx, ctx->x, ctx->W, ctx->D, &Ld->halt);
+        if (c == cudaSuccess)
+            c = grad_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, ctx->loss_part, ctx->n, ctx->x, ctx->u,
+                            0.0, 1.0, 0.0, ctx->g, ctx->S, ctx->sc, cs, Ld, (unsigned long long)hk,
+                            (unsigned long long)hl, 1);
+        // the IF node after the captured nodes
+        cudaStreamCaptureStatus st;
+        cudaGraph_t capg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        if (c == cudaSuccess) c = cudaStreamGetCaptureInfo(cs, &st, nullptr, &capg, &deps, nullptr, &nd);
+        cudaGraphNodeParams ip{};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = hk;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t inode;
+        if (c == cudaSuccess) c = cudaGraphAddNode(&inode, capg, deps, nullptr, nd, &ip);
+        if (c == cudaSuccess) {
+            ifbody = ip.conditional.phGraph_out[0];
+            c = cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        }
+        cudaGraph_t captured = nullptr;
+        const cudaError_t c2 = cudaStreamEndCapture(cs, &captured);
+        e = c != cudaSuccess ? c : c2;
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t c = grad_pass(ctx, ctx->z, nullptr, nullptr, nullptr);
+        if (c == cudaSuccess)
+            c = kkt_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, ctx->n, ctx->z, 0.0, 0.0, ctx->S, ctx->sc,
+                           cs, o.box, o.box_lo, o.box_hi, Ld, (unsigned long long)hl, 1);
+        cudaGraph_t captured = nullptr;
+        const cudaError_t c2 = cudaStreamEndCapture(cs, &captured);
+        e = c != cudaSuccess ? c : c2;
+    }
+    ctx->stream = saved;
+    ctx->launches = saved_launches;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->loop_exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        ctx->loop_exec = nullptr;
+        ctx->err = std::string("CUDA graph for the ADMM loop: ") + cudaGetErrorString(e);
+        return GENIOS_ECUDA;
+    }
+    ctx->loop_graph = g;
+    ctx->loop_graph_sk = sk_now;
+    ctx->loop_graph_d = dvec;
+    return GENIOS_OK;
+}
+
 // The CG loop of §2.1 on the current rhs (after rhs_init).  Graph mode: one launch of the
 // device-side loop and one read of the device state.  Host mode (profile, or use_graphs = 0):
 // the host launches each iteration and reads S->cg_done after it, with CUDA events around the
@@ -905,10 +1022,10 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
     KktSchedule kkt(o.kkt_check_every, 1);
     const double sqn = std::sqrt((double)n);
     const double floor = cg_floor(ctx);
-    // Device-side loop: the same iteration, its decisions taken on the device (loop_decide) so
-    // that the host enqueues iterations back to back; it syncs at re-sketches (which read the
-    // state) and after chunks of 4, 8, ..., 64 iterations, and the kernels queued after a stop
-    // return at once.
+    // Device-side loop: the same iteration, its decisions taken on the device (by the last block
+    // of the gradient finish, and of the KKT finish when a check is due) so that the host
+    // enqueues iterations back to back; it syncs at re-sketches (which read the state) and after
+    // chunks of 4, 8, ..., 64 iterations, and the kernels queued after a stop return at once.
     const bool dev_loop = o.device_loop && ctx->cgl.ok && !(o.stop_rule & GENIOS_STOP_GAP) && !o.profile &&
                           o.verbose == 0;
     if (dev_loop) {
@@ -939,25 +1056,75 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
         L.rho = rho;
         L.u_scale = 1.0;
         L.rel_kkt = NAN;
+        L.cont = 1;
+        L.resketch_every = o.resketch_every;
+        L.use_pc = use_pc ? 1 : 0;
+        L.quadratic = quadratic ? 1 : 0;
         CK(cudaMemcpyAsync(&ctx->S->loop, &L, sizeof(DevLoop), cudaMemcpyHostToDevice, s));
         DevLoop* Ld = &ctx->S->loop;
         const bool kkt_rule = (o.stop_rule & GENIOS_STOP_KKT) != 0;
+        const bool graph = o.use_graphs && !ctx->loop_graph_failed;
         int chunk = 4, since = 0;
-        for (int k = 1; k <= o.max_iter; ++k) {
-            // gradient pass at x^k (§3.3), then the residual and KKT-schedule decisions
-            CK(grad_pass(ctx, ctx->x, ctx->W, ctx->D, &Ld->stop));
+        if (graph) {
+            // iteration 1's gradient pass and decisions, then graph launches of the WHILE loop, with
+            // the host's re-sketches between them
+            CK(grad_pass(ctx, ctx->x, ctx->W, ctx->D, &Ld->halt));
             CK(grad_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, ctx->loss_part, n, ctx->x,
-                           ctx->u, lam2, rho, lam1, ctx->g, ctx->S, ctx->sc, s, &Ld->stop, &Ld->rho));
-            CK(loop_decide(0, ctx->S, s));
-            ctx->launches += 2;
+                           ctx->u, lam2, rho, lam1, ctx->g, ctx->S, ctx->sc, s, Ld));
+            ctx->launches++;
+            if (kkt_rule) {
+                CK(grad_pass(ctx, ctx->z, nullptr, nullptr, &Ld->skip_kkt));
+                CK(kkt_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, n, ctx->z, lam2, lam1,
+                              ctx->S, ctx->sc, s, o.box, o.box_lo, o.box_hi, Ld));
+                ctx->launches++;
+            }
+            for (int guard = 0;; ++guard) {
+                genios_status st = read_state(ctx);
+                if (st != GENIOS_OK) return st;
+                const DevLoop& Lh = ctx->Sh->loop;
+                if (Lh.stop || Lh.last_cg >= o.max_iter) break;
+                if (guard > o.max_iter + 1) FAIL(GENIOS_ESTATE, "ADMM loop graph: no progress");
+                const int k = Lh.k;   // the next x-step is iteration k's
+                if (use_pc) {
+                    const bool first = !ctx->have_precond;
+                    const bool resk = !quadratic && o.resketch_every > 0 && k > 1 && (k - 1) % o.resketch_every == 0;
+                    if (first || resk) {
+                        if (first && o.sketch_adaptive && !ctx->sketch_adapted && ctx->sk_alloc > ctx->sk)
+                            st = adapt_sketch(ctx, dvec, Lh.nu, &inf.t_sketch_ms);
+                        else
+                            st = build_precond(ctx, dvec, &inf.t_sketch_ms);
+                        if (st != GENIOS_OK) return st;
+                        inf.sketches++;
+                    }
+                }
+                const int sk_now = use_pc && ctx->have_precond ? ctx->sk : 0;
+                if (!ctx->loop_exec || ctx->loop_graph_sk != sk_now || ctx->loop_graph_d != dvec) {
+                    st = build_loop_graph(ctx, dvec, sk_now);
+                    if (st != GENIOS_OK) return st;
+                }
+                CK(cudaGraphLaunch(ctx->loop_exec, s));
+            }
+            {
+                genios_status st = read_state(ctx);
+                if (st != GENIOS_OK) return st;
+                const DevLoop& Lh = ctx->Sh->loop;
+                // kernels run by the graph: per iteration after the first the gradient pass and its
+                // finish, per KKT check two more, and the persistent CG launches
+                ctx->launches += 2 * (int64_t)(Lh.k - 1) + 2 * (Lh.grad_passes - Lh.k) + ctx->Sh->cgl_count;
+            }
+        }
+        for (int k = 1; k <= o.max_iter && !graph; ++k) {
+            // gradient pass at x^k (§3.3), then the residual and KKT-schedule decisions
+            CK(grad_pass(ctx, ctx->x, ctx->W, ctx->D, &Ld->halt));
+            CK(grad_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, ctx->loss_part, n, ctx->x,
+                           ctx->u, lam2, rho, lam1, ctx->g, ctx->S, ctx->sc, s, Ld));
+            ctx->launches++;
             if (kkt_rule) {   // relative KKT at z, run only when due (reading R21)
                 CK(grad_pass(ctx, ctx->z, nullptr, nullptr, &Ld->skip_kkt));
                 CK(kkt_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, n, ctx->z, lam2, lam1,
-                              ctx->S, ctx->sc, s, o.box, o.box_lo, o.box_hi, &Ld->skip_kkt));
+                              ctx->S, ctx->sc, s, o.box, o.box_lo, o.box_hi, Ld));
                 ctx->launches++;
             }
-            CK(loop_decide(1, ctx->S, s));   // KKT stop, penalty update, CG tolerance
-            ctx->launches++;
             // (re-)sketch (§2.2, §3.3) with D at x^k: the host reads the decisions first
             if (use_pc) {
                 const bool first = !ctx->have_precond;
@@ -1259,6 +1426,13 @@ static void drop_subs(genios_ctx* ctx) {
     ctx->subs.clear();
 }
 
+// Lanes of an independent-problem batch: min(K, batch_streams) (1: in turn on the context's
+// stream).
+static int batch_lanes(const genios_ctx* ctx, int K) {
+    const int L = std::max(1, std::min(K, (int)ctx->opt.batch_streams));
+    return L;
+}
+
 extern "C" genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const int64_t* m,
                                          const int64_t* n, const void* const* A, int A_dtype,
                                          const int64_t* lda, const void* const* b, int shared_A) {
@@ -1277,7 +1451,17 @@ extern "C" genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const
         }
         return st;
     }
-    // K independent problems: one sub-context each (same options, device and stream)
+    // K independent problems: one sub-context each (same options, device and stream).  With
+    // L > 1 lanes their launch plans use SMs / L of the device, so that L solves run side by
+    // side (see solve_lanes).
+    CK(cudaSetDevice(ctx->device));
+    const int L = batch_lanes(ctx, K);
+    int sms_all = 0;
+    {
+        SmCapScope none(0);
+        sms_all = device_sm_count();
+    }
+    const int cap = L > 1 ? std::max(1, sms_all / L) : 0;
     for (int k = 0; k < K; ++k) {
         genios_ctx* c = nullptr;
         genios_status st = genios_create(&ctx->opt, ctx->device, ctx->stream, &c);
@@ -1286,6 +1470,7 @@ extern "C" genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const
             FAIL(st, "batch: creating sub-context " + std::to_string(k) + ": " + g_create_error);
         }
         ctx->subs.push_back(c);
+        SmCapScope scope(cap);
         st = set_data_one(c, loss, m + k, n + k, A + k, A_dtype, lda + k, b + k);
         if (st != GENIOS_OK) {
             const std::string e = c->err;
@@ -1403,6 +1588,65 @@ static genios_status solve_lockstep(genios_ctx* ctx, const double* lambda1, cons
     return (genios_status)r.status;
 }
 
+// K independent problems on L concurrent lanes: L host threads, each with its own stream, take
+// the problems largest first (by m x n) from a shared counter and run the same solve as the
+// sequential batch on their stream; the sub-contexts' launch plans use SMs / L of the device
+// (genios_set_data), so that the lanes' persistent CG launches are co-resident.  Each problem's
+// kernels wait only on their own launch's CTAs.  Returns the worst status, as the sequential
+// form does; the first hard error ends the batch after the lanes finish their current problem.
+static genios_status solve_lanes(genios_ctx* ctx, const double* lambda1, const double* lambda2, void* x_out,
+                                 int out_dtype, genios_info* info, int warm_start) {
+    const int K = ctx->K;
+    const int L = batch_lanes(ctx, K);
+    CK(cudaSetDevice(ctx->device));
+    while ((int)ctx->lanes.size() < L) {
+        cudaStream_t l;
+        CK(cudaStreamCreateWithFlags(&l, cudaStreamNonBlocking));
+        ctx->lanes.push_back(l);
+    }
+    // work that the caller queued on the context's stream comes first
+    CK(cudaStreamSynchronize(ctx->stream));
+    const size_t es = out_dtype == GENIOS_DT_F64 ? 8 : 4;
+    std::vector<size_t> off(K, 0);
+    for (int k = 1; k < K; ++k) off[k] = off[k - 1] + (size_t)ctx->subs[k - 1]->n * es;
+    std::vector<int> order(K);
+    for (int k = 0; k < K; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (double)ctx->subs[a]->m * ctx->subs[a]->n > (double)ctx->subs[b]->m * ctx->subs[b]->n;
+    });
+    std::atomic<int> next{0};
+    std::atomic<int> failed{-1};
+    std::vector<genios_status> st(K, GENIOS_OK);
+    auto lane = [&](int li) {
+        cudaSetDevice(ctx->device);
+        for (;;) {
+            if (failed.load() >= 0) break;
+            const int j = next.fetch_add(1);
+            if (j >= K) break;
+            const int k = order[j];
+            genios_ctx* c = ctx->subs[k];
+            c->stream = ctx->lanes[li];
+            st[k] = solve_one(c, lambda1 + k, lambda2 + k, static_cast<char*>(x_out) + off[k], out_dtype,
+                              info ? info + k : nullptr, warm_start);
+            if (st[k] != GENIOS_OK && st[k] != GENIOS_EMAXITER) {
+                int none = -1;
+                failed.compare_exchange_strong(none, k);
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int li = 1; li < L; ++li) th.emplace_back(lane, li);
+    lane(0);
+    for (auto& t : th) t.join();
+    const int f = failed.load();
+    if (f >= 0) FAIL(st[f], "batch: problem " + std::to_string(f) + ": " + ctx->subs[f]->err);
+    genios_status worst = GENIOS_OK;
+    for (int k = 0; k < K; ++k)
+        if (st[k] == GENIOS_EMAXITER) worst = GENIOS_EMAXITER;
+    ctx->solved = true;
+    return worst;
+}
+
 // K = 1: one solve.  Shared data (lambda path): the K problems in the order given, each warm-
 // started from the previous solution (x, z, u, rho) and sharing the sketch when the loss'' is
 // constant.  Independent problems: each sub-context in turn.  x_out holds the K solutions back
@@ -1420,6 +1664,8 @@ extern "C" genios_status genios_solve(genios_ctx* ctx, const double* lambda1, co
     const size_t es = out_dtype == GENIOS_DT_F64 ? 8 : 4;
     char* out = static_cast<char*>(x_out);
     genios_status worst = GENIOS_OK;
+    if (!ctx->subs.empty() && batch_lanes(ctx, ctx->K) > 1)
+        return solve_lanes(ctx, lambda1, lambda2, x_out, out_dtype, info, warm_start);
     for (int k = 0; k < ctx->K; ++k) {
         genios_ctx* c = ctx->subs.empty() ? ctx : ctx->subs[k];
         const int warm = ctx->subs.empty() ? (k > 0 || warm_start) : warm_start;

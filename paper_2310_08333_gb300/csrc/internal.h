@@ -1,6 +1,8 @@
 // Internal interfaces between the host engine and the kernels (not part of the C ABI).
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -14,8 +16,9 @@ namespace genios {
 
 // Scalars that kernels produce and consume on the device.  One instance per context,
 // in device memory; the host reads it with an async copy when it needs a decision.
-// State of the ADMM loop when its per-iteration decisions run on the device (loop_decide): the
-// host enqueues iterations without reading back and syncs only at re-sketches and chunk ends.
+// State of the ADMM loop when its per-iteration decisions run on the device (in the last block of
+// the gradient and KKT finishing kernels): the host enqueues iterations without reading back and
+// syncs only at re-sketches and chunk ends.
 // The configuration fields are written by the host at solve start.
 struct DevLoop {
     // configuration
@@ -37,6 +40,12 @@ struct DevLoop {
     // results
     double r_p, r_d, rel_kkt, objective;
     int64_t cg_iters, grad_passes;
+    // graph form (a WHILE node over [x-step k, gradient pass k + 1, IF(KKT check)])
+    int32_t halt;            // 1: no further gradient pass (stopped, or iteration k = max_iter)
+    int32_t cont;            // 1: run x-step k next (no stop, no re-sketch due at k)
+    int32_t last_cg;         // iteration of the last x-step that ran
+    int32_t resketch_every;  // re-sketch schedule, for the exit before a due sketch
+    int32_t use_pc, quadratic, pad2, pad3;
 };
 
 struct DevState {
@@ -124,7 +133,40 @@ struct RowpassPlan {
     size_t smem;
 };
 
+// SMs the launch plans may use: the device's, or the cap set on this thread (set_sm_cap; 0 =
+// none).  Independent problems solved concurrently plan their row passes and persistent CG
+// launches for a share of the SMs, so that several cooperative launches are co-resident.
 int device_sm_count();
+void set_sm_cap(int cap);
+int sm_cap();
+// Raises a kernel's dynamic shared-memory limit to the most the device allows it (the opt-in
+// maximum per block less the kernel's static shared memory), once per kernel and device.  The
+// limit only bounds the size a launch may ask for, so one value serves every shape; setting it
+// per call would race when several threads launch the same kernel with different sizes
+// (independent problems solved concurrently).
+template <auto K>
+cudaError_t smem_optin() {
+    static std::atomic<int> done[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    int v = 0;
+    e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, K);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, v - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) done[dev].store(1, std::memory_order_release);
+    return e;
+}
+
+struct SmCapScope {
+    int saved;
+    explicit SmCapScope(int cap) : saved(sm_cap()) { set_sm_cap(cap); }
+    ~SmCapScope() { set_sm_cap(saved); }
+};
 // Device address (current device) of the word where op-level row passes record a bounded wait
 // that ran out; genios_op_status reads and clears it.  Looked up once per device, allocates nothing.
 cudaError_t op_fault_address(int** out);
@@ -169,8 +211,11 @@ struct CgLoopArgs {
     double* zu_part;           // grid x 6 float64 partials of the z/u norms
     DevState* S;               // cg_fault must be 0 at launch; results: cg_it, rr, rz, ...
     int timed;                 // accumulate H-phase and launch device times in S
-    const DevLoop* loop;       // non-null: rho, u_scale, nu, tol (and zu_rho = rho) are read from
-                               // it at launch, and the kernel returns at once once it has stopped
+    DevLoop* loop;             // non-null: rho, u_scale, nu, tol (and zu_rho = rho, zu_lam1) are read
+                               // from it at launch, the kernel returns at once once it has stopped,
+                               // and CTA 0 records the iteration in last_cg
+    unsigned long long loop_cond;   // use_cond: the WHILE handle of the graph-form loop, cleared at launch
+    int use_cond;
 };
 // ok = false when the shape does not fit (n > 1024 per SM, s > 128, the split-BF16 stream, or a
 // ring that does not fit one CTA per SM); the caller then uses the per-kernel CG path.
@@ -227,23 +272,24 @@ cudaError_t rhs_init(bool dbl, int64_t n, const void* g, const void* x, const vo
                      void* delta, void* p, void* zc, const void* U, int sk, DevState* S,
                      Scratch sc, cudaStream_t s);
 // gradient finish: g = sum_b P[b] + mu x; norms for r_d, objective, gap; loss sum
-// skip: when non-null and *skip != 0 the kernel returns at once; rho_dev: when non-null the
-// penalty is read from it instead of `rho` (the device-side loop)
+// loop: when non-null (device-side loop) the kernel returns at once once the loop has stopped,
+// reads the penalty from it, and its last block takes the iteration's first decisions (and the
+// second ones when no KKT check is due); see DevLoop
+// use_cond (graph form): the last block sets the IF handle kkt_cond to "a KKT check is due" and,
+// when none is, the WHILE handle loop_cond to DevLoop::cont.  With a loop, lambda_1 and
+// lambda_2 (mu) are read from it.
 cudaError_t grad_finish(bool dbl, const void* P, int G, int64_t ldp, const double* loss_part,
                         int64_t n, const void* x, const void* u, double mu, double rho,
                         double lam1, void* g, DevState* S, Scratch sc, cudaStream_t s,
-                        const int* skip = nullptr, const double* rho_dev = nullptr);
+                        DevLoop* loop = nullptr, unsigned long long kkt_cond = 0,
+                        unsigned long long loop_cond = 0, int use_cond = 0);
 // KKT finish at z: gz = sum_b P[b] + mu z; subgradient distance norms (box = 1: the distance of
-// 0 from gz + N(z), N the normal cone of [lo, hi]^n)
+// 0 from gz + N(z), N the normal cone of [lo, hi]^n).  loop: when non-null the kernel returns at
+// once unless a KKT check is due, and its last block takes the iteration's second decisions
 cudaError_t kkt_finish(bool dbl, const void* P, int G, int64_t ldp, int64_t n, const void* z,
                        double mu, double lam1, DevState* S, Scratch sc, cudaStream_t s, int box = 0,
-                       double lo = 0.0, double hi = 0.0, const int* skip = nullptr);
-// Device-side ADMM loop (DevLoop): the decisions of one iteration, one thread.
-//   phase 0 (after the gradient pass at x^k): count the previous x-step's CG iterations, faults,
-//     non-finite values, the residual test of §2.3 and whether a KKT check is due (skip_kkt);
-//   phase 1 (after the KKT pass, which returns at once when skip_kkt): the KKT stop test, the
-//     penalty update of §2.5 and the CG tolerance of §2.1 for the x-step.
-cudaError_t loop_decide(int phase, DevState* S, cudaStream_t s);
+                       double lo = 0.0, double hi = 0.0, DevLoop* loop = nullptr,
+                       unsigned long long loop_cond = 0, int use_cond = 0);
 // duality gap pieces from W = loss'(Ax - b) (m-vector)
 cudaError_t gap_pieces(bool dbl, int loss, int64_t m, const void* W, const void* b, double mu,
                        double lam1, DevState* S, Scratch sc, cudaStream_t s);

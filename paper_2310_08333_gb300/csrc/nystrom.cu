@@ -403,6 +403,65 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int sk, const double* G,
     if (threadIdx.x == 0) status[0] = 1;
 }
 
+// The same factorisation and triangular inverse in float32 (float value types): G of the sketch
+// is rounded to float, the right-looking Cholesky and the column-by-column inverse run in float
+// arithmetic.  Float32 is about 64x the float64 rate of this part; the factor's backward error
+// (~s eps32 ||G||) is far below the shift eta (= sqrt(n) eps32 ||Y||_F) for every sketch with a
+// moderately conditioned core, and a non-positive pivot reports failure (status 0) so that the
+// caller repeats the attempt in float64.
+__global__ void __launch_bounds__(1024) chol_inv_f32_kernel(int sk, const double* G, float* Cinv, int* status) {
+    extern __shared__ __align__(16) unsigned char csm[];
+    float* c = reinterpret_cast<float*>(csm);  // s x s
+    float* tmp = c + sk * sk;                  // s
+    __shared__ int ok;
+    for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) {
+        const int i = e / sk, j = e % sk;
+        c[e] = (float)(0.5 * (G[i * sk + j] + G[j * sk + i]));
+    }
+    if (threadIdx.x == 0) ok = 1;
+    __syncthreads();
+    for (int k = 0; k < sk; ++k) {
+        if (threadIdx.x == 0) {
+            const float d = c[k * sk + k];
+            if (!(d > 0.0f)) ok = 0;
+            c[k * sk + k] = d > 0.0f ? sqrtf(d) : 1.0f;
+        }
+        __syncthreads();
+        if (!ok) break;
+        const float rpiv = 1.0f / c[k * sk + k];
+        for (int j = k + 1 + threadIdx.x; j < sk; j += blockDim.x) c[k * sk + j] *= rpiv;
+        __syncthreads();
+        const int rem = sk - k - 1;
+        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+            const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+            if (j >= i) c[i * sk + j] = fmaf(-c[k * sk + i], c[k * sk + j], c[i * sk + j]);
+        }
+        __syncthreads();
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) status[0] = 0;
+        return;
+    }
+    for (int j = 0; j < sk; ++j) {
+        for (int l = threadIdx.x; l < j; l += blockDim.x) tmp[l] = c[l * sk + j];
+        __syncthreads();
+        const float ajj = 1.0f / c[j * sk + j];
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+            float acc = 0.0f;
+            for (int l = i; l < j; ++l) acc = fmaf(c[i * sk + l], tmp[l], acc);
+            c[i * sk + j] = -ajj * acc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) c[j * sk + j] = ajj;
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) {
+        const int i = e / sk, j = e % sk;
+        Cinv[e] = j >= i ? c[e] : 0.0f;
+    }
+    if (threadIdx.x == 0) status[0] = 1;
+}
+
 // Cyclic Jacobi eigendecomposition of the symmetric s x s matrix M (one CTA), arithmetic in T.
 // Round-robin ("circle") ordering: in round r of a sweep over se = s + (s odd) indices, index
 // se - 1 meets r and, for k = 1 .. se/2 - 1, (r + k) mod (se - 1) meets (r - k) mod (se - 1);
@@ -415,6 +474,7 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int sk, const double* G,
 // the rotations.  Rows of M and V are stored with an odd stride so that the column updates
 // are free of bank conflicts.  Out: Vout (s x s, columns = eigenvectors), ev (unsorted).
 constexpr int JAC_MAX_PER_THREAD = 8;   // ceil((s/2) * s / 1024) for s <= 128
+constexpr int JAC_MAX_BLK = 3;          // ceil((s/2) (s/2 + 1) / 2 / 1024) for s <= 128
 template <typename T, bool VS>
 __global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min, const T* Vinit, T* Vout,
                                                      double* ev, int max_sweeps, double rot_tol,
@@ -448,6 +508,26 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min,
     }
     const T tol = (T)rot_tol;
     const T ctol = (T)sqrt(rot_tol);
+    // this thread's pair blocks (a, b), b >= a, of the one-pass two-sided update, fixed for the
+    // whole iteration (half (half + 1) / 2 <= 2080 blocks for s <= 128)
+    int ba[JAC_MAX_BLK], bbv[JAC_MAX_BLK];
+    int nb = 0;
+    {
+        int a = 0, rem = threadIdx.x;
+        while (a < half && rem >= half - a) { rem -= half - a; ++a; }
+#pragma unroll
+        for (int r = 0; r < JAC_MAX_BLK; ++r) {
+            ba[r] = 0; bbv[r] = 0;
+            if (a < half) { ba[r] = a; bbv[r] = a + rem; nb = r + 1; }
+            // advance by blockDim.x blocks
+            int step = blockDim.x;
+            while (a < half && step > 0) {
+                const int left = half - a - rem;   // blocks left in row a after this one
+                if (step < left) { rem += step; step = 0; }
+                else { step -= left; ++a; rem = 0; }
+            }
+        }
+    }
     int sweep = 0;
     __syncthreads();
     for (; sweep < max_sweeps; ++sweep) {
@@ -476,30 +556,47 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min,
                 cs[k] = c; sn[k] = s; pp[k] = p; qq[k] = q;
             }
             __syncthreads();
+            // M <- R M R^T in one pass: the 2 x 2 block of rows {p_a, q_a} and columns {p_b, q_b}
+            // becomes R_a X R_b^T, with R_k = [[c_k, -s_k], [s_k, c_k]]; the blocks are disjoint,
+            // so each is read and written by one thread (b >= a, mirrored: M stays symmetric)
 #pragma unroll
-            for (int r = 0; r < JAC_MAX_PER_THREAD; ++r) {            // rows: M <- J^T M
-                if (r >= nw) break;
-                const int k = wk[r], j = wj[r];
-                const T sv = sn[k];
-                if (sv == T(0)) continue;
-                const int p = pp[k], q = qq[k];
-                const T cv = cs[k];
-                const T mp = M[p * ld + j], mq = M[q * ld + j];
-                M[p * ld + j] = cv * mp - sv * mq;
-                M[q * ld + j] = sv * mp + cv * mq;
+            for (int r = 0; r < JAC_MAX_BLK; ++r) {
+                if (r >= nb) break;
+                const int a = ba[r], bb = bbv[r];
+                const T sa = sn[a], sb = sn[bb];
+                if (sa == T(0) && sb == T(0)) continue;
+                const T ca = cs[a], cb = cs[bb];
+                const int pa = pp[a], qa = qq[a], pb = pp[bb], qb = qq[bb];
+                const bool qa_ok = qa < sk, qb_ok = qb < sk;
+                const T x00 = M[pa * ld + pb];
+                const T x01 = qb_ok ? M[pa * ld + qb] : T(0);
+                const T x10 = qa_ok ? M[qa * ld + pb] : T(0);
+                const T x11 = (qa_ok && qb_ok) ? M[qa * ld + qb] : T(0);
+                // T = R_a X
+                const T t00 = ca * x00 - sa * x10, t01 = ca * x01 - sa * x11;
+                const T t10 = sa * x00 + ca * x10, t11 = sa * x01 + ca * x11;
+                // X' = T R_b^T
+                const T y00 = t00 * cb - t01 * sb, y01 = t00 * sb + t01 * cb;
+                const T y10 = t10 * cb - t11 * sb, y11 = t10 * sb + t11 * cb;
+                M[pa * ld + pb] = y00;
+                if (qb_ok) M[pa * ld + qb] = y01;
+                if (qa_ok) M[qa * ld + pb] = y10;
+                if (qa_ok && qb_ok) M[qa * ld + qb] = y11;
+                if (a != bb) {
+                    M[pb * ld + pa] = y00;
+                    if (qb_ok) M[qb * ld + pa] = y01;
+                    if (qa_ok) M[pb * ld + qa] = y10;
+                    if (qa_ok && qb_ok) M[qb * ld + qa] = y11;
+                }
             }
-            __syncthreads();
 #pragma unroll
-            for (int r = 0; r < JAC_MAX_PER_THREAD; ++r) {            // cols: M <- M J, V <- V J
+            for (int r = 0; r < JAC_MAX_PER_THREAD; ++r) {            // V <- V R^T
                 if (r >= nw) break;
                 const int k = wk[r], i = wj[r];
                 const T sv = sn[k];
                 if (sv == T(0)) continue;
                 const int p = pp[k], q = qq[k];
                 const T cv = cs[k];
-                const T mp = M[i * ld + p], mq = M[i * ld + q];
-                M[i * ld + p] = cv * mp - sv * mq;
-                M[i * ld + q] = sv * mp + cv * mq;
                 const T vp = V[i * vld + p], vq = V[i * vld + q];
                 V[i * vld + p] = cv * vp - sv * vq;
                 V[i * vld + q] = sv * vp + cv * vq;
@@ -697,9 +794,13 @@ static cudaError_t orthonormalize(int64_t n, int sk, const VT* Om, NysWork w, cu
     const size_t gsm = 2 * GR_ROWS * sk * sizeof(VT);
     const size_t tsm = (size_t)(sk * sk + 16 * sk) * sizeof(VT);
     const size_t csm = (size_t)ss * 8 + (size_t)sk * 8;
-    cudaFuncSetAttribute(ts_gemm<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm + 1024);
-    cudaFuncSetAttribute(chol_inv_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm + 1024);
-    cudaFuncSetAttribute(gram_partial<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm + 1024);
+    {
+        cudaError_t e = smem_optin<ts_gemm<VT>>();
+        if (e == cudaSuccess) e = smem_optin<chol_inv_kernel<VT>>();
+        if (e == cudaSuccess) e = smem_optin<gram_partial<VT>>();
+        if (e != cudaSuccess) return e;
+    }
+    (void)tsm; (void)csm; (void)gsm;
     VT* Q = static_cast<VT*>(w.Oq);
     VT* Rinv = static_cast<VT*>(w.Cinv);
     const VT* src = Om;
@@ -724,28 +825,10 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
     double* eta = w.scal + 1;
     unsigned* counter = reinterpret_cast<unsigned*>(w.scal + 8);
     cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
-    // partials for the sum of squares reuse gpart (>= 1024 doubles as gram_blocks*ss >= s^2)
+    // partials for the sum of squares reuse gpart (>= 1024 doubles as gram_blocks*ss >= s^2);
+    // ||Y||_F^2 is read back together with the first Cholesky's status (one host sync)
     sumsq_kernel<VT><<<256, 256, 0, s>>>(total, Y, w.gpart, counter, fro2);
     NYS_CHECK("sumsq");
-    {
-        double f2 = 0.0;
-        cudaMemcpyAsync(&f2, fro2, sizeof(double), cudaMemcpyDeviceToHost, s);
-        cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return e;
-        if (!std::isfinite(f2)) {
-            *chol_ok = -1;  // non-finite sketch
-            return cudaSuccess;
-        }
-        if (f2 == 0.0) {
-            // A^T D A Omega = 0 (e.g. D = 0): the approximation is 0, lam = 0 and any orthonormal
-            // U; Eq. (10) then reduces to the identity
-            cudaMemcpyAsync(U, Om, (size_t)total * sizeof(VT), cudaMemcpyDeviceToDevice, s);
-            cudaMemsetAsync(lam, 0, (size_t)sk * sizeof(double), s);
-            if (eta_out) cudaMemsetAsync(eta_out, 0, sizeof(double), s);
-            *chol_ok = 2;   // success without eigenvectors (nothing to warm-start from)
-            return cudaGetLastError();
-        }
-    }
     const int ss = sk * sk;
     const int gb = gram_blocks(n);
     const size_t gsm = 2 * GR_ROWS * sk * sizeof(VT);
@@ -755,16 +838,22 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
     const size_t sld = (size_t)sk * (size_t)(sk | 1);
     const bool vs = 2 * sld * sizeof(VT) + (size_t)se * (sizeof(VT) + 4) <= 200 * 1024;
     const size_t jsm = (vs ? 2 : 1) * sld * sizeof(VT) + (size_t)se * (sizeof(VT) + 4) + 64;
-    cudaFuncSetAttribute(ts_gemm<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm + 1024);
-    cudaFuncSetAttribute(chol_inv_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm + 1024);
-    cudaFuncSetAttribute(jacobi_kernel<VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm + 1024);
-    cudaFuncSetAttribute(jacobi_kernel<VT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm + 1024);
-    cudaFuncSetAttribute(gram_partial<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm + 1024);
+    {
+        cudaError_t e = smem_optin<ts_gemm<VT>>();
+        if (e == cudaSuccess) e = smem_optin<chol_inv_kernel<VT>>();
+        if (e == cudaSuccess) e = smem_optin<jacobi_kernel<VT, true>>();
+        if (e == cudaSuccess) e = smem_optin<jacobi_kernel<VT, false>>();
+        if (e == cudaSuccess) e = smem_optin<gram_partial<VT>>();
+        if (e == cudaSuccess && sizeof(VT) == 4) e = smem_optin<chol_inv_f32_kernel>();
+        if (e != cudaSuccess) return e;
+    }
     VT* Ye = static_cast<VT*>(w.B);
     VT* Cinv = static_cast<VT*>(w.Cinv);
     double* V = w.C;  // reuse: C scratch holds eigenvectors after the Cholesky stage
     *chol_ok = 0;
     double mult = 1.0;
+    const bool f32 = sizeof(VT) == 4;
+    const size_t csm32 = (size_t)ss * 4 + (size_t)sk * 4;
     for (int attempt = 0; attempt < 7; ++attempt, mult *= 10.0) {
         shift_kernel<VT><<<512, 256, 0, s>>>(total, n, eps, mult, fro2, Y, Om, Ye, eta);
         NYS_CHECK("shift");
@@ -772,16 +861,35 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
         NYS_CHECK("gram_partial(Omega, Y_eta)");
         gram_reduce<<<(ss + 255) / 256, 256, 0, s>>>(gb, ss, w.gpart, w.G, 1, sk);
         NYS_CHECK("gram_reduce");
-        chol_inv_kernel<VT><<<1, 1024, csm, s>>>(sk, w.G, w.M, Cinv, w.status);
-        NYS_CHECK("chol_inv");
-        int st = 0;
-        cudaMemcpyAsync(&st, w.status, sizeof(int), cudaMemcpyDeviceToHost, s);
-        cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return e;
-        if (st == 1) {
-            *chol_ok = 1;
-            break;
+        // float value types factor in float32 first, and in float64 only if that fails
+        for (int dbl_pass = f32 ? 0 : 1; dbl_pass < 2; ++dbl_pass) {
+            if (dbl_pass) chol_inv_kernel<VT><<<1, 1024, csm, s>>>(sk, w.G, w.M, Cinv, w.status);
+            else chol_inv_f32_kernel<<<1, 1024, csm32, s>>>(sk, w.G, reinterpret_cast<float*>(Cinv), w.status);
+            NYS_CHECK("chol_inv");
+            struct { double f2; int st; } hv{0.0, 0};
+            cudaMemcpyAsync(&hv.f2, fro2, sizeof(double), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(&hv.st, w.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return e;
+            if (!std::isfinite(hv.f2)) {
+                *chol_ok = -1;  // non-finite sketch
+                return cudaSuccess;
+            }
+            if (hv.f2 == 0.0) {
+                // A^T D A Omega = 0 (e.g. D = 0): the approximation is 0, lam = 0 and any
+                // orthonormal U; Eq. (10) then reduces to the identity
+                cudaMemcpyAsync(U, Om, (size_t)total * sizeof(VT), cudaMemcpyDeviceToDevice, s);
+                cudaMemsetAsync(lam, 0, (size_t)sk * sizeof(double), s);
+                if (eta_out) cudaMemsetAsync(eta_out, 0, sizeof(double), s);
+                *chol_ok = 2;   // success without eigenvectors (nothing to warm-start from)
+                return cudaGetLastError();
+            }
+            if (hv.st == 1) {
+                *chol_ok = 1;
+                break;
+            }
         }
+        if (*chol_ok) break;
     }
     if (!*chol_ok) return cudaSuccess;
     // B = Y_eta C^{-1} (in place)

@@ -173,11 +173,18 @@ static const int kNch[] = {1, 2, 3, 4, 6, 8, 10};
 
 static int max_nch(int prec) { return prec == P_FP64 ? 8 : 10; }
 
+// SM budget of the launch plans made on this thread (0: the whole device); see SmCapScope
+static thread_local int t_sm_cap = 0;
+
+void set_sm_cap(int cap) { t_sm_cap = cap; }
+int sm_cap() { return t_sm_cap; }
+
 int device_sm_count() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return n > 0 ? n : 1;
+    if (n <= 0) n = 1;
+    return t_sm_cap > 0 && t_sm_cap < n ? t_sm_cap : n;
 }
 
 RowpassPlan rowpass_plan(int prec, int64_t m, int64_t n, int64_t lda, size_t smem_budget) {
@@ -225,13 +232,8 @@ RowpassPlan rowpass_plan(int prec, int64_t m, int64_t n, int64_t lda, size_t sme
 template <int P, int NCH, int MODE>
 static cudaError_t launch_one(const RowpassArgs& a, const RowpassPlan& p, cudaStream_t s) {
     auto kern = rowpass_kernel<P, NCH, MODE>;
-    static bool attr_set = false;  // per instantiation; attribute is per device function
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)RP_SMEM_BUDGET + 4096);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t e = smem_optin<rowpass_kernel<P, NCH, MODE>>();
+    if (e != cudaSuccess) return e;
     kern<<<p.grid, RP_THREADS, p.smem, s>>>(a, p.rows_per_stage, p.nstages);
     return cudaGetLastError();
 }

@@ -463,7 +463,7 @@ cudaError_t tc_gemm(const unsigned char* A, const unsigned char* B, float* out, 
     a.err = err;
     if (N < 16 || N > 256 || (N % 16) != 0 || splits < 1 || splits > ktiles) return cudaErrorInvalidValue;
     const size_t smem = (size_t)a.stages * (UM_TILE_A + (size_t)N * 128) + 1024;
-    cudaError_t e = cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_optin<umma_gemm_kernel>();
     if (e != cudaSuccess) return e;
     umma_gemm_kernel<<<(unsigned)(mtiles * splits), UM_THREADS, smem, s>>>(a);
     return cudaGetLastError();

@@ -195,13 +195,134 @@ __global__ void rhs_init_kernel(int64_t n, const VT* g, const VT* x, const VT* z
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Device-side ADMM loop: the host loop's per-iteration decisions (genios_api.cu solve_one), in
+// the same order and arithmetic, taken by one thread in the last block of the finishing
+// kernels of the gradient and KKT passes.
+// ------------------------------------------------------------------------------------------
+// The KKT check schedule of KktSchedule (internal.h): due when the residual test first passes,
+// then after a gap of 1..kkt_every iterations predicted from the decrease between the last two
+// evaluations.
+GENIOS_DEV bool loop_kkt_due(DevLoop* L, int k, bool resid_ok) {
+    const bool first = resid_ok && !L->resid_seen;
+    if (resid_ok) L->resid_seen = 1;
+    return first || k - L->kkt_last >= L->kkt_gap;
+}
+
+GENIOS_DEV void loop_kkt_record(DevLoop* L, int k, double v) {
+    int g = L->kkt_every;
+    if (L->kkt_vlast > 0.0 && v > L->eps_kkt && v < L->kkt_vlast && k > L->kkt_last) {
+        const double rate = log(v / L->kkt_vlast) / (double)(k - L->kkt_last);
+        const double need = log(L->eps_kkt / v) / rate;
+        g = need < (double)L->kkt_every ? (int)ceil(need) : L->kkt_every;
+        if (g < 1) g = 1;
+    }
+    L->kkt_gap = g;
+    L->kkt_last = k;
+    L->kkt_vlast = v;
+}
+
+GENIOS_DEV void loop_stop(DevLoop* L, int iters) {
+    L->stop = 1;
+    L->halt = 1;
+    L->cont = 0;
+    L->iters = iters;
+}
+
+// Phase a, after the gradient pass at x^k (thread 0 of grad_finish's last block, once its values
+// are in S): the previous x-step's CG count, faults, non-finite values, the residual test of
+// §2.3 and whether a KKT check is due.
+GENIOS_DEV void loop_phase_a(DevLoop* L, const DevState* S) {
+    L->skip_kkt = 1;
+    {
+        const int k = ++L->k;
+        if (k > 1) L->cg_iters += S->cg_it;   // the previous x-step's CG solve
+        L->grad_passes += 1;
+        if (S->cg_fault != 0 || S->rp_fault != 0) {
+            L->status = GENIOS_ETIMEOUT;
+            loop_stop(L, k);
+            return;
+        }
+        L->objective = S->loss_sum + L->lam1 * S->gx1 + 0.5 * L->lam2 * S->gx2;
+        if (!isfinite(S->rd2) || !isfinite(S->loss_sum)) {
+            L->status = GENIOS_ENUMERIC;
+            loop_stop(L, k);
+            return;
+        }
+        if (k > 1) {   // residuals of the previous iterate (Eqs. (11)-(12)) and the stop tests
+            const double rp = sqrt(S->rp2), rd = sqrt(S->rd2);
+            L->last_rp = rp;
+            L->last_rd = rd;
+            L->r_p = rp;
+            L->r_d = rd;
+            const bool resid_ok = rp <= L->sqn * L->eps_abs + L->eps_rel * fmax(sqrt(S->x2), sqrt(S->z2)) &&
+                                  rd <= L->sqn * L->eps_abs + L->eps_rel * sqrt(S->rhou2);
+            if (L->stop_resid && resid_ok) {
+                L->status = GENIOS_OK;
+                loop_stop(L, k - 1);
+                return;
+            }
+            if (L->stop_kkt && loop_kkt_due(L, k, resid_ok)) {
+                L->skip_kkt = 0;
+                L->grad_passes += 1;
+            }
+        }
+    }
+}
+
+// Phase b, after the KKT pass when one was due (thread 0 of kkt_finish's last block), else right
+// after phase a: the KKT stop test, the penalty update of §2.5 and the CG tolerance of §2.1.
+GENIOS_DEV void loop_phase_b(DevLoop* L, const DevState* S) {
+    if (L->stop) return;
+    const int k = L->k;
+    if (!L->skip_kkt) {   // relative KKT at z (reading R6)
+        const double v = sqrt(S->kd2) / fmax(fmax(sqrt(S->kg2), L->lam1), 1e-30);
+        L->rel_kkt = v;
+        loop_kkt_record(L, k, v);
+        if (v <= L->eps_kkt) {
+            L->status = GENIOS_OK;
+            loop_stop(L, k - 1);
+            return;
+        }
+    }
+    // penalty update (§2.5)
+    double u_scale = 1.0, rho = L->rho;
+    if (k > 1 && L->rho_every > 0 && (k - 1) % L->rho_every == 0 && L->n_rho < L->rho_max && k <= L->rho_until) {
+        double nr = rho;
+        if (L->last_rp > L->rho_mu * L->last_rd) nr = rho * L->rho_tau;
+        else if (L->last_rd > L->rho_mu * L->last_rp) nr = rho / L->rho_tau;
+        if (nr != rho) {
+            u_scale = rho / nr;
+            rho = nr;
+            L->n_rho += 1;
+        }
+    }
+    L->rho = rho;
+    L->u_scale = u_scale;
+    L->nu = rho + L->lam2 + L->sigma;
+    // CG tolerance (§2.1)
+    double tol = k <= 1 ? L->cg_first : fmin(sqrt(L->last_rp * L->last_rd), 1.0) / pow((double)k, L->gamma);
+    L->tol = fmax(tol, L->cg_floor);
+    // graph form: no gradient pass after the last x-step; leave the loop before an x-step whose
+    // re-sketch (§2.2, every resketch_every iterations) the host runs
+    if (k >= L->max_iter) L->halt = 1;
+    const bool sketch_due = L->use_pc && !L->quadratic && L->resketch_every > 0 && k > 1 &&
+                            (k - 1) % L->resketch_every == 0;
+    L->cont = sketch_due ? 0 : 1;
+}
+
 template <typename VT>
 __global__ void grad_finish_kernel(const VT* P, int G, int64_t ldp, const double* loss_part,
                                    int64_t n, const VT* x, const VT* u, double mu, double rho,
-                                   double lam1, VT* g, DevState* S, Scratch sc, const int* skip,
-                                   const double* rho_dev) {
-    if (skip != nullptr && *skip != 0) return;   // uniform across the grid
-    if (rho_dev != nullptr) rho = *rho_dev;
+                                   double lam1, VT* g, DevState* S, Scratch sc, DevLoop* loop,
+                                   cudaGraphConditionalHandle kkt_cond, cudaGraphConditionalHandle loop_cond,
+                                   int use_cond) {
+    if (loop != nullptr) {   // device-side loop: nothing to do once it halted (uniform across the grid)
+        if (loop->halt) return;
+        rho = loop->rho;
+        mu = loop->lam2;
+        lam1 = loop->lam1;
+    }
     __shared__ double sh[8 * 33];
     const int64_t j = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
     double sum = column_sum<VT, double>(P, G, ldp, j, n, sh);
@@ -237,6 +358,14 @@ __global__ void grad_finish_kernel(const VT* P, int G, int64_t ldp, const double
             S->gx1 = out[4];
             S->gx2 = out[5];
             S->atw_inf = outm[0];
+            if (loop != nullptr) {
+                loop_phase_a(loop, S);
+                if (loop->skip_kkt) loop_phase_b(loop, S);
+                if (use_cond) {
+                    cudaGraphSetConditional(kkt_cond, loop->skip_kkt ? 0u : 1u);
+                    if (loop->skip_kkt) cudaGraphSetConditional(loop_cond, loop->cont ? 1u : 0u);
+                }
+            }
         }
     }
 }
@@ -244,8 +373,13 @@ __global__ void grad_finish_kernel(const VT* P, int G, int64_t ldp, const double
 template <typename VT>
 __global__ void kkt_finish_kernel(const VT* P, int G, int64_t ldp, int64_t n, const VT* z,
                                   double mu, double lam1, DevState* S, Scratch sc, int box, double lo,
-                                  double hi, const int* skip) {
-    if (skip != nullptr && *skip != 0) return;   // uniform across the grid
+                                  double hi, DevLoop* loop, cudaGraphConditionalHandle loop_cond,
+                                  int use_cond) {
+    if (loop != nullptr) {
+        if (loop->skip_kkt) return;   // no check due (uniform across the grid)
+        mu = loop->lam2;
+        lam1 = loop->lam1;
+    }
     __shared__ double sh[8 * 33];
     const int64_t j = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
     double sum = column_sum<VT, double>(P, G, ldp, j, n, sh);
@@ -272,6 +406,10 @@ __global__ void kkt_finish_kernel(const VT* P, int G, int64_t ldp, int64_t n, co
             S->kd2 = out[0];
             S->kg2 = out[1];
             S->kdmax = outm[0];
+            if (loop != nullptr) {
+                loop_phase_b(loop, S);
+                if (use_cond) cudaGraphSetConditional(loop_cond, loop->cont ? 1u : 0u);
+            }
         }
     }
 }
@@ -450,127 +588,24 @@ cudaError_t rhs_init(bool dbl, int64_t n, const void* g, const void* x, const vo
 
 cudaError_t grad_finish(bool dbl, const void* P, int G, int64_t ldp, const double* loss_part,
                         int64_t n, const void* x, const void* u, double mu, double rho,
-                        double lam1, void* g, DevState* S, Scratch sc, cudaStream_t s,
-                        const int* skip, const double* rho_dev) {
+                        double lam1, void* g, DevState* S, Scratch sc, cudaStream_t s, DevLoop* loop,
+                        unsigned long long kkt_cond, unsigned long long loop_cond, int use_cond) {
     const int grid = nblocks(n, 32);
-    if (dbl) grad_finish_kernel<double><<<grid, VT_THREADS, 0, s>>>(CC<double>(P), G, ldp, loss_part, n, CC<double>(x), CC<double>(u), mu, rho, lam1, C<double>(g), S, sc, skip, rho_dev);
-    else grad_finish_kernel<float><<<grid, VT_THREADS, 0, s>>>(CC<float>(P), G, ldp, loss_part, n, CC<float>(x), CC<float>(u), mu, rho, lam1, C<float>(g), S, sc, skip, rho_dev);
+    if (dbl) grad_finish_kernel<double><<<grid, VT_THREADS, 0, s>>>(CC<double>(P), G, ldp, loss_part, n, CC<double>(x), CC<double>(u), mu, rho, lam1, C<double>(g), S, sc, loop, (cudaGraphConditionalHandle)kkt_cond, (cudaGraphConditionalHandle)loop_cond, use_cond);
+    else grad_finish_kernel<float><<<grid, VT_THREADS, 0, s>>>(CC<float>(P), G, ldp, loss_part, n, CC<float>(x), CC<float>(u), mu, rho, lam1, C<float>(g), S, sc, loop, (cudaGraphConditionalHandle)kkt_cond, (cudaGraphConditionalHandle)loop_cond, use_cond);
     return cudaGetLastError();
 }
 
 cudaError_t kkt_finish(bool dbl, const void* P, int G, int64_t ldp, int64_t n, const void* z,
                        double mu, double lam1, DevState* S, Scratch sc, cudaStream_t s, int box, double lo,
-                       double hi, const int* skip) {
+                       double hi, DevLoop* loop, unsigned long long loop_cond, int use_cond) {
     const int grid = nblocks(n, 32);
-    if (dbl) kkt_finish_kernel<double><<<grid, VT_THREADS, 0, s>>>(CC<double>(P), G, ldp, n, CC<double>(z), mu, lam1, S, sc, box, lo, hi, skip);
-    else kkt_finish_kernel<float><<<grid, VT_THREADS, 0, s>>>(CC<float>(P), G, ldp, n, CC<float>(z), mu, lam1, S, sc, box, lo, hi, skip);
+    if (dbl) kkt_finish_kernel<double><<<grid, VT_THREADS, 0, s>>>(CC<double>(P), G, ldp, n, CC<double>(z), mu, lam1, S, sc, box, lo, hi, loop, (cudaGraphConditionalHandle)loop_cond, use_cond);
+    else kkt_finish_kernel<float><<<grid, VT_THREADS, 0, s>>>(CC<float>(P), G, ldp, n, CC<float>(z), mu, lam1, S, sc, box, lo, hi, loop, (cudaGraphConditionalHandle)loop_cond, use_cond);
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------------------------------
-// Device-side ADMM loop: the host loop's per-iteration decisions (genios_api.cu solve_one), in
-// the same order and arithmetic, taken by one thread between the iteration's kernels.
-// ------------------------------------------------------------------------------------------
-// The KKT check schedule of KktSchedule (internal.h): due when the residual test first passes,
-// then after a gap of 1..kkt_every iterations predicted from the decrease between the last two
-// evaluations.
-GENIOS_DEV bool loop_kkt_due(DevLoop* L, int k, bool resid_ok) {
-    const bool first = resid_ok && !L->resid_seen;
-    if (resid_ok) L->resid_seen = 1;
-    return first || k - L->kkt_last >= L->kkt_gap;
-}
 
-GENIOS_DEV void loop_kkt_record(DevLoop* L, int k, double v) {
-    int g = L->kkt_every;
-    if (L->kkt_vlast > 0.0 && v > L->eps_kkt && v < L->kkt_vlast && k > L->kkt_last) {
-        const double rate = log(v / L->kkt_vlast) / (double)(k - L->kkt_last);
-        const double need = log(L->eps_kkt / v) / rate;
-        g = need < (double)L->kkt_every ? (int)ceil(need) : L->kkt_every;
-        if (g < 1) g = 1;
-    }
-    L->kkt_gap = g;
-    L->kkt_last = k;
-    L->kkt_vlast = v;
-}
-
-__global__ void loop_decide_kernel(int phase, DevState* S) {
-    DevLoop* L = &S->loop;
-    if (L->stop) return;
-    if (phase == 0) {
-        const int k = ++L->k;
-        if (k > 1) L->cg_iters += S->cg_it;   // the previous x-step's CG solve
-        L->grad_passes += 1;
-        if (S->cg_fault != 0 || S->rp_fault != 0) {
-            L->status = GENIOS_ETIMEOUT;
-            L->stop = 1;
-            L->iters = k;
-            return;
-        }
-        L->objective = S->loss_sum + L->lam1 * S->gx1 + 0.5 * L->lam2 * S->gx2;
-        if (!isfinite(S->rd2) || !isfinite(S->loss_sum)) {
-            L->status = GENIOS_ENUMERIC;
-            L->stop = 1;
-            L->iters = k;
-            return;
-        }
-        L->skip_kkt = 1;
-        if (k > 1) {   // residuals of the previous iterate (Eqs. (11)-(12)) and the stop tests
-            const double rp = sqrt(S->rp2), rd = sqrt(S->rd2);
-            L->last_rp = rp;
-            L->last_rd = rd;
-            L->r_p = rp;
-            L->r_d = rd;
-            const bool resid_ok = rp <= L->sqn * L->eps_abs + L->eps_rel * fmax(sqrt(S->x2), sqrt(S->z2)) &&
-                                  rd <= L->sqn * L->eps_abs + L->eps_rel * sqrt(S->rhou2);
-            if (L->stop_resid && resid_ok) {
-                L->status = GENIOS_OK;
-                L->stop = 1;
-                L->iters = k - 1;
-                return;
-            }
-            if (L->stop_kkt && loop_kkt_due(L, k, resid_ok)) {
-                L->skip_kkt = 0;
-                L->grad_passes += 1;
-            }
-        }
-        return;
-    }
-    const int k = L->k;
-    if (!L->skip_kkt) {   // relative KKT at z (reading R6)
-        const double v = sqrt(S->kd2) / fmax(fmax(sqrt(S->kg2), L->lam1), 1e-30);
-        L->rel_kkt = v;
-        loop_kkt_record(L, k, v);
-        if (v <= L->eps_kkt) {
-            L->status = GENIOS_OK;
-            L->stop = 1;
-            L->iters = k - 1;
-            return;
-        }
-    }
-    // penalty update (§2.5)
-    double u_scale = 1.0, rho = L->rho;
-    if (k > 1 && L->rho_every > 0 && (k - 1) % L->rho_every == 0 && L->n_rho < L->rho_max && k <= L->rho_until) {
-        double nr = rho;
-        if (L->last_rp > L->rho_mu * L->last_rd) nr = rho * L->rho_tau;
-        else if (L->last_rd > L->rho_mu * L->last_rp) nr = rho / L->rho_tau;
-        if (nr != rho) {
-            u_scale = rho / nr;
-            rho = nr;
-            L->n_rho += 1;
-        }
-    }
-    L->rho = rho;
-    L->u_scale = u_scale;
-    L->nu = rho + L->lam2 + L->sigma;
-    // CG tolerance (§2.1)
-    double tol = k <= 1 ? L->cg_first : fmin(sqrt(L->last_rp * L->last_rd), 1.0) / pow((double)k, L->gamma);
-    L->tol = fmax(tol, L->cg_floor);
-}
-
-cudaError_t loop_decide(int phase, DevState* S, cudaStream_t s) {
-    loop_decide_kernel<<<1, 1, 0, s>>>(phase, S);
-    return cudaGetLastError();
-}
 
 cudaError_t gap_pieces(bool dbl, int loss, int64_t m, const void* W, const void* b, double mu,
                        double lam1, DevState* S, Scratch sc, cudaStream_t s) {
