@@ -162,9 +162,10 @@ typedef struct genios_options {
                                 reads the device state and decides after every gradient pass.
                                 Both take the same steps */
     int32_t batch_streams;   /* K independent problems (genios_set_data with shared_A = 0): solved on
-                                up to this many concurrent streams, each lane's launch plans made
-                                for SMs / lanes of the device, largest problems first; 1 (default):
-                                in turn on the context's stream */
+                                up to this many concurrent streams (default 8), each lane's launch
+                                plans made for SMs / lanes of the device, largest problems first,
+                                the CG loop as ordinary launches (cooperative launches from several
+                                streams do not overlap); 1: in turn on the context's stream */
 } genios_options;
 
 typedef struct genios_info {

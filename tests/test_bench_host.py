@@ -5,6 +5,7 @@ import json
 import os
 
 import numpy as np
+import pytest
 
 import bench
 
@@ -82,3 +83,36 @@ def test_oracle_leg_certifies_z_and_times_an_iteration():
     assert leg["kind"] == "oracle" and leg["cores"] >= 1 and "x 50 iterations" in leg["sample"]
     bad = bench.oracle_leg(P, lam, 1.0, np.zeros(P.n), iters=1, sample_iters=1)
     assert bad["rel_kkt_oracle"] > 1e-3     # z = 0 is not the solution below lambda_max
+
+
+def test_record_traffic_parses_ncu_csv_and_keys_by_source_hash(tmp_path, monkeypatch):
+    """The traffic record is (dram read + write bytes of the cgloop launch) / iterations, keyed by
+    the current hash of the kernel's sources; other kernels' rows are ignored."""
+    csvf = tmp_path / "cap.csv"
+    csvf.write_text(
+        '==PROF== Connected\n'
+        '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n'
+        '"0","1","python","h","void genios::cgloop_kernel<1, 4>(CgLoopArgs, int, int)","1","7","(544, 1, 1)","(152, 1, 1)","0","10.3","Command line profiler metrics","dram__bytes_read.sum","Gbyte","12.83"\n'
+        '"0","1","python","h","void genios::cgloop_kernel<1, 4>(CgLoopArgs, int, int)","1","7","(544, 1, 1)","(152, 1, 1)","0","10.3","Command line profiler metrics","dram__bytes_write.sum","Mbyte","50.80"\n'
+        '"1","1","python","h","void genios::rowpass_kernel<1, 4, 1>(RowpassArgs, int, int)","1","7","(544, 1, 1)","(152, 1, 1)","0","10.3","Command line profiler metrics","dram__bytes_read.sum","Gbyte","0.64"\n')
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "cgloop_source_hash", lambda: "a" * 16)
+    rec = bench.record_traffic(str(csvf), 20)
+    assert rec["source_hash"] == "a" * 16
+    assert rec["dram_bytes_per_iteration"] == pytest.approx((12.83e9 + 50.8e6) / 20)
+    assert bench.traffic_record("cgloop_fp32", "logistic_20000x8000") == pytest.approx(rec["dram_bytes_per_iteration"])
+
+
+def test_record_traffic_reads_the_raw_page_export(tmp_path, monkeypatch):
+    """The same record from ncu's raw-page CSV export (one column per metric, units in row 2)."""
+    csvf = tmp_path / "raw.csv"
+    csvf.write_text(
+        '"ID","Kernel Name","dram__bytes_read.sum","dram__bytes_write.sum","gpu__time_duration.sum"\n'
+        '"","","Mbyte","Kbyte","msecond"\n'
+        '"0","void genios::cgloop_kernel<1, 4>(CgLoopArgs, int, int)","12,833.10","50,800.00","2.11"\n')
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "cgloop_source_hash", lambda: "b" * 16)
+    rec = bench.record_traffic(str(csvf), 20)
+    assert rec["dram_bytes_per_iteration"] == pytest.approx((12833.1e6 + 50.8e6) / 20)
