@@ -33,7 +33,7 @@ import problems  # noqa: E402
 METRIC = "time-to-1e-4 KKT solve & Hv HBM GB/s: plain vs mixed/batched, same GB300"
 WORKLOADS = {
     # name: (generator kwargs, rho, description)
-    "logistic_20000x8000": (dict(m=20000, n=8000), 30.0,
+    "logistic_20000x8000": (dict(m=20000, n=8000), 240.0,
                             "l1-logistic 20000x8000 low-rank(50)+0.1 noise, 400 nnz, lambda=0.02 lambda_max, rank 100"),
     "lasso_1000x10000": (None, 1.0, "Lasso 1000x10000 AR(1) rows, 200 nnz, lambda=0.05 lambda_max, rank 50"),
 }
@@ -42,6 +42,12 @@ WORKLOADS = {
 # the same ADMM iteration count (5334 / 5331 / 5340) with 26.8k / 21.3k / 16.6k CG iterations, and
 # 1e-1 nearly doubles it (9876); every returned z is certified at 1e-4 by the float64 oracle.
 CG_FLOOR = {"logistic_20000x8000": 5e-2}
+# Penalty schedule per workload (§2.5).  On the 20000 x 8000 logistic workload residual balancing
+# lowers rho to 15 from any start, and the solve then takes 3000-5300 iterations; held fixed, rho =
+# 60 / 120 / 240 / 480 / 960 take 1335 / 658 / 272 / 371 / 451 iterations (FP32, floor 5e-2, every
+# returned z certified at 1e-4 by the float64 oracle).  The bench holds rho = 240, the best of that
+# doubling grid.
+RHO_UPDATE_EVERY = {"logistic_20000x8000": 0}
 PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
@@ -286,9 +292,12 @@ def run_ours(args):
 
     floor = CG_FLOOR.get(args.workload, -1.0) if args.cg_floor is None else args.cg_floor
 
+    every = RHO_UPDATE_EVERY.get(args.workload, 25)
+
     def solver(p, profile=0):
         return G.Solver(precision=p, stop_rule=G.STOP_KKT, eps_kkt=args.eps_kkt,
-                        sketch_rank=P.sketch_rank, rho=rho, max_iter=args.max_iter, cg_tol_floor=floor,
+                        sketch_rank=P.sketch_rank, rho=rho, rho_update_every=every, max_iter=args.max_iter,
+                        cg_tol_floor=floor,
                         profile=1 if args.no_graphs else profile,
                         use_graphs=0 if args.no_graphs else 1,
                         persistent_cg=0 if args.per_kernel_cg else 1)
@@ -443,7 +452,8 @@ def run_ours(args):
             "data": "synthetic (seeded generator; the paper's datasets are not available)",
             "config": {"workload": args.workload, "description": desc, "m": P.m, "n": P.n,
                        "loss": P.loss, "lambda1": lam, "rho": rho, "sketch_rank": P.sketch_rank,
-                       "eps_kkt": args.eps_kkt, "cg_tol_floor": floor, "precision": args.precision,
+                       "eps_kkt": args.eps_kkt, "cg_tol_floor": floor, "rho_update_every": every,
+                       "precision": args.precision,
                        "l2": "inputs larger than L2 (A = %d MB)" % (A32.nbytes // 2 ** 20),
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "value_note": "seconds per solve to 1e-4 relative KKT, whole job (time / solves)",
