@@ -16,7 +16,7 @@ from oracle import admm as oadmm, checks  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-BENCH_RHO = 240.0   # fixed penalty of the 20000 x 8000 logistic workload (with the CG floor 5e-2)
+BENCH_RHO = 240.0   # fixed penalty of the 20000 x 8000 logistic workload (with the CG floor 0.2)
 
 
 @pytest.fixture(scope="module")
@@ -326,14 +326,16 @@ def test_mixed_precision_reaches_kkt_and_reports_error(G, prec):
 
 def test_config3_full_size_kkt_property(G):
     """Full 20000 x 8000 logistic workload in the benchmark's configuration (FP32, rho = 240 held
-    fixed, CG floor 5e-2, rank 100, stop at a 1e-4 relative KKT residual): the oracle cannot run its exact solve here
+    fixed, CG floor 0.2, rank 100 re-sketched every 80 iterations, stop at a 1e-4 relative KKT
+    residual): the oracle cannot run its exact solve here
     in seconds, so it certifies the GPU's z by the float64 optimality conditions, which hold at
     any size: its relative KKT residual at z meets the tolerance the GPU stopped on (to float32
     rounding of the GPU's own evaluation) and equals the value the GPU reported."""
     P = problems.logistic_lowrank()
     A32 = P.A.astype(np.float32)
     z, info, lmax = gpu_solve(G, P, 1, P.lam_frac * checks.lambda_max(A32.astype(np.float64), P.b, "logistic"),
-                              rho=BENCH_RHO, rho_update_every=0, cg_tol_floor=5e-2, eps_kkt=1e-4, max_iter=12000)
+                              rho=BENCH_RHO, rho_update_every=0, cg_tol_floor=0.2, resketch_every=80, eps_kkt=1e-4,
+                              max_iter=12000)
     A = A32.astype(np.float64)
     lam = info["lambda1"]
     kkt = checks.rel_kkt(A, P.b, z, "logistic", lam)
@@ -345,9 +347,9 @@ def test_config3_full_size_kkt_property(G):
     S = checks.support(z)
     g = checks.grad_f(A, P.b, z, "logistic")
     assert np.max(np.abs(np.delete(g, S))) <= lam * (1 + 1e-3)
-    # the rank-100 Nystrom preconditioner keeps the CG solves short (about 2 iterations per
-    # x-update here); a broken preconditioner runs into the 50-iteration cap instead
-    assert info["cg_iters_total"] <= 6 * info["iters"], (info["cg_iters_total"], info["iters"])
+    # the rank-100 Nystrom preconditioner keeps the CG solves short (about one iteration per
+    # x-update at this floor); a broken preconditioner runs into the 50-iteration cap instead
+    assert info["cg_iters_total"] <= 3 * info["iters"], (info["cg_iters_total"], info["iters"])
 
 
 def test_b_is_read_with_the_dtype_of_A(G):
