@@ -72,6 +72,17 @@ GENIOS_DEV void loss_eval(int loss, T t, T& l0, T& l1, T& l2) {
     }
 }
 
+// l'(t) alone, the same value loss_eval gives as l1
+template <typename T>
+GENIOS_DEV T loss_d1(int loss, T t) {
+    if (loss == LOSS_SQUARED) return t;
+    if (loss == LOSS_HUBER) {
+        const T at = t < T(0) ? -t : t;
+        return at <= T(1) ? T(2) * t : (t < T(0) ? T(-2) : T(2));
+    }
+    return sigmoid_<T>(t);
+}
+
 // Fenchel conjugate of the loss (App. A), +inf outside the domain.
 GENIOS_DEV double loss_conj(int loss, double v) {
     if (loss == LOSS_SQUARED) return 0.5 * v * v;

@@ -238,103 +238,167 @@ __global__ void sumsq_kernel(int64_t total, const VT* X, double* part, unsigned*
         if (threadIdx.x == 0) *out = o[0];
 }
 
-// Yeta = Y + eta * Omega, eta = sqrt(n) * eps * sqrt(fro2) * mult (written to eta_out by block 0)
-template <typename VT>
-__global__ void shift_kernel(int64_t total, int64_t n, double eps, double mult, const double* fro2,
-                             const VT* Y, const VT* Om, VT* Ye, double* eta_out) {
-    const double eta = sqrt((double)n) * eps * sqrt(*fro2) * mult;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *eta_out = eta;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x)
-        Ye[e] = Y[e] + (VT)eta * Om[e];
-}
+// The shifted sketch Y_eta = Y + eta Omega (§2.2) is never stored: the kernels that read it form
+// it on the fly as fma(eta, Omega, Y), the same value type rounding wherever it is read.
+// eta = c_eta sqrt(||Y||_F^2), c_eta = sqrt(n) eps mult (mult grows by 10x per failed attempt).
 
-// Gram partials: part[b][a*s + c] = sum over the block's rows of X[j,a] * Y[j,c].  Rows are
-// staged through shared memory GR_ROWS at a time; each thread owns an 8 x 8 tile of the s x s
-// output (s <= 128) accumulated in the value type over the block's rows, written as float64.
-constexpr int GR_THREADS = 256, GR_ROWS = 16, GR_T = 8;
+// 4-wide value-type vector (16 bytes for float, 32 for double)
+template <typename VT> struct alignas(4 * sizeof(VT)) TsVec4 { VT v[4]; };
+
+// Gram partials: part[b][a*s + c] = sum over block b's rows j of X[j,a] * Y'[j,c], with
+// Y' = Y + eta Yadd when Yadd is given (block 0 then stores eta).  A block takes a contiguous
+// share of the rows and stages them GR_ROWS at a time in shared memory (rows padded to a multiple
+// of 4 entries); each thread owns up to GR_TILES 4 x 4 tiles of the s x s output (s <= 128) and
+// accumulates them in the value type over the block's rows: per row, one 4-wide load of each
+// operand per tile feeds 16 FMAs.  The partials are written as float64.
+constexpr int GR_THREADS = 256, GR_ROWS = 32;
+constexpr int GR_TILES = (32 * 32 + GR_THREADS - 1) / GR_THREADS;   // (s/4)^2 tiles, s <= 128
 template <typename VT>
-__global__ void __launch_bounds__(GR_THREADS) gram_partial(int64_t n, int sk, const VT* X,
-                                                          const VT* Y, double* part) {
+static size_t gram_smem(int sk) { return (size_t)2 * GR_ROWS * ((sk + 3) & ~3) * sizeof(VT); }
+template <typename VT>
+__global__ void __launch_bounds__(GR_THREADS) gram_partial(int64_t n, int sk, const VT* X, const VT* Y,
+                                                          const VT* Yadd, const double* fro2, double c_eta,
+                                                          double* eta_out, double* part) {
     extern __shared__ __align__(16) unsigned char gsm[];
-    VT* xs = reinterpret_cast<VT*>(gsm);
-    VT* ys = xs + GR_ROWS * sk;
-    const int ss = sk * sk;
-    const int nt = (sk + GR_T - 1) / GR_T;
-    const bool active = (int)threadIdx.x < nt * nt;
-    const int a0 = ((int)threadIdx.x / nt) * GR_T, c0 = ((int)threadIdx.x % nt) * GR_T;
+    const int ldr = (sk + 3) & ~3;
+    VT* xs = reinterpret_cast<VT*>(gsm);   // GR_ROWS x ldr
+    VT* ys = xs + GR_ROWS * ldr;           // GR_ROWS x ldr
+    const int ncg = ldr / 4;
+    const int ntile = ncg * ncg;
+    const VT eta = Yadd ? (VT)(c_eta * sqrt(*fro2)) : VT(0);
+    if (Yadd && blockIdx.x == 0 && threadIdx.x == 0) *eta_out = (double)eta;
     const int64_t rows_per_block = (n + gridDim.x - 1) / gridDim.x;
     const int64_t j0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t j1 = min(n, j0 + rows_per_block);
-    VT acc[GR_T][GR_T];
+    VT acc[GR_TILES][4][4];
 #pragma unroll
-    for (int i = 0; i < GR_T; ++i)
+    for (int t = 0; t < GR_TILES; ++t)
 #pragma unroll
-        for (int j = 0; j < GR_T; ++j) acc[i][j] = VT(0);
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[t][i][c] = VT(0);
     for (int64_t jt = j0; jt < j1; jt += GR_ROWS) {
         const int rows = (int)min((int64_t)GR_ROWS, j1 - jt);
-        for (int e = threadIdx.x; e < GR_ROWS * sk; e += GR_THREADS) {
-            const int r = e / sk;
-            xs[e] = r < rows ? X[(jt + r) * sk + e % sk] : VT(0);
-            ys[e] = r < rows ? Y[(jt + r) * sk + e % sk] : VT(0);
+        __syncthreads();   // the previous chunk's reads are done
+        for (int e = threadIdx.x; e < GR_ROWS * ldr; e += GR_THREADS) {
+            const int r = e / ldr, k = e % ldr;
+            const bool in = r < rows && k < sk;
+            const int64_t g = (jt + r) * sk + k;
+            xs[e] = in ? X[g] : VT(0);
+            ys[e] = in ? (Yadd ? fma(eta, Yadd[g], Y[g]) : Y[g]) : VT(0);
         }
         __syncthreads();
-        if (active) {
-            for (int r = 0; r < GR_ROWS; ++r) {
-                VT xa[GR_T], yc[GR_T];
 #pragma unroll
-                for (int i = 0; i < GR_T; ++i) {
-                    xa[i] = a0 + i < sk ? xs[r * sk + a0 + i] : VT(0);
-                    yc[i] = c0 + i < sk ? ys[r * sk + c0 + i] : VT(0);
+        for (int t = 0; t < GR_TILES; ++t) {
+            const int tile = threadIdx.x + t * GR_THREADS;
+            if (tile < ntile) {
+                const int a0 = (tile / ncg) * 4, c0 = (tile % ncg) * 4;
+                for (int r = 0; r < rows; ++r) {
+                    const TsVec4<VT> xa = *reinterpret_cast<const TsVec4<VT>*>(xs + r * ldr + a0);
+                    const TsVec4<VT> yc = *reinterpret_cast<const TsVec4<VT>*>(ys + r * ldr + c0);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[t][i][c] = fma(xa.v[i], yc.v[c], acc[t][i][c]);
                 }
-#pragma unroll
-                for (int i = 0; i < GR_T; ++i)
-#pragma unroll
-                    for (int j = 0; j < GR_T; ++j) acc[i][j] = fma(xa[i], yc[j], acc[i][j]);
             }
         }
-        __syncthreads();
     }
-    if (active) {
+    const int ss = sk * sk;
 #pragma unroll
-        for (int i = 0; i < GR_T; ++i)
+    for (int t = 0; t < GR_TILES; ++t) {
+        const int tile = threadIdx.x + t * GR_THREADS;
+        if (tile < ntile) {
+            const int a0 = (tile / ncg) * 4, c0 = (tile % ncg) * 4;
 #pragma unroll
-            for (int j = 0; j < GR_T; ++j)
-                if (a0 + i < sk && c0 + j < sk)
-                    part[(int64_t)blockIdx.x * ss + (a0 + i) * sk + c0 + j] = (double)acc[i][j];
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (a0 + i < sk && c0 + c < sk)
+                        part[(int64_t)blockIdx.x * ss + (a0 + i) * sk + c0 + c] = (double)acc[t][i][c];
+        }
     }
 }
 
-__global__ void gram_reduce(int nb, int ss, const double* part, double* G, int symmetrize, int sk) {
+// G[e] = sum over the nb partials, in block order (four interleaved running sums, combined in a
+// fixed order: the result does not depend on the launch)
+__global__ void gram_reduce(int nb, int ss, const double* part, double* G) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ss; e += gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int b = 0; b < nb; ++b) acc += part[(int64_t)b * ss + e];
-        G[e] = acc;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int b = 0;
+        for (; b + 3 < nb; b += 4) {
+            a0 += part[(int64_t)b * ss + e];
+            a1 += part[(int64_t)(b + 1) * ss + e];
+            a2 += part[(int64_t)(b + 2) * ss + e];
+            a3 += part[(int64_t)(b + 3) * ss + e];
+        }
+        for (; b < nb; ++b) a0 += part[(int64_t)b * ss + e];
+        G[e] = (a0 + a1) + (a2 + a3);
     }
-    (void)symmetrize;
-    (void)sk;
 }
 
-// C (n x s) = X (n x s) * Wm (s x s, value type), 16 rows per block, in place allowed
+// C (n x s) = X' (n x s) * Wm (s x s, value type), X' = X + eta Xadd when Xadd is given; in place
+// (Cout == X) allowed: a block stages its tile of rows in shared memory before writing them.  Wm is
+// staged once per block (rows padded to a multiple of 4 entries); each thread owns a 4 x 4 tile
+// of the TS_ROWS x s output tile: per k, four broadcast loads of X' and one 4-wide load of Wm feed
+// 16 FMAs.
+constexpr int TS_THREADS = 256, TS_ROWS = 32;
 template <typename VT>
-__global__ void __launch_bounds__(256) ts_gemm(int64_t n, int sk, const VT* X, const VT* Wm, VT* Cout) {
+static size_t ts_smem(int sk) {
+    const size_t ldw = (size_t)((sk + 3) & ~3);
+    return ((size_t)sk * ldw + (size_t)TS_ROWS * (sk + 1)) * sizeof(VT);
+}
+template <typename VT>
+__global__ void __launch_bounds__(TS_THREADS) ts_gemm(int64_t n, int sk, const VT* X, const VT* Xadd,
+                                                     const double* eta_p, const VT* Wm, VT* Cout) {
     extern __shared__ __align__(16) unsigned char tsm[];
-    VT* ws = reinterpret_cast<VT*>(tsm);
-    VT* xs = ws + sk * sk;
-    for (int e = threadIdx.x; e < sk * sk; e += blockDim.x) ws[e] = Wm[e];
-    for (int64_t j0 = (int64_t)blockIdx.x * 16; j0 < n; j0 += (int64_t)gridDim.x * 16) {
-        const int rows = (int)min((int64_t)16, n - j0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < 16 * sk; e += blockDim.x) {
-            const int r = e / sk;
-            xs[e] = r < rows ? X[(j0 + r) * sk + e % sk] : VT(0);
+    const int ldw = (sk + 3) & ~3, ldx = sk + 1;
+    VT* ws = reinterpret_cast<VT*>(tsm);   // sk x ldw
+    VT* xs = ws + sk * ldw;                // TS_ROWS x ldx
+    const VT eta = Xadd ? (VT)*eta_p : VT(0);
+    for (int e = threadIdx.x; e < sk * ldw; e += TS_THREADS) {
+        const int k = e / ldw, c = e % ldw;
+        ws[e] = c < sk ? Wm[k * sk + c] : VT(0);
+    }
+    const int ncg = ldw / 4;
+    const int rg = threadIdx.x / ncg, cg = threadIdx.x % ncg;
+    const bool act = rg < TS_ROWS / 4;
+    const int64_t ntile = (n + TS_ROWS - 1) / TS_ROWS;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int64_t j0 = tile * TS_ROWS;
+        const int rows = (int)min((int64_t)TS_ROWS, n - j0);
+        __syncthreads();   // Wm staged; the previous tile's reads are done
+        for (int e = threadIdx.x; e < TS_ROWS * sk; e += TS_THREADS) {
+            const int r = e / sk, k = e % sk;
+            const int64_t g = (j0 + r) * sk + k;
+            xs[r * ldx + k] = r < rows ? (Xadd ? fma(eta, Xadd[g], X[g]) : X[g]) : VT(0);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < rows * sk; e += blockDim.x) {
-            const int r = e / sk, c = e % sk;
-            VT acc = VT(0);
-            for (int k = 0; k < sk; ++k) acc = fma(xs[r * sk + k], ws[k * sk + c], acc);
-            Cout[(j0 + r) * sk + c] = acc;
+        if (act) {
+            VT acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[i][c] = VT(0);
+            const VT* xr = xs + (rg * 4) * ldx;
+            for (int k = 0; k < sk; ++k) {
+                const TsVec4<VT> w4 = *reinterpret_cast<const TsVec4<VT>*>(ws + k * ldw + cg * 4);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const VT xv = xr[i * ldx + k];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[i][c] = fma(xv, w4.v[c], acc[i][c]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = rg * 4 + i;
+                if (r < rows) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (cg * 4 + c < sk) Cout[(j0 + r) * sk + cg * 4 + c] = acc[i][c];
+                }
+            }
         }
     }
 }
@@ -708,6 +772,7 @@ __global__ void eig_finish_kernel(int sk, const T* V, const double* ev, const do
 // ------------------------------------------------------------------------------------------
 static size_t al(size_t b) { return (b + 255) & ~size_t(255); }
 static int gram_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(128, n / 64)); }
+static int ts_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(304, (n + TS_ROWS - 1) / TS_ROWS)); }
 
 size_t nystrom_work_bytes(int prec, int64_t m, int64_t n, int sk) {
     const size_t vt = prec == P_FP64 ? 8 : 4;
@@ -791,8 +856,8 @@ template <typename VT>
 static cudaError_t orthonormalize(int64_t n, int sk, const VT* Om, NysWork w, cudaStream_t s) {
     const int ss = sk * sk;
     const int gb = gram_blocks(n);
-    const size_t gsm = 2 * GR_ROWS * sk * sizeof(VT);
-    const size_t tsm = (size_t)(sk * sk + 16 * sk) * sizeof(VT);
+    const size_t gsm = gram_smem<VT>(sk);
+    const size_t tsm = ts_smem<VT>(sk);
     const size_t csm = (size_t)ss * 8 + (size_t)sk * 8;
     {
         cudaError_t e = smem_optin<ts_gemm<VT>>();
@@ -800,16 +865,15 @@ static cudaError_t orthonormalize(int64_t n, int sk, const VT* Om, NysWork w, cu
         if (e == cudaSuccess) e = smem_optin<gram_partial<VT>>();
         if (e != cudaSuccess) return e;
     }
-    (void)tsm; (void)csm; (void)gsm;
     VT* Q = static_cast<VT*>(w.Oq);
     VT* Rinv = static_cast<VT*>(w.Cinv);
     const VT* src = Om;
     for (int pass = 0; pass < 2; ++pass) {
-        gram_partial<VT><<<gb, GR_THREADS, gsm, s>>>(n, sk, src, src, w.gpart);
-        gram_reduce<<<(ss + 255) / 256, 256, 0, s>>>(gb, ss, w.gpart, w.G, 1, sk);
+        gram_partial<VT><<<gb, GR_THREADS, gsm, s>>>(n, sk, src, src, nullptr, nullptr, 0.0, nullptr, w.gpart);
+        gram_reduce<<<(ss + 255) / 256, 256, 0, s>>>(gb, ss, w.gpart, w.G);
         chol_inv_kernel<VT><<<1, 1024, csm, s>>>(sk, w.G, w.M, Rinv, w.status);
         NYS_CHECK("orthonormalize");
-        ts_gemm<VT><<<512, 256, tsm, s>>>(n, sk, src, Rinv, Q);
+        ts_gemm<VT><<<ts_grid(n), TS_THREADS, tsm, s>>>(n, sk, src, nullptr, nullptr, Rinv, Q);
         NYS_CHECK("orthonormalize ts_gemm");
         src = Q;
     }
@@ -831,8 +895,8 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
     NYS_CHECK("sumsq");
     const int ss = sk * sk;
     const int gb = gram_blocks(n);
-    const size_t gsm = 2 * GR_ROWS * sk * sizeof(VT);
-    const size_t tsm = (size_t)(sk * sk + 16 * sk) * sizeof(VT);
+    const size_t gsm = gram_smem<VT>(sk);
+    const size_t tsm = ts_smem<VT>(sk);
     const size_t csm = (size_t)ss * 8 + (size_t)sk * 8;
     const int se = sk + (sk & 1);
     const size_t sld = (size_t)sk * (size_t)(sk | 1);
@@ -847,7 +911,7 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
         if (e == cudaSuccess && sizeof(VT) == 4) e = smem_optin<chol_inv_f32_kernel>();
         if (e != cudaSuccess) return e;
     }
-    VT* Ye = static_cast<VT*>(w.B);
+    VT* B = static_cast<VT*>(w.B);
     VT* Cinv = static_cast<VT*>(w.Cinv);
     double* V = w.C;  // reuse: C scratch holds eigenvectors after the Cholesky stage
     *chol_ok = 0;
@@ -855,11 +919,11 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
     const bool f32 = sizeof(VT) == 4;
     const size_t csm32 = (size_t)ss * 4 + (size_t)sk * 4;
     for (int attempt = 0; attempt < 7; ++attempt, mult *= 10.0) {
-        shift_kernel<VT><<<512, 256, 0, s>>>(total, n, eps, mult, fro2, Y, Om, Ye, eta);
-        NYS_CHECK("shift");
-        gram_partial<VT><<<gb, GR_THREADS, gsm, s>>>(n, sk, Om, Ye, w.gpart);
+        // Omega^T Y_eta with Y_eta = Y + eta Omega, eta = sqrt(n) eps ||Y||_F mult (stored in eta)
+        gram_partial<VT><<<gb, GR_THREADS, gsm, s>>>(n, sk, Om, Y, Om, fro2, std::sqrt((double)n) * eps * mult,
+                                                     eta, w.gpart);
         NYS_CHECK("gram_partial(Omega, Y_eta)");
-        gram_reduce<<<(ss + 255) / 256, 256, 0, s>>>(gb, ss, w.gpart, w.G, 1, sk);
+        gram_reduce<<<(ss + 255) / 256, 256, 0, s>>>(gb, ss, w.gpart, w.G);
         NYS_CHECK("gram_reduce");
         // float value types factor in float32 first, and in float64 only if that fails
         for (int dbl_pass = f32 ? 0 : 1; dbl_pass < 2; ++dbl_pass) {
@@ -892,13 +956,13 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
         if (*chol_ok) break;
     }
     if (!*chol_ok) return cudaSuccess;
-    // B = Y_eta C^{-1} (in place)
-    ts_gemm<VT><<<512, 256, tsm, s>>>(n, sk, Ye, Cinv, Ye);
+    // B = Y_eta C^{-1}
+    ts_gemm<VT><<<ts_grid(n), TS_THREADS, tsm, s>>>(n, sk, Y, Om, eta, Cinv, B);
     NYS_CHECK("ts_gemm(B)");
     // M = B^T B
-    gram_partial<VT><<<gb, GR_THREADS, gsm, s>>>(n, sk, Ye, Ye, w.gpart);
+    gram_partial<VT><<<gb, GR_THREADS, gsm, s>>>(n, sk, B, B, nullptr, nullptr, 0.0, nullptr, w.gpart);
     NYS_CHECK("gram_partial(B, B)");
-    gram_reduce<<<(ss + 255) / 256, 256, 0, s>>>(gb, ss, w.gpart, w.M, 1, sk);
+    gram_reduce<<<(ss + 255) / 256, 256, 0, s>>>(gb, ss, w.gpart, w.M);
     NYS_CHECK("gram_reduce(M)");
     // Jacobi in the value type (a float64 Jacobi at s = 100 costs ~25 ms on this part's float64
     // pipe); in float32 the eigenvalues are then refined by float64 Rayleigh quotients
@@ -934,7 +998,7 @@ static cudaError_t core(int64_t n, int sk, const VT* Om, VT* Y, NysWork w, VT* U
     eig_finish_kernel<VT, VT><<<1, 256, 0, s>>>(sk, Vj, w.ev, eta, Cinv, lam);
     NYS_CHECK("eig_finish");
     // U = B V Sigma^{-1}
-    ts_gemm<VT><<<512, 256, tsm, s>>>(n, sk, Ye, Cinv, U);
+    ts_gemm<VT><<<ts_grid(n), TS_THREADS, tsm, s>>>(n, sk, B, nullptr, nullptr, Cinv, U);
     NYS_CHECK("ts_gemm(U)");
     if (eta_out) cudaMemcpyAsync(eta_out, eta, sizeof(double), cudaMemcpyDeviceToDevice, s);
     return cudaGetLastError();

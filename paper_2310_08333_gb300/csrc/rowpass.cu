@@ -154,7 +154,20 @@ rowpass_kernel(const RowpassArgs a, const int rps, const int nst_cap) {
             }
         }
     }
-    if (MODE == RP_GRAD && tid == 0 && a.loss_part != nullptr) a.loss_part[blockIdx.x] = lsum;
+    if (MODE == RP_GRAD && a.loss_part != nullptr) {
+        // the rows' loss values sit in the lsum of one lane per row: a fixed-order block sum
+        __shared__ double lred[RP_CWARPS];
+        double v = lsum;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) lred[wid] = v;
+        named_bar_sync(1, RP_CTHREADS);
+        if (tid == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < RP_CWARPS; ++w) tot += lred[w];
+            a.loss_part[blockIdx.x] = tot;
+        }
+    }
     if (a.timer != nullptr) {
         __syncwarp();
         named_bar_sync(1, RP_CTHREADS);

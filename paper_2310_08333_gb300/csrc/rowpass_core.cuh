@@ -23,7 +23,8 @@ __host__ __device__ constexpr int rp_rb(int prec, int nch) {
 // Consumes `rows` rows (global indices i0, i0 + 1, ...) of one stage at sb.  Called by the
 // 512 consumer threads together (it synchronises them with named barrier 1).  red: the
 // [2][RB][RP_CWARPS] row-total scratch; par alternates its halves.  vr / yr: the thread's
-// chunks of v and of the partial y.  Gradient mode adds the loss values into lsum (thread 0);
+// chunks of v and of the partial y.  Gradient mode adds each row's loss value into the lsum of
+// one consumer thread (the caller sums the threads' lsum in a fixed order);
 // Hv mode with want_wt adds sum_i w_i t_i (the rows' share of v^T A^T diag(d) A v) into wt
 // (thread 0).
 template <int P, int NCH, int MODE>
@@ -122,7 +123,7 @@ GENIOS_DEV void rp_consume_stage(const RowpassArgs& a, const unsigned char* smem
                 red[(par * RB + lane / GS) * RP_CWARPS + wid] = dot[0];
         }
         named_bar_sync(1, RP_CTHREADS);
-        VT tot[RB];
+        VT wq[RB];
         {
             const int g = lane / GS, sidx = lane & (GS - 1);
             VT t = VT(0);
@@ -130,33 +131,46 @@ GENIOS_DEV void rp_consume_stage(const RowpassArgs& a, const unsigned char* smem
             for (int w = sidx; w < RP_CWARPS; w += GS) t += red[(par * RB + g) * RP_CWARPS + w];
 #pragma unroll
             for (int off = GS >> 1; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+            if constexpr (MODE == RP_HV) {
+                VT tot[RB];
 #pragma unroll
-            for (int q = 0; q < RB; ++q) tot[q] = __shfl_sync(0xffffffffu, t, q * GS);
-        }
-        VT wq[RB];
+                for (int q = 0; q < RB; ++q) tot[q] = __shfl_sync(0xffffffffu, t, q * GS);
 #pragma unroll
-        for (int q = 0; q < RB; ++q) {
-            VT t = tot[q];
-            wq[q] = VT(0);
-            if (rr + q < rows) {
-                const int64_t i = i0 + rr + q;
-                VT sc = VT(1);
-                if constexpr (FP8) sc = GCHK(a.dbg, i, a.m) ? (VT)__ldg(a.row_scale + i) : VT(1);
-                t *= sc;
-                if (MODE == RP_HV) {
-                    VT w = (dvec != nullptr && GCHK(a.dbg, i, a.m)) ? dvec[i] * t : t;
-                    wq[q] = w * sc;
-                    if (want_wt && tid == 0) wt += w * t;
-                } else {
-                    VT l0, l1, l2;
-                    loss_eval<VT>(a.loss, t - (GCHK(a.dbg, i, a.m) ? bvec[i] : VT(0)), l0, l1, l2);
-                    wq[q] = l1 * sc;
-                    if (tid == 0 && GCHK(a.dbg, i, a.m)) {
+                for (int q = 0; q < RB; ++q) {
+                    VT tq = tot[q];
+                    wq[q] = VT(0);
+                    if (rr + q < rows) {
+                        const int64_t i = i0 + rr + q;
+                        VT sc = VT(1);
+                        if constexpr (FP8) sc = GCHK(a.dbg, i, a.m) ? (VT)__ldg(a.row_scale + i) : VT(1);
+                        tq *= sc;
+                        VT w = (dvec != nullptr && GCHK(a.dbg, i, a.m)) ? dvec[i] * tq : tq;
+                        wq[q] = w * sc;
+                        if (want_wt && tid == 0) wt += w * tq;
+                    }
+                }
+            } else {
+                // Row g's weight l'(t_g - b_g) is formed by its own lane group (one loss
+                // derivative per lane instead of RB per thread), then broadcast.  The row's loss
+                // value and l'' are formed by one lane, in a warp that rotates with the row, and
+                // go to W_out / D_out and to that lane's share of the loss sum.
+                VT w = VT(0);
+                const int64_t i = i0 + rr + g;
+                if (rr + g < rows && GCHK(a.dbg, i, a.m)) {
+                    VT sc = VT(1);
+                    if constexpr (FP8) sc = (VT)__ldg(a.row_scale + i);
+                    const VT u = t * sc - bvec[i];
+                    w = loss_d1<VT>(a.loss, u) * sc;
+                    if (sidx == 0 && wid == (int)(i % RP_CWARPS)) {
+                        VT l0, l1, l2;
+                        loss_eval<VT>(a.loss, u, l0, l1, l2);
                         if (Wout) Wout[i] = l1;
                         if (Dout) Dout[i] = l2;
                         lsum += (double)l0;
                     }
                 }
+#pragma unroll
+                for (int q = 0; q < RB; ++q) wq[q] = __shfl_sync(0xffffffffu, w, q * GS);
             }
         }
         par ^= 1;
