@@ -334,9 +334,12 @@ def run_ours(args):
     status_ok = all(i["status"] == 0 for i in infos)
 
     # roofline of the dominant kernel, the persistent CG kernel (one launch per x-step; each CG
-    # iteration streams A once).  Inside the timed region every launch is timed on the device
-    # (globaltimer of CTA 0, launch start to end); one extra solve with profile = 1 times each
-    # launch with CUDA events on its stream as a cross-check.
+    # iteration streams A once, and so does the gradient pass at the new x that rides on the launch
+    # in the graph form (fused_grad_passes); its algorithmic bytes, A once plus x, b, l', l'' and
+    # the partial sums, are within 0.1 % of an Hessian pass's and are counted as one).  Inside the
+    # timed region every launch is timed on the device (globaltimer of CTA 0, launch start to end);
+    # one extra solve with profile = 1 (the host-driven loop, no fused gradient) times each launch
+    # with CUDA events on its stream as a cross-check.
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
     hv_bytes = infos[0]["hv_bytes"]
@@ -345,9 +348,11 @@ def run_ours(args):
     cg_n = sum(i["cg_launches"] for i in infos)
     hv_ms = sum(i["hv_ms"] for i in infos)
     hv_n = sum(i["hv_launches"] for i in infos)
+    fused = sum(i.get("fused_grad_passes", 0) for i in infos)
     if cg_n:
         it_per_launch = cg_it / cg_n
-        bytes_launch = it_per_launch * hv_bytes
+        passes_per_launch = (cg_it + fused) / cg_n
+        bytes_launch = passes_per_launch * hv_bytes
         avg_ms = cg_ms / cg_n
         achieved = bytes_launch / (avg_ms * 1e-3) / 1e9 if cg_ms > 0 else None
         ev_achieved = ev_avg_us = None
@@ -361,13 +366,15 @@ def run_ours(args):
                 ev_achieved = (ip["cg_iters_total"] * hv_bytes) / (ip["cg_ms"] * 1e-3) / 1e9
         tpi = traffic_record("cgloop_fp32", args.workload) if args.precision == "fp32" else None
         ph = [sum(i["cg_phase_ms"][k] for i in infos) * 1e3 / max(1, cg_it) for k in range(6)]
-        roof = {"bound": "hbm", "kernel": "cgloop_kernel<FP32> (persistent CG, one launch per x-step)",
+        roof = {"bound": "hbm", "kernel": "cgloop_kernel<FP32> (persistent CG, one launch per x-step, with the gradient pass at the new x)",
                 "achieved": achieved, "peak": hbm,
                 "peak_kind": f"{peak_kind} STREAM copy (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                 "unit": "GB/s", "frac": achieved / hbm if achieved else None,
-                "traffic": tpi * it_per_launch if tpi else None,
-                "bytes_per_launch": bytes_launch, "bytes_per_cg_iteration": hv_bytes,
-                "cg_iterations_per_launch": it_per_launch, "avg_launch_us": avg_ms * 1e3, "launches": cg_n,
+                "traffic": tpi * passes_per_launch if tpi else None,
+                "bytes_per_launch": bytes_launch, "bytes_per_pass": hv_bytes,
+                "cg_iterations_per_launch": it_per_launch,
+                "fused_gradient_passes_per_launch": fused / cg_n,
+                "passes_of_A_per_launch": passes_per_launch, "avg_launch_us": avg_ms * 1e3, "launches": cg_n,
                 "timing": "device globaltimer per launch inside the timed region",
                 "achieved_cuda_events": ev_achieved, "avg_launch_us_cuda_events": ev_avg_us,
                 "cuda_events_leg": "one extra solve (profile = 1), events around each persistent CG launch",

@@ -166,6 +166,13 @@ typedef struct genios_options {
                                 plans made for SMs / lanes of the device, largest problems first,
                                 the CG loop as ordinary launches (cooperative launches from several
                                 streams do not overlap); 1: in turn on the context's stream */
+    int32_t fuse_gradient;   /* 1 (default): in the graph form of the device-side loop with the
+                                persistent CG kernel, and when the gradient reads the same matrix
+                                as the Hessian (FP64, FP32), each launch of that kernel goes on
+                                after the z/u update with the gradient pass at the new x, its
+                                finish and the loop's decisions, so that one launch per ADMM
+                                iteration streams A without a break; 0: the gradient pass and its
+                                finish are launches of their own.  Both take the same steps */
 } genios_options;
 
 typedef struct genios_info {
@@ -194,13 +201,15 @@ typedef struct genios_info {
     double grad_ms;          /* their total device time (profile = 1), else 0 */
     double hv_bytes;         /* algorithmic bytes of one Hv launch (A once + vectors) */
     int32_t sketch_rank_used;/* the sketch rank s in use (after the adaptive choice) */
-    int32_t pad0;
+    int32_t fused_grad_passes; /* gradient passes run inside persistent CG launches (fuse_gradient) */
     double sketch_bound;     /* (lam_s + ||E||) / nu of the adaptive choice, NaN when not adaptive */
     int64_t cg_launches;     /* persistent CG launches (persistent_cg = 1), else 0 */
     double cg_ms;            /* their total time: CUDA events around each launch on its stream
                                 (profile = 1), else the device's globaltimer (CTA 0, start to end) */
     double cg_phase_ms[6];   /* the device time of CTA 0 in those launches by phase: Hv pass,
                                 barrier, residual update, barrier, new direction, barrier */
+    double fused_phase_ms[2];/* CTA 0's time in the gradient passes that rode on those launches
+                                (fuse_gradient): the pass with its barriers, and the finish */
 } genios_info;
 
 /* Fill *o with the defaults listed above.  o != NULL. */

@@ -43,6 +43,7 @@ class Options(C.Structure):
         ("box_lo", C.c_double), ("box_hi", C.c_double), ("sketch_adaptive", C.c_int32),
         ("sketch_rank_max", C.c_int32), ("sketch_theta", C.c_double), ("device_loop", C.c_int32),
         ("batch_streams", C.c_int32),
+        ("fuse_gradient", C.c_int32),
     ]
 
 
@@ -55,9 +56,9 @@ class Info(C.Structure):
         ("objective", C.c_double), ("t_setup_ms", C.c_double), ("t_sketch_ms", C.c_double),
         ("t_solve_ms", C.c_double), ("kernel_launches", C.c_int64), ("hv_launches", C.c_int64),
         ("hv_ms", C.c_double), ("grad_launches", C.c_int64), ("grad_ms", C.c_double),
-        ("hv_bytes", C.c_double), ("sketch_rank_used", C.c_int32), ("pad0", C.c_int32),
+        ("hv_bytes", C.c_double), ("sketch_rank_used", C.c_int32), ("fused_grad_passes", C.c_int32),
         ("sketch_bound", C.c_double), ("cg_launches", C.c_int64), ("cg_ms", C.c_double),
-        ("cg_phase_ms", C.c_double * 6),
+        ("cg_phase_ms", C.c_double * 6), ("fused_phase_ms", C.c_double * 2),
     ]
 
     def as_dict(self) -> dict:

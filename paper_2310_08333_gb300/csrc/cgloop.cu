@@ -20,6 +20,7 @@
 // DevState::cg_fault, which makes the other CTAs leave at their next barrier, its producer waits
 // for the copies it issued, and the kernel returns.
 #include "rowpass_core.cuh"
+#include "devloop.cuh"
 
 #include <algorithm>
 
@@ -57,6 +58,7 @@ struct CglShared {
     VT colsum[8][64];
     VT red16[RP_CTHREADS * (16 / sizeof(VT))];   // 16-byte partial sums of the partial-row reduction
     VT sh16[RP_CWARPS];
+    double dsh16[RP_CWARPS];     // csum of float64 values
     VT rz_old, rhs2, rr, rz, alpha, beta, pq;
     unsigned long long t_start, t_mark;
     int64_t j0, r0, nrows;      // the slice and the row block
@@ -498,6 +500,141 @@ GENIOS_DEV void zu_phase(const CgLoopArgs& a, CglShared<VT>& sh) {
     }
 }
 
+// The gradient finish after the fused gradient pass: g = the sum of the CTAs' partial rows plus
+// lambda_2 x, the norms of grad_finish (||g + rho u||^2, ||rho u||^2, ||g||^2,
+// ||(|A^T w| - lambda_1)_+||^2, ||x||_1, ||x||^2, max |A^T w|) and the loss sum, then the loop's
+// decisions (phase a, and phase b when no KKT check is due) and the graph conditionals.  Every
+// value is formed in grad_finish's order, bit for bit: a block of 32 columns (one per lane; the
+// column sum over the CTAs' rows in eight interleaved classes, as column_sum does) ends in the
+// block's butterfly sums; the last CTA to finish sums the blocks as grid_sum_max's
+// last block does (256 threads, block t, t + 256, ... per thread, a butterfly within and across
+// the 8 warps).
+template <typename VT>
+GENIOS_DEV void grad_finish_phase(const CgLoopArgs& a, CglShared<VT>& sh) {
+    __shared__ double gsh[8][8];
+    __shared__ int glast;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int G = gridDim.x;
+    DevLoop* L = a.loop;
+    const double mu = L->lam2, rho = L->rho, lam1 = L->lam1;
+    const VT* P = static_cast<const VT*>(a.rp.partial);
+    const int64_t ldp = a.rp.ldp, n = a.rp.n;
+    const VT* x = static_cast<const VT*>(a.zu_x);
+    const VT* u = static_cast<const VT*>(a.u);
+    VT* g = static_cast<VT*>(a.g_out);
+    const int nblk = (int)((n + 31) / 32);
+    // two blocks of 32 columns at a time per CTA, eight warps each: warp q of a group forms the
+    // column sums of class q (rows q, q + 8, ... in increasing order, loads issued ahead), the
+    // group's first warp adds the classes 0..7 in order and finishes the columns
+    // the class sums [2][8][32] doubles live in the slice buffer, free once the CG solve is over
+    // (4 KB: 1024 floats or half of 1024 doubles), so that the kernel's static shared memory
+    // stays within the device's limit beside the ring
+    static_assert(sizeof(VT) * CGL_SLICE_MAX >= 2 * 8 * 32 * sizeof(double), "slice buffer too small");
+    double (*csh)[8][32] = reinterpret_cast<double (*)[8][32]>(sh.vsl);
+    const int grp = wid >> 3, q = wid & 7;
+    for (int base = blockIdx.x * 2; base < nblk; base += G * 2) {   // uniform over the CTA
+        const int blk = base + grp;
+        const int64_t j = (int64_t)blk * 32 + lane;
+        double accq = 0.0;
+        if (blk < nblk && j < n) {
+            for (int b0 = q; b0 < G; b0 += 64) {
+                VT w[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) w[t] = b0 + 8 * t < G ? __ldcg(P + (int64_t)(b0 + 8 * t) * ldp + j) : VT(0);
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (b0 + 8 * t < G) accq += (double)w[t];
+            }
+        }
+        csh[grp][q][lane] = accq;
+        named_bar_sync(1, RP_CTHREADS);
+        if (q == 0 && blk < nblk) {
+            double v[6] = {0, 0, 0, 0, 0, 0};
+            double mx = 0.0;
+            if (j < n) {
+                double sum = 0.0;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) sum += csh[grp][k][lane];
+                const double xj = (double)x[j];
+                const double gj = fma(mu, xj, sum);
+                g[j] = (VT)gj;
+                const double rhou = __dmul_rn(rho, (double)u[j]);
+                const double rd = __dadd_rn(gj, rhou);
+                const double atw = fabs(sum);
+                const double ex = fmax(atw - lam1, 0.0);
+                v[0] = rd * rd;
+                v[1] = rhou * rhou;
+                v[2] = gj * gj;
+                v[3] = ex * ex;
+                v[4] = fabs(xj);
+                v[5] = xj * xj;
+                mx = atw;
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) v[k] = warp_sum(v[k]);
+            mx = warp_max(mx);
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) a.gf_part[(size_t)blk * 8 + k] = v[k];
+                a.gf_part[(size_t)blk * 8 + 6] = mx;
+            }
+        }
+        named_bar_sync(1, RP_CTHREADS);   // csh is free again
+    }
+    named_bar_sync(1, RP_CTHREADS);
+    if (tid == 0) {
+        __threadfence();
+        glast = atomicAdd(a.bar + 2, 1u) == (unsigned)(G - 1) ? 1 : 0;
+    }
+    named_bar_sync(1, RP_CTHREADS);
+    if (!glast) return;
+    __threadfence();
+    double acc[6] = {0, 0, 0, 0, 0, 0}, am = -1e300, ls = 0.0;
+    if (tid < 256) {
+        for (int bb = tid; bb < nblk; bb += 256) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[k] += __ldcg(a.gf_part + (size_t)bb * 8 + k);
+            am = fmax(am, __ldcg(a.gf_part + (size_t)bb * 8 + 6));
+        }
+        for (int bb = tid; bb < G; bb += 256) ls += __ldcg(a.rg.loss_part + bb);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = warp_sum(acc[k]);
+    am = warp_max(am);
+    ls = warp_sum(ls);
+    if (lane == 0 && wid < 8) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) gsh[k][wid] = acc[k];
+        gsh[6][wid] = am;
+        gsh[7][wid] = ls;
+    }
+    named_bar_sync(1, RP_CTHREADS);
+    if (wid == 0) {
+        double o[8];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o[k] = warp_sum(lane < 8 ? gsh[k][lane] : 0.0);
+        o[6] = warp_max(lane < 8 ? gsh[6][lane] : -1e300);
+        o[7] = warp_sum(lane < 8 ? gsh[7][lane] : 0.0);
+        if (lane == 0) {
+            DevState* S = a.S;
+            S->rd2 = o[0];
+            S->rhou2 = o[1];
+            S->g2 = o[2];
+            S->excess2 = o[3];
+            S->gx1 = o[4];
+            S->gx2 = o[5];
+            S->atw_inf = o[6];
+            S->loss_sum = o[7];
+            loop_phase_a(L, S);
+            if (L->skip_kkt) loop_phase_b(L, S);
+            if (a.use_cond) {
+                cudaGraphSetConditional((cudaGraphConditionalHandle)a.kkt_cond, L->skip_kkt ? 0u : 1u);
+                if (L->skip_kkt) cudaGraphSetConditional((cudaGraphConditionalHandle)a.loop_cond, L->cont ? 1u : 0u);
+            }
+        }
+    }
+}
+
 // CTA 0, thread 0 of a timed launch: adds the time since the last mark to phase k
 template <typename VT>
 GENIOS_DEV void phase_mark(const CgLoopArgs& a, CglShared<VT>& sh, int k) {
@@ -506,6 +643,76 @@ GENIOS_DEV void phase_mark(const CgLoopArgs& a, CglShared<VT>& sh, int k) {
         a.S->cgl_phase_ns[k] += (double)(t - sh.t_mark);
         sh.t_mark = t;
     }
+}
+
+// The fused gradient pass of one CTA (a.grad): stages of the CTA's rows from the ring at
+// v = x, the partial row of A^T l'(A x - b) and the CTA's loss sum.  Sets the producer's stop
+// flag once the pass has taken its stages; false (the same in every consumer thread) on a wait
+// that ran out.
+template <int P, int NCH>
+GENIOS_DEV bool fused_grad_pass(const CgLoopArgs& a, CglShared<typename VType<P>::T>& sh,
+                                             unsigned char* smem, uint64_t* full, uint64_t* empty, int rps,
+                                             int nst_cap, int& cs, int& par) {
+    using AS = AStore<P>;
+    constexpr int VEC = AS::VEC;
+    using VT = typename VType<P>::T;
+    const RowpassArgs& rp = a.rp;
+    const int tid = threadIdx.x, lane = tid & 31, b = blockIdx.x;
+    const int64_t row_bytes = rp.lda * (int64_t)sizeof(typename AS::T);
+    const int64_t stage_bytes = (int64_t)rps * row_bytes;
+    const int nchunk_row = (int)(row_bytes / 16);
+    const int64_t n = rp.n;
+    const VT* xg = static_cast<const VT*>(a.zu_x);
+    VT vr[NCH][VEC], yr[NCH][VEC];
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+        const int c = tid + k * RP_CTHREADS;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            const int64_t j = (int64_t)c * VEC + e;
+            vr[k][e] = (c < nchunk_row && j < n && GCHK(rp.dbg, j, n)) ? __ldcg(xg + j) : VT(0);
+            yr[k][e] = VT(0);
+        }
+    }
+    double lsum = 0.0;
+    VT wt_unused = VT(0);
+    const int nstage_work = sh.nstage_work;
+    const int64_t r0 = sh.r0, nrows = sh.nrows;
+    VT* red = reinterpret_cast<VT*>(empty + nst_cap);
+    bool ok = true;
+    for (int w = 0; w < nstage_work; ++w, ++cs) {
+        const int s = cs % nst_cap;
+        const int use = cs / nst_cap;
+        const bool got = mbar_wait_bounded(&full[s], (uint32_t)(use & 1), rp.wait_limit);
+        if (named_bar_or(2, RP_CTHREADS, !got)) {
+            if (tid == 0) atomicCAS(reinterpret_cast<int*>(&a.S->cg_fault), 0, DERR_TIMEOUT_FULL);
+            ok = false;
+            break;
+        }
+        rp_consume_stage<P, NCH, RP_GRAD>(a.rg, smem, smem + (size_t)s * stage_bytes,
+                                          (int)min((int64_t)rps, nrows - (int64_t)w * rps), r0 + (int64_t)w * rps,
+                                          row_bytes, nchunk_row, rps, red, par, vr, yr, lsum, false, wt_unused);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+    if (tid == 0) *reinterpret_cast<volatile int32_t*>(&sh.stop) = 1;
+    if (!ok) return false;
+    VT* Pout = static_cast<VT*>(rp.partial) + (int64_t)b * rp.ldp;
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+        const int c = tid + k * RP_CTHREADS;
+        if (c < nchunk_row) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const int64_t j = (int64_t)c * VEC + e;
+                if (j < rp.ldp && GCHK(rp.dbg, (long long)b * rp.ldp + j, rp.partial_len)) Pout[j] = yr[k][e];
+            }
+        }
+    }
+    // the rows' loss values sit in the lsum of one lane per row: a fixed-order CTA sum
+    const double ls = csum(lsum, sh.dsh16);
+    if (tid == 0) a.rg.loss_part[b] = ls;
+    return true;
 }
 
 template <int P, int NCH>
@@ -715,8 +922,10 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
         phase_mark(a, sh, 3);
     }
 
-    // ---- the producer stops; the result is in delta
-    if (tid == 0) *reinterpret_cast<volatile int32_t*>(&sh.stop) = 1;
+    // ---- the result is in delta; the producer stops here unless the gradient pass follows
+    // (a.loop->halt was written by an earlier kernel: every CTA reads the same value)
+    const bool gradp = ok && a.grad && a.zu && a.loop != nullptr && a.loop->halt == 0;
+    if (!gradp && tid == 0) *reinterpret_cast<volatile int32_t*>(&sh.stop) = 1;
     if (ok && a.zu) zu_phase<VT>(a, sh);
     // one thread records the final scalars
     if (b == 0 && tid == 0) {
@@ -732,11 +941,31 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
         S->nu = sh.nu;
         S->tol = sh.tol;
         S->cg_max = a.cg_max;
-        if (a.timed) {
+        if (a.timed && !gradp) {
             S->cgl_ns += (double)(gtimer() - sh.t_start);
             S->cgl_count += 1;
             S->cgl_iters += sh.it;
         }
+    }
+    if (!gradp) return;
+
+    // ---- gradient pass at the new x over the CTA's rows (the ring already holds its first
+    // stages), then its finish and the loop's decisions
+    phase_mark(a, sh, 4);   // the final stop test and the z/u update count as direction work
+    bool gok = grid_sync(a, sh);   // x is complete in every slice
+    if (gok) {
+        gok = fused_grad_pass<P, NCH>(a, sh, smem, full, empty, rps, nst_cap, cs, par);
+        if (gok) gok = grid_sync(a, sh);   // every partial row is written
+    } else if (tid == 0) {
+        *reinterpret_cast<volatile int32_t*>(&sh.stop) = 1;
+    }
+    phase_mark(a, sh, 6);
+    if (gok) grad_finish_phase<VT>(a, sh);
+    phase_mark(a, sh, 7);
+    if (b == 0 && tid == 0 && a.timed) {
+        S->cgl_ns += (double)(gtimer() - sh.t_start);
+        S->cgl_count += 1;
+        S->cgl_iters += sh.it;
     }
 }
 
@@ -800,6 +1029,7 @@ CgLoopPlan cgloop_plan(int prec, int64_t m, int64_t n, int64_t lda, int sk) {
 
 size_t cgloop_part_elems(int grid) { return (size_t)grid * (CGL_ST + 2); }
 size_t cgloop_zu_offset_bytes(int grid) { return ((size_t)grid * (CGL_ST + 2) * 8 + 255) & ~size_t(255); }
+size_t cgloop_gf_offset_bytes(int grid) { return cgloop_zu_offset_bytes(grid) + (((size_t)grid * 6 * 8 + 255) & ~size_t(255)); }
 
 template <int P, int NCH>
 static cudaError_t launch_cgl(const CgLoopArgs& a, const RowpassPlan& p, cudaStream_t s) {
@@ -838,7 +1068,12 @@ cudaError_t cgloop_launch(const CgLoopPlan& pl, const CgLoopArgs& c, cudaStream_
     a.rp.mode = RP_HV;
     a.rp.smem_bytes = (long long)pl.rp.smem;
     a.rp.partial_len = (long long)pl.rp.grid * c.rp.ldp;
-    cudaError_t e = cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), s);   // grid barrier, last-CTA count
+    a.rg.smem_bytes = a.rp.smem_bytes;
+    a.rg.partial_len = a.rp.partial_len;
+    if (c.grad && (c.loop == nullptr || !c.zu || c.g_out == nullptr || c.gf_part == nullptr ||
+                   c.rg.b == nullptr || c.rg.loss_part == nullptr))
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(c.bar, 0, 3 * sizeof(unsigned), s);   // grid barrier, last-CTA counts
     if (e != cudaSuccess) return e;
     switch (c.rp.prec) {
         case P_FP64: return dispatch_cgl<P_FP64>(a, pl.rp, s);

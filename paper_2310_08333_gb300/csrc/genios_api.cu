@@ -207,6 +207,7 @@ extern "C" void genios_default_options(genios_options* o) {
     o->sketch_theta = 10.0;
     o->device_loop = 1;
     o->batch_streams = 8;
+    o->fuse_gradient = 1;
 }
 
 extern "C" genios_status genios_create(const genios_options* opts, int device, void* stream,
@@ -475,6 +476,11 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
     ctx->sketch_adapted = false;
     ctx->sketch_bound = NAN;
     ctx->cgl = ctx->opt.persistent_cg ? cgloop_plan(hvp, M, N, ctx->lda, ctx->sk_alloc) : CgLoopPlan{};
+    // When the gradient reads the Hessian's matrix, its own passes split the rows as the
+    // persistent CG kernel does, so that a gradient pass riding on that kernel (fuse_gradient)
+    // forms the same partial sums, bit for bit, and both forms take the same steps.
+    if (ctx->cgl.ok && ctx->A_g == ctx->A_hv && ctx->lda_g == ctx->lda && ctx->gprec == hvp)
+        ctx->plan_g.grid = ctx->cgl.rp.grid;
     const int G = std::max(std::max(ctx->plan_hv.grid, ctx->plan_g.grid), ctx->cgl.ok ? ctx->cgl.rp.grid : 0);
     CK(ctx->mem.get(&ctx->Pbuf, (size_t)G * ctx->ldp * vt));
     CK(ctx->mem.get((void**)&ctx->loss_part, (size_t)G * 8));
@@ -575,11 +581,20 @@ static cudaError_t hv_pass(genios_ctx* ctx, const void* v, const void* d,
 // ctx->delta and the final scalars in DevState (cg_it, rr, rhs2, ...).
 // zu: with the CG solve, the z/u update (x += delta; Eq. (5)) with penalty zu_rho, lambda_1 = zu_lam1
 // and relaxation zu_alpha on ctx->x, ctx->z, ctx->u.
+// The gradient pass can ride on the persistent CG launch when it reads the same matrix as the
+// Hessian passes (FP64, FP32; BF16 and FP8 stream a quantised A for the Hessian and the split
+// planes for the gradient) and the finish's block partials fit the scratch.
+static bool gradient_fusable(const genios_ctx* ctx) {
+    return ctx->opt.fuse_gradient && ctx->cgl.ok && ctx->A_g == ctx->A_hv && ctx->lda_g == ctx->lda &&
+           ctx->gprec == hv_prec(ctx) && ctx->b != nullptr &&
+           cgloop_gf_offset_bytes(ctx->cgl.rp.grid) + (size_t)((ctx->n + 31) / 32) * 64 <= (size_t)262144 * 8;
+}
+
 static cudaError_t cg_persistent(genios_ctx* ctx, const void* d, const void* g, const void* x, const void* z,
                                  void* u, double rho, double u_scale, double nu, double tol, int cg_max, int sk,
                                  const void* mask, bool zu = false, double zu_rho = 1.0, double zu_lam1 = 0.0,
                                  double zu_alpha = 1.0, DevLoop* loop = nullptr, unsigned long long loop_cond = 0,
-                                 int use_cond = 0) {
+                                 int use_cond = 0, bool fuse_grad = false, unsigned long long kkt_cond = 0) {
     CgLoopArgs a{};
     a.rp.prec = hv_prec(ctx);
     a.rp.mode = RP_HV;
@@ -627,6 +642,20 @@ static cudaError_t cg_persistent(genios_ctx* ctx, const void* d, const void* g, 
     a.loop = loop;
     a.loop_cond = loop_cond;
     a.use_cond = use_cond;
+    if (fuse_grad) {   // the gradient pass at the new x over the same stream of A (gradient_fusable)
+        a.grad = 1;
+        a.rg = a.rp;
+        a.rg.mode = RP_GRAD;
+        a.rg.loss = ctx->loss;
+        a.rg.b = ctx->b;
+        a.rg.W_out = ctx->W;
+        a.rg.D_out = ctx->D;
+        a.rg.loss_part = ctx->loss_part;
+        a.g_out = ctx->g;
+        a.gf_part = reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->sc.part) +
+                                              cgloop_gf_offset_bytes(ctx->cgl.rp.grid));
+        a.kkt_cond = kkt_cond;
+    }
     ctx->launches++;
     return cgloop_launch(ctx->cgl, a, ctx->stream);
 }
@@ -821,10 +850,14 @@ static genios_status build_loop_graph(genios_ctx* ctx, const void* dvec, int sk_
     cudaGraph_t ifbody = nullptr;
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
+        // the x-step and z/u update, then the gradient pass at the new x and its finish: in one
+        // launch when the gradient rides on the persistent kernel's stream of A
+        const bool fuse = gradient_fusable(ctx);
         cudaError_t c = cg_persistent(ctx, dvec, ctx->g, ctx->x, ctx->z, ctx->u, 1.0, 1.0, 1.0, 1.0, o.max_cg_iter,
-                                      sk_now, nullptr, /*zu=*/true, 1.0, 0.0, o.alpha, Ld, (unsigned long long)hl, 1);
-        if (c == cudaSuccess) c = grad_pass(ctx, ctx->x, ctx->W, ctx->D, &Ld->halt);
-        if (c == cudaSuccess)
+                                      sk_now, nullptr, /*zu=*/true, 1.0, 0.0, o.alpha, Ld, (unsigned long long)hl, 1,
+                                      fuse, (unsigned long long)hk);
+        if (c == cudaSuccess && !fuse) c = grad_pass(ctx, ctx->x, ctx->W, ctx->D, &Ld->halt);
+        if (c == cudaSuccess && !fuse)
             c = grad_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, ctx->loss_part, ctx->n, ctx->x, ctx->u,
                             0.0, 1.0, 0.0, ctx->g, ctx->S, ctx->sc, cs, Ld, (unsigned long long)hk,
                             (unsigned long long)hl, 1);
@@ -1081,6 +1114,9 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
             for (int guard = 0;; ++guard) {
                 genios_status st = read_state(ctx);
                 if (st != GENIOS_OK) return st;
+                // a wait of the persistent kernel that ran out (with the gradient riding on it, no
+                // finish took the decision to stop)
+                if (ctx->Sh->cg_fault) FAIL(GENIOS_ETIMEOUT, "persistent CG kernel: a bounded device wait ran out");
                 const DevLoop& Lh = ctx->Sh->loop;
                 if (Lh.stop || Lh.last_cg >= o.max_iter) break;
                 if (guard > o.max_iter + 1) FAIL(GENIOS_ESTATE, "ADMM loop graph: no progress");
@@ -1109,8 +1145,10 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
                 if (st != GENIOS_OK) return st;
                 const DevLoop& Lh = ctx->Sh->loop;
                 // kernels run by the graph: per iteration after the first the gradient pass and its
-                // finish, per KKT check two more, and the persistent CG launches
-                ctx->launches += 2 * (int64_t)(Lh.k - 1) + 2 * (Lh.grad_passes - Lh.k) + ctx->Sh->cgl_count;
+                // finish (unless they ride on the persistent CG launch), per KKT check two more, and
+                // the persistent CG launches
+                ctx->launches += (gradient_fusable(ctx) ? 0 : 2 * (int64_t)(Lh.k - 1)) +
+                                 2 * (Lh.grad_passes - Lh.k) + ctx->Sh->cgl_count;
             }
         }
         for (int k = 1; k <= o.max_iter && !graph; ++k) {
@@ -1174,6 +1212,8 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
         }
         inf.hv_launches = inf.cg_iters_total;
         inf.grad_launches = Lh.grad_passes;
+        // every gradient pass at x after the first rode on a persistent CG launch
+        if (graph && gradient_fusable(ctx)) inf.fused_grad_passes = std::max(0, Lh.k - 1);
         inf.r_p = Lh.r_p;
         inf.r_d = Lh.r_d;
         inf.rel_kkt = Lh.rel_kkt;
@@ -1407,6 +1447,7 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
     inf.cg_launches = ctx->Sh->cgl_count;
     inf.cg_ms = o.profile ? cg_ev_ms : ctx->Sh->cgl_ns * 1e-6;
     for (int k = 0; k < 6; ++k) inf.cg_phase_ms[k] = ctx->Sh->cgl_phase_ns[k] * 1e-6;
+    for (int k = 0; k < 2; ++k) inf.fused_phase_ms[k] = ctx->Sh->cgl_phase_ns[6 + k] * 1e-6;
     {
         const size_t es = ctx->prec == GENIOS_FP64 ? 8 : ctx->prec == GENIOS_FP32 ? 4
                           : ctx->prec == GENIOS_BF16 ? 2 : 1;

@@ -90,8 +90,10 @@ struct DevState {
     double cgl_ns;    // accumulated device time of the persistent CG launches (timed)
     int32_t cgl_count, cgl_iters;   // those launches and their CG iterations
     double nys_dots[4];             // adaptive sketch: [v^T E v, ||E v||^2, v^T v] of a power step
-    double cgl_phase_ns[6];         // CTA 0's time by phase: Hv, barrier, update, barrier,
-                                    // direction, barrier
+    double cgl_phase_ns[8];         // CTA 0's time by phase: Hv, barrier, update, barrier,
+                                    // direction, barrier; the fused gradient pass (from the
+                                    // barrier after the z/u update to the one after the pass's
+                                    // partial rows) and the finish
     DevLoop loop;                   // device-side ADMM loop (device_loop = 1)
     double w[256];    // U^T r (Nystrom preconditioner), s <= 256 (op-level preconditioner)
     double cgc[128];  // preconditioner coefficients c_i w_i for the next direction
@@ -201,7 +203,7 @@ struct CgLoopArgs {
     double rho, u_scale, nu, tol;
     int cg_max;
     void* part;                // cgloop_part_elems(grid) value-type partials
-    unsigned* bar;             // [0] grid-barrier counter, [1] last-CTA count (zeroed by cgloop_launch)
+    unsigned* bar;             // [0] grid-barrier counter, [1], [2] last-CTA counts (zeroed by cgloop_launch)
     int zu;                    // 1: after the CG solve, the z/u update of Eq. (5) on zu_x, zu_z, u
     void* zu_x;                // x (x += delta) and z, value type
     void* zu_z;
@@ -216,6 +218,15 @@ struct CgLoopArgs {
                                // and CTA 0 records the iteration in last_cg
     unsigned long long loop_cond;   // use_cond: the WHILE handle of the graph-form loop, cleared at launch
     int use_cond;
+    int grad;                  // 1 (with zu and loop): after the z/u update, the gradient pass at the
+                               // new x over the same rows of rp.A (§3.3), its finish and the loop's
+                               // decisions, in the same launch (the stream of A goes on without a
+                               // break); skipped once the loop has halted
+    RowpassArgs rg;            // grad: the gradient pass (loss, b, W_out, D_out, loss_part); partial
+                               // and ldp are rp's
+    void* g_out;               // grad: g = A^T l'(A x - b) + lambda_2 x (value type)
+    double* gf_part;           // grad: ceil(n / 32) x 8 float64 partials of the finish's norms
+    unsigned long long kkt_cond;   // grad with use_cond: the IF handle of the KKT pass
 };
 // ok = false when the shape does not fit (n > 1024 per SM, s > 128, the split-BF16 stream, or a
 // ring that does not fit one CTA per SM); the caller then uses the per-kernel CG path.
@@ -223,6 +234,8 @@ CgLoopPlan cgloop_plan(int prec, int64_t m, int64_t n, int64_t lda, int sk);
 size_t cgloop_part_elems(int grid);
 // byte offset in the partials buffer where the z/u norm partials start
 size_t cgloop_zu_offset_bytes(int grid);
+// byte offset in the partials buffer where the gradient finish's norm partials start
+size_t cgloop_gf_offset_bytes(int grid);
 cudaError_t cgloop_launch(const CgLoopPlan& pl, const CgLoopArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------

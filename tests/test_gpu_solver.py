@@ -407,8 +407,9 @@ def test_device_wait_timeout_reports_etimeout_and_context_recovers(G):
 
 @pytest.mark.parametrize("case", ["logistic_fp64", "logistic_fp32", "lasso_resid", "huber_maxiter", "lasso_zero"])
 def test_device_loop_takes_the_host_loops_steps(G, case):
-    """The device-side ADMM loop (decisions of §2.1-§2.5 taken on the device, in its graph form and
-    with stream launches, the host syncing only at re-sketches and chunk ends) and the host loop
+    """The device-side ADMM loop (decisions of §2.1-§2.5 taken on the device, in its graph form with
+    and without the gradient pass fused into the persistent CG launch, and with stream launches,
+    the host syncing only at re-sketches and chunk ends) and the host loop
     (device state read after every gradient pass) take the same iterations: same iteration and
     CG counts, penalty changes, stop status and z, for the KKT and residual stop rules, a
     re-sketching loss, a quadratic one (no re-sketch: chunk syncs only), a solve cut off by
@@ -432,18 +433,25 @@ def test_device_loop_takes_the_host_loops_steps(G, case):
         lam = 1.01 * lmax if case == "lasso_zero" else 0.1 * lmax
         kw = dict(stop_rule=G.STOP_RESID | G.STOP_KKT, eps_rel=1e-6, eps_abs=1e-8) if case == "lasso_resid" else {}
     zh, ihost, _ = gpu_solve(G, P, prec, lam, device_loop=0, **kw)
-    # the graph form (WHILE node over the iteration, IF node for the KKT pass) and the same
-    # decisions with stream launches
-    for graphs in (1, 0):
-        zd, idev, _ = gpu_solve(G, P, prec, lam, device_loop=1, use_graphs=graphs, **kw)
-        print(case, graphs, {k: (idev[k], ihost[k]) for k in ("iters", "cg_iters_total", "rho_updates", "status", "grad_launches")})
+    # the graph form (WHILE node over the iteration, IF node for the KKT pass), with the gradient
+    # pass riding on the persistent CG launch (the default: one launch per iteration) and as
+    # launches of its own, and the same decisions with stream launches
+    for graphs, fuse in ((1, 1), (1, 0), (0, 1)):
+        zd, idev, _ = gpu_solve(G, P, prec, lam, device_loop=1, use_graphs=graphs, fuse_gradient=fuse, **kw)
+        print(case, graphs, fuse, {k: (idev[k], ihost[k]) for k in ("iters", "cg_iters_total", "rho_updates", "status", "grad_launches")})
+        # FP64 and FP32 read the same matrix for the gradient and the Hessian: the graph form
+        # then runs every gradient pass after the first inside the persistent launch
+        if graphs == 1 and fuse == 1:
+            assert idev["iters"] <= 3 or idev["fused_grad_passes"] > 0, idev["fused_grad_passes"]
+        else:
+            assert idev["fused_grad_passes"] == 0, idev["fused_grad_passes"]
         for k in ("status", "iters", "cg_iters_total", "rho_updates", "sketches", "grad_launches", "nnz"):
-            assert idev[k] == ihost[k], (graphs, k, idev[k], ihost[k])
+            assert idev[k] == ihost[k], (graphs, fuse, k, idev[k], ihost[k])
         assert idev["rho"] == ihost["rho"]
         np.testing.assert_allclose(zd, zh, rtol=0, atol=1e-12 * max(1.0, np.max(np.abs(zh))))
         for k in ("rel_kkt", "r_p", "r_d", "objective"):
             a, b_ = idev[k], ihost[k]
-            assert (np.isnan(a) and np.isnan(b_)) or a == pytest.approx(b_, rel=1e-12, abs=1e-300), (graphs, k, a, b_)
+            assert (np.isnan(a) and np.isnan(b_)) or a == pytest.approx(b_, rel=1e-12, abs=1e-300), (graphs, fuse, k, a, b_)
         if case == "huber_maxiter":
             assert idev["status"] == 5 and idev["iters"] == 23        # GENIOS_EMAXITER
         if case == "lasso_zero":
