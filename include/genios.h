@@ -166,8 +166,8 @@ typedef struct genios_options {
                                 plans made for SMs / lanes of the device, largest problems first,
                                 the CG loop as ordinary launches (cooperative launches from several
                                 streams do not overlap); 1: in turn on the context's stream */
-    int32_t fuse_gradient;   /* 1 (default): in the graph form of the device-side loop with the
-                                persistent CG kernel, and when the gradient reads the same matrix
+    int32_t fuse_gradient;   /* 1 (default): in the device-side loop (graph or stream form) with
+                                the persistent CG kernel, and when the gradient reads the same matrix
                                 as the Hessian (FP64, FP32), each launch of that kernel goes on
                                 after the z/u update with the gradient pass at the new x, its
                                 finish and the loop's decisions, so that one launch per ADMM

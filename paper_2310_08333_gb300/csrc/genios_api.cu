@@ -1151,12 +1151,16 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
                                  2 * (Lh.grad_passes - Lh.k) + ctx->Sh->cgl_count;
             }
         }
+        const bool fuse_stream = gradient_fusable(ctx);
         for (int k = 1; k <= o.max_iter && !graph; ++k) {
-            // gradient pass at x^k (§3.3), then the residual and KKT-schedule decisions
-            CK(grad_pass(ctx, ctx->x, ctx->W, ctx->D, &Ld->halt));
-            CK(grad_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, ctx->loss_part, n, ctx->x,
-                           ctx->u, lam2, rho, lam1, ctx->g, ctx->S, ctx->sc, s, Ld));
-            ctx->launches++;
+            // gradient pass at x^k (§3.3), then the residual and KKT-schedule decisions (after
+            // the first iteration they rode on the previous persistent launch when fused)
+            if (k == 1 || !fuse_stream) {
+                CK(grad_pass(ctx, ctx->x, ctx->W, ctx->D, &Ld->halt));
+                CK(grad_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, ctx->loss_part, n, ctx->x,
+                               ctx->u, lam2, rho, lam1, ctx->g, ctx->S, ctx->sc, s, Ld));
+                ctx->launches++;
+            }
             if (kkt_rule) {   // relative KKT at z, run only when due (reading R21)
                 CK(grad_pass(ctx, ctx->z, nullptr, nullptr, &Ld->skip_kkt));
                 CK(kkt_finish(ctx->dbl, ctx->Pbuf, ctx->plan_g.grid, ctx->ldp, n, ctx->z, lam2, lam1,
@@ -1183,7 +1187,8 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
             // x-step (§2.1) and z/u update (Eq. (5)) in one persistent launch, parameters from Ld
             const int sk_now = use_pc && ctx->have_precond ? ctx->sk : 0;
             CK(cg_persistent(ctx, dvec, ctx->g, ctx->x, ctx->z, ctx->u, rho, 1.0, rho + lam2 + o.sigma, floor,
-                             o.max_cg_iter, sk_now, nullptr, /*zu=*/true, rho, lam1, o.alpha, Ld));
+                             o.max_cg_iter, sk_now, nullptr, /*zu=*/true, rho, lam1, o.alpha, Ld, 0, 0,
+                             fuse_stream));
             if (++since >= chunk && k < o.max_iter) {
                 genios_status st = read_state(ctx);
                 if (st != GENIOS_OK) return st;
@@ -1213,7 +1218,7 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
         inf.hv_launches = inf.cg_iters_total;
         inf.grad_launches = Lh.grad_passes;
         // every gradient pass at x after the first rode on a persistent CG launch
-        if (graph && gradient_fusable(ctx)) inf.fused_grad_passes = std::max(0, Lh.k - 1);
+        if (gradient_fusable(ctx)) inf.fused_grad_passes = std::max(0, Lh.k - 1);
         inf.r_p = Lh.r_p;
         inf.r_d = Lh.r_d;
         inf.rel_kkt = Lh.rel_kkt;
