@@ -924,7 +924,11 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
 
     // ---- the result is in delta; the producer stops here unless the gradient pass follows
     // (a.loop->halt was written by an earlier kernel: every CTA reads the same value)
-    const bool gradp = ok && a.grad && a.zu && a.loop != nullptr && a.loop->halt == 0;
+    // (only the FP64 and FP32 instantiations carry the gradient pass: the quantised Hessian
+    // streams of BF16 and FP8 are not the gradient's matrix, and leaving it out keeps their
+    // register allocation as it was)
+    constexpr bool kGradCapable = (P == P_FP32 || P == P_FP64);
+    const bool gradp = kGradCapable && ok && a.grad && a.zu && a.loop != nullptr && a.loop->halt == 0;
     if (!gradp && tid == 0) *reinterpret_cast<volatile int32_t*>(&sh.stop) = 1;
     if (ok && a.zu) zu_phase<VT>(a, sh);
     // one thread records the final scalars
@@ -952,16 +956,18 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
     // ---- gradient pass at the new x over the CTA's rows (the ring already holds its first
     // stages), then its finish and the loop's decisions
     phase_mark(a, sh, 4);   // the final stop test and the z/u update count as direction work
-    bool gok = grid_sync(a, sh);   // x is complete in every slice
-    if (gok) {
-        gok = fused_grad_pass<P, NCH>(a, sh, smem, full, empty, rps, nst_cap, cs, par);
-        if (gok) gok = grid_sync(a, sh);   // every partial row is written
-    } else if (tid == 0) {
-        *reinterpret_cast<volatile int32_t*>(&sh.stop) = 1;
+    if constexpr (kGradCapable) {
+        bool gok = grid_sync(a, sh);   // x is complete in every slice
+        if (gok) {
+            gok = fused_grad_pass<P, NCH>(a, sh, smem, full, empty, rps, nst_cap, cs, par);
+            if (gok) gok = grid_sync(a, sh);   // every partial row is written
+        } else if (tid == 0) {
+            *reinterpret_cast<volatile int32_t*>(&sh.stop) = 1;
+        }
+        phase_mark(a, sh, 6);
+        if (gok) grad_finish_phase<VT>(a, sh);
+        phase_mark(a, sh, 7);
     }
-    phase_mark(a, sh, 6);
-    if (gok) grad_finish_phase<VT>(a, sh);
-    phase_mark(a, sh, 7);
     if (b == 0 && tid == 0 && a.timed) {
         S->cgl_ns += (double)(gtimer() - sh.t_start);
         S->cgl_count += 1;
