@@ -177,7 +177,8 @@ def oracle_leg(P, lam: float, rho: float, z, iters: int, sample_iters: int = 2) 
       * value: seconds to the stop rule on this workload for the oracle's exact-solve ADMM =
         (seconds per iteration, timed at full size over `sample_iters` iterations) x `iters`, the
         ADMM iteration count of this run (the count does not depend on how accurately the
-        x-step is solved: CG floors from 1e-6 to 1e-2 take the same count on this workload)."""
+        x-step is solved: CG floors from 1e-2 to 0.8 take the same count on this workload, and the
+        oracle's exact-solve ADMM run to the end stops at the same iteration)."""
     from oracle import checks
     kkt = checks.rel_kkt(P.A, P.b, z, P.loss, lam, P.mu)
     ts = [oracle_iteration_seconds(P, lam, rho) for _ in range(sample_iters)]
