@@ -247,7 +247,10 @@ genios_status genios_lambda_max(genios_ctx* ctx, double* out);
  * out_dtype (F64 or F32), host or device, receiving the K solutions z back to back (K * n
  * elements for a shared data set, sum of n_k for independent ones; exact zeros off the
  * support).  info: host array of K structs or NULL.  warm_start: 1 reuses x, z, u, rho of the
- * previous solve on this context.  A shared data set solves its K problems in the order given,
+ * previous solve on this context and, for a loss whose curvature depends on x (logistic,
+ * Huber), its Nystrom preconditioner; 0 starts from zero and sketches at the solve's first
+ * iterate (the squared loss's sketch depends on the data only and is kept across solves).
+ * A shared data set solves its K problems in the order given,
  * each started from the previous solution (pass lambda_1 decreasing for a path) and sharing the
  * Nystrom sketch when loss'' is constant.  Returns GENIOS_OK when every problem met the stop
  * rule, GENIOS_EMAXITER (iterates still written) if one did not. */

@@ -1042,6 +1042,10 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
         CK(cudaMemsetAsync(ctx->z, 0, vbytes, s));
         CK(cudaMemsetAsync(ctx->u, 0, vbytes, s));
         ctx->rho = o.rho;
+        // a cold solve builds its own preconditioner at its first iterate when the curvature
+        // depends on x (the squared loss's depends on the data only, and its sketch is kept);
+        // the eigensolver may still start from the previous eigenvectors
+        if (ctx->loss != GENIOS_LOSS_SQUARED) ctx->have_precond = false;
     }
     CK(cudaMemsetAsync(ctx->S, 0, offsetof(DevState, w), s));
     double rho = ctx->rho;

@@ -16,7 +16,7 @@ from oracle import admm as oadmm, checks  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-BENCH_RHO = 240.0   # fixed penalty of the 20000 x 8000 logistic workload (with the CG floor 0.2)
+BENCH_RHO = 240.0   # fixed penalty of the 20000 x 8000 logistic workload (with the CG floor 0.8)
 
 
 @pytest.fixture(scope="module")
@@ -295,6 +295,29 @@ def test_warm_start_reuses_state(G):
     assert np.linalg.norm(z2 - z3) <= 1e-4 * np.linalg.norm(z3)
 
 
+def test_cold_solve_builds_its_own_preconditioner(G):
+    """A cold solve (warm_start = 0) of a logistic problem sketches at its own first iterate: a
+    second cold solve on the same context takes the steps of a first solve on a fresh context
+    (same sketches, iterations and CG iterations, the same z up to the eigensolver's tolerance,
+    whose warm start from the previous eigenvectors is all that carries over)."""
+    P = problems.logistic_lowrank(2000, 800, nnz=20, sketch_rank=40, seed=problems.seed_for(3, 12))
+    A = torch.from_numpy(P.A).to("cuda", torch.float32)
+    b = torch.from_numpy(P.b).to("cuda", torch.float32)
+    kw = dict(precision=1, stop_rule=G.STOP_KKT, eps_kkt=1e-5, sketch_rank=40, rho=30.0, resketch_every=20)
+    with G.Solver(**kw) as s:
+        s.set_data(A, b, "logistic")
+        lam = P.lam_frac * s.lambda_max()
+        z1, i1 = s.solve(lam)
+        z2, i2 = s.solve(lam)
+    with G.Solver(**kw) as s:
+        s.set_data(A, b, "logistic")
+        z0, i0 = s.solve(lam)
+    for k in ("status", "iters", "sketches"):
+        assert i2[k] == i0[k] == i1[k], (k, i0[k], i1[k], i2[k])
+    assert abs(i2["cg_iters_total"] - i0["cg_iters_total"]) <= 2, (i2["cg_iters_total"], i0["cg_iters_total"])
+    assert np.linalg.norm(z2 - z0) <= 1e-4 * np.linalg.norm(z0)
+
+
 def test_host_buffers_and_errors(G):
     P = problems.lasso_iid(100, 300, nnz=5, seed=12)
     with G.Solver(precision=1) as s:
@@ -326,7 +349,7 @@ def test_mixed_precision_reaches_kkt_and_reports_error(G, prec):
 
 def test_config3_full_size_kkt_property(G):
     """Full 20000 x 8000 logistic workload in the benchmark's configuration (FP32, rho = 240 held
-    fixed, CG floor 0.2, rank 100 re-sketched every 80 iterations, KKT checks at most 80 apart,
+    fixed, CG floor 0.8, rank 100 re-sketched every 60 iterations, KKT checks at most 80 apart,
     stop at a 1e-4 relative KKT residual): the oracle cannot run its exact solve here
     in seconds, so it certifies the GPU's z by the float64 optimality conditions, which hold at
     any size: its relative KKT residual at z meets the tolerance the GPU stopped on (to float32
@@ -334,7 +357,7 @@ def test_config3_full_size_kkt_property(G):
     P = problems.logistic_lowrank()
     A32 = P.A.astype(np.float32)
     z, info, lmax = gpu_solve(G, P, 1, P.lam_frac * checks.lambda_max(A32.astype(np.float64), P.b, "logistic"),
-                              rho=BENCH_RHO, rho_update_every=0, cg_tol_floor=0.2, resketch_every=80, kkt_check_every=80,
+                              rho=BENCH_RHO, rho_update_every=0, cg_tol_floor=0.8, resketch_every=60, kkt_check_every=80,
                               eps_kkt=1e-4, max_iter=12000)
     A = A32.astype(np.float64)
     lam = info["lambda1"]
