@@ -374,7 +374,9 @@ def run_ours(args):
                 ev_achieved = (ip["cg_iters_total"] * hv_bytes) / (ip["cg_ms"] * 1e-3) / 1e9
         tpi = traffic_record("cgloop_fp32", args.workload) if args.precision == "fp32" else None
         ph = [sum(i["cg_phase_ms"][k] for i in infos) * 1e3 / max(1, cg_it) for k in range(6)]
-        roof = {"bound": "hbm", "kernel": "cgloop_kernel<FP32> (persistent CG, one launch per x-step, with the gradient pass at the new x)",
+        kdesc = (f"cgloop_kernel<{args.precision.upper()}> (persistent CG, one launch per x-step"
+                 + (", with the gradient pass at the new x)" if fused else ")"))
+        roof = {"bound": "hbm", "kernel": kdesc,
                 "achieved": achieved, "peak": hbm,
                 "peak_kind": f"{peak_kind} STREAM copy (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                 "unit": "GB/s", "frac": achieved / hbm if achieved else None,

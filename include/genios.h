@@ -59,9 +59,9 @@ typedef enum { GENIOS_LOSS_SQUARED = 0, GENIOS_LOSS_LOGISTIC = 1, GENIOS_LOSS_HU
 /* Precision in which A is stored and streamed by the Hessian-vector products.
  *   FP64: A and all vectors in float64.
  *   FP32: A and vectors in float32 (scalar reductions in float64).
- *   BF16: Hv streams a bfloat16 copy of A; the gradient / residual pass streams the split
- *         hi + lo bfloat16 pair (a ~= hi + lo) with float32 arithmetic.
- *   FP8_E4M3: Hv streams E4M3 codes with a float32 scale per row; gradient as BF16. */
+ *   BF16: Hv streams a bfloat16 copy of A (round to nearest); the gradient / residual pass
+ *         streams the float32 A, so that the fixed point is the problem's own.
+ *   FP8_E4M3: Hv streams E4M3 codes with a float32 scale per row; the gradient as in BF16. */
 typedef enum {
     GENIOS_FP64 = 0,
     GENIOS_FP32 = 1,

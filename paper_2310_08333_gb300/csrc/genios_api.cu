@@ -88,7 +88,7 @@ struct genios_ctx {
     int loss = 0;
     int64_t m = 0, n = 0;
     int prec = P_FP32;   // Hv storage precision
-    int gprec = P_FP32;  // gradient-pass storage precision (P_FP64, P_FP32, P_HILO)
+    int gprec = P_FP32;  // gradient-pass storage precision (P_FP64 or P_FP32; BF16 / FP8 modes keep the float32 A)
     bool dbl = false;
     size_t vt = 4;
     int64_t lda = 0, lda_g = 0, ldp = 0;
@@ -245,7 +245,7 @@ extern "C" genios_status genios_create(const genios_options* opts, int device, v
     ctx->prec = o.precision;
     ctx->dbl = (o.precision == GENIOS_FP64);
     ctx->vt = ctx->dbl ? 8 : 4;
-    ctx->gprec = o.precision == GENIOS_FP64 ? P_FP64 : o.precision == GENIOS_FP32 ? P_FP32 : P_HILO;
+    ctx->gprec = o.precision == GENIOS_FP64 ? P_FP64 : P_FP32;   // BF16 / FP8: the float32 A
     if (cudaMalloc(&ctx->S, sizeof(DevState)) != cudaSuccess ||
         cudaMallocHost(&ctx->Sh, sizeof(DevState)) != cudaSuccess ||
         cudaMalloc(&ctx->sc.part, 262144 * sizeof(double)) != cudaSuccess ||
@@ -430,13 +430,18 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
             ctx->lda_g = ld32;
             CK(tc_setup(ctx, P_FP32, A32, ld32, nullptr, M, N));
         } else {
-            ctx->lda_g = padded_lda(P_BF16, N);
-            CK(ctx->mem.get(&ctx->A_g, (size_t)M * ctx->lda_g * 2));
-            CK(ctx->mem.get(&ctx->A_glo, (size_t)M * ctx->lda_g * 2));
-            CK(quantize_bf16_hilo(M, N, A32, ld32, ctx->A_g, ctx->A_glo, ctx->lda_g, s));
+            // The gradient streams the float32 matrix itself (the problem's own A, and the
+            // cheapest row pass to decode); the Hessian streams the quantised copy
+            ctx->A_g = A32;
+            ctx->lda_g = ld32;
             if (ctx->prec == GENIOS_BF16) {
-                ctx->A_hv = ctx->A_g;  // the hi part is the BF16 copy
-                ctx->lda = ctx->lda_g;
+                ctx->lda = padded_lda(P_BF16, N);
+                void* lo = nullptr;   // the low half of the split is not kept
+                CK(ctx->mem.get(&ctx->A_hv, (size_t)M * ctx->lda * 2));
+                CK(ctx->mem.get(&lo, (size_t)M * ctx->lda * 2));
+                CK(quantize_bf16_hilo(M, N, A32, ld32, ctx->A_hv, lo, ctx->lda, s));
+                CK(cudaStreamSynchronize(s));
+                ctx->mem.release(lo);
             } else {
                 ctx->lda = padded_lda(P_FP8, N);
                 CK(ctx->mem.get(&ctx->A_hv, (size_t)M * ctx->lda));
@@ -445,8 +450,6 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
                                      ctx->lda, s));
             }
             CK(tc_setup(ctx, P_FP32, A32, ld32, nullptr, M, N));
-            CK(cudaStreamSynchronize(s));
-            ctx->mem.release(A32);
         }
     }
     // b in the value type

@@ -314,7 +314,10 @@ def test_cold_solve_builds_its_own_preconditioner(G):
         z0, i0 = s.solve(lam)
     for k in ("status", "iters", "sketches"):
         assert i2[k] == i0[k] == i1[k], (k, i0[k], i1[k], i2[k])
-    assert abs(i2["cg_iters_total"] - i0["cg_iters_total"]) <= 2, (i2["cg_iters_total"], i0["cg_iters_total"])
+    # the eigenvectors' warm start moves the preconditioner within the eigensolver's tolerance,
+    # which moves a CG stopping test by an iteration here and there over the whole solve
+    assert abs(i2["cg_iters_total"] - i0["cg_iters_total"]) <= 0.005 * i0["cg_iters_total"] + 2, \
+        (i2["cg_iters_total"], i0["cg_iters_total"])
     assert np.linalg.norm(z2 - z0) <= 1e-4 * np.linalg.norm(z0)
 
 
