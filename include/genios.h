@@ -210,6 +210,14 @@ typedef struct genios_info {
                                 barrier, residual update, barrier, new direction, barrier */
     double fused_phase_ms[2];/* CTA 0's time in the gradient passes that rode on those launches
                                 (fuse_gradient): the pass with its barriers, and the finish */
+    double cg_span_ms;       /* those launches (fuse_gradient) from CTA 0's first instruction to
+                                the end of the last CTA's finish (device globaltimer) */
+    double cg_gap_ms;        /* the device time between one such launch's end and the next one's
+                                first instruction, within one run of the device-side loop: launch,
+                                graph-node and kernel set-up overhead */
+    double cg_tail_ms[4];    /* the finish of those launches in the last CTA to arrive: from the
+                                previous mark (CTA 0's end of the pass barrier) to its arrival, its
+                                reductions, the loop's decisions, the graph conditionals */
 } genios_info;
 
 /* Fill *o with the defaults listed above.  o != NULL. */
@@ -233,8 +241,8 @@ genios_status genios_create(const genios_options* opts, int device, void* stream
  * Size limits: each thread of the fused row pass keeps its slice of an n-vector in registers,
  * and a CTA's shared-memory ring holds at least two stages of rows, so n <= 8192 in
  * GENIOS_FP64, n <= 20480 in GENIOS_FP32 and n <= 28096 in GENIOS_BF16 and GENIOS_FP8_E4M3
- * (their gradient pass streams a row's bf16 hi and lo planes together); a larger n returns
- * GENIOS_EUNSUPPORTED.  m is limited only by device memory. */
+ * (up to n = 20480 their gradient pass streams the float32 A, beyond it a bf16 hi + lo split of
+ * A whose two planes it reads together); a larger n returns GENIOS_EUNSUPPORTED.  m is limited only by device memory. */
 genios_status genios_set_data(genios_ctx* ctx, int loss, int K, const int64_t* m, const int64_t* n,
                               const void* const* A, int A_dtype, const int64_t* lda,
                               const void* const* b, int shared_A);

@@ -59,6 +59,7 @@ class Info(C.Structure):
         ("hv_bytes", C.c_double), ("sketch_rank_used", C.c_int32), ("fused_grad_passes", C.c_int32),
         ("sketch_bound", C.c_double), ("cg_launches", C.c_int64), ("cg_ms", C.c_double),
         ("cg_phase_ms", C.c_double * 6), ("fused_phase_ms", C.c_double * 2),
+        ("cg_span_ms", C.c_double), ("cg_gap_ms", C.c_double), ("cg_tail_ms", C.c_double * 4),
     ]
 
     def as_dict(self) -> dict:

@@ -511,12 +511,14 @@ GENIOS_DEV void zu_phase(const CgLoopArgs& a, CglShared<VT>& sh) {
 // the 8 warps).
 template <typename VT>
 GENIOS_DEV void grad_finish_phase(const CgLoopArgs& a, CglShared<VT>& sh) {
-    __shared__ double gsh[8][8];
     __shared__ int glast;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int G = gridDim.x;
     DevLoop* L = a.loop;
     const double mu = L->lam2, rho = L->rho, lam1 = L->lam1;
+    // k^gamma for the decisions (phase a makes this iteration k + 1), read now: its latency hides
+    // behind the column sums
+    const double kpow_next = tid == 0 ? loop_kpow(L, L->k + 1) : 0.0;
     const VT* P = static_cast<const VT*>(a.rp.partial);
     const int64_t ldp = a.rp.ldp, n = a.rp.n;
     const VT* x = static_cast<const VT*>(a.zu_x);
@@ -589,6 +591,9 @@ GENIOS_DEV void grad_finish_phase(const CgLoopArgs& a, CglShared<VT>& sh) {
     named_bar_sync(1, RP_CTHREADS);
     if (!glast) return;
     __threadfence();
+    unsigned long long tm[4];
+    if (a.timed && tid == 0) tm[0] = gtimer();
+    __shared__ double gsh[8][8];
     double acc[6] = {0, 0, 0, 0, 0, 0}, am = -1e300, ls = 0.0;
     if (tid < 256) {
         for (int bb = tid; bb < nblk; bb += 256) {
@@ -609,29 +614,49 @@ GENIOS_DEV void grad_finish_phase(const CgLoopArgs& a, CglShared<VT>& sh) {
         gsh[7][wid] = ls;
     }
     named_bar_sync(1, RP_CTHREADS);
+    double o[8];
     if (wid == 0) {
-        double o[8];
 #pragma unroll
         for (int k = 0; k < 6; ++k) o[k] = warp_sum(lane < 8 ? gsh[k][lane] : 0.0);
         o[6] = warp_max(lane < 8 ? gsh[6][lane] : -1e300);
         o[7] = warp_sum(lane < 8 ? gsh[7][lane] : 0.0);
-        if (lane == 0) {
-            DevState* S = a.S;
-            S->rd2 = o[0];
-            S->rhou2 = o[1];
-            S->g2 = o[2];
-            S->excess2 = o[3];
-            S->gx1 = o[4];
-            S->gx2 = o[5];
-            S->atw_inf = o[6];
-            S->loss_sum = o[7];
-            loop_phase_a(L, S);
-            if (L->skip_kkt) loop_phase_b(L, S);
-            if (a.use_cond) {
-                cudaGraphSetConditional((cudaGraphConditionalHandle)a.kkt_cond, L->skip_kkt ? 0u : 1u);
-                if (L->skip_kkt) cudaGraphSetConditional((cudaGraphConditionalHandle)a.loop_cond, L->cont ? 1u : 0u);
+    }
+    // the loop's decisions on a shared copy of the state's head (the slice buffer is free here)
+    static_assert(sizeof(VT) * CGL_SLICE_MAX >= kStateHeadBytes, "slice buffer too small for the state head");
+    DevState* S = a.S;
+    if (a.timed && tid == 0) tm[1] = gtimer();
+    loop_decide_shared(
+        S, reinterpret_cast<unsigned long long*>(sh.vsl), tid, RP_CTHREADS, [] { named_bar_sync(1, RP_CTHREADS); },
+        [&](DevState* Ss) {   // the totals, into the copy and the state
+            for (DevState* T : {Ss, S}) {
+                T->rd2 = o[0];
+                T->rhou2 = o[1];
+                T->g2 = o[2];
+                T->excess2 = o[3];
+                T->gx1 = o[4];
+                T->gx2 = o[5];
+                T->atw_inf = o[6];
+                T->loss_sum = o[7];
             }
-        }
+        },
+        [&](DevLoop* Lc, DevState* Ss) {
+            loop_phase_a(Lc, Ss);
+            if (Lc->skip_kkt) loop_phase_b(Lc, Ss, kpow_next);
+            if (a.timed) tm[2] = gtimer();
+            if (a.use_cond) {
+                cudaGraphSetConditional((cudaGraphConditionalHandle)a.kkt_cond, Lc->skip_kkt ? 0u : 1u);
+                if (Lc->skip_kkt) cudaGraphSetConditional((cudaGraphConditionalHandle)a.loop_cond, Lc->cont ? 1u : 0u);
+            }
+        });
+    if (a.timed && tid == 0) {   // the launch's last work: its span, and the start of the next gap
+        const unsigned long long t = gtimer();
+        const unsigned long long f0 = __ldcg(&S->cgl_fin0);
+        S->cgl_tail_ns[0] += tm[0] > f0 ? (double)(tm[0] - f0) : 0.0;
+        S->cgl_tail_ns[1] += (double)(tm[1] - tm[0]);
+        S->cgl_tail_ns[2] += (double)(tm[2] - tm[1]);
+        S->cgl_tail_ns[3] += (double)(t - tm[2]);
+        S->cgl_span_ns += (double)(t - S->cgl_t0);
+        S->cgl_last_end = t;
     }
 }
 
@@ -715,6 +740,32 @@ GENIOS_DEV bool fused_grad_pass(const CgLoopArgs& a, CglShared<typename VType<P>
     return true;
 }
 
+// Thread 0 of each CTA, before the x-step: its parameters (from the device-side loop's state when
+// there is one) and a fresh CG state.
+template <typename VT>
+GENIOS_DEV void xstep_begin(const CgLoopArgs& a, CglShared<VT>& sh) {
+    if (a.loop != nullptr) {
+        const DevLoop* L = a.loop;
+        sh.rho = __ldcg(&L->rho);
+        sh.u_scale = __ldcg(&L->u_scale);
+        sh.nu = __ldcg(&L->nu);
+        sh.tol = __ldcg(&L->tol);
+        sh.zu_rho = sh.rho;
+        sh.zu_lam1 = __ldcg(&L->lam1);
+        if (blockIdx.x == 0) a.loop->last_cg = __ldcg(&L->k);
+    } else {
+        sh.rho = a.rho;
+        sh.u_scale = a.u_scale;
+        sh.nu = a.nu;
+        sh.tol = a.tol;
+        sh.zu_rho = a.zu_rho;
+        sh.zu_lam1 = a.zu_lam1;
+    }
+    sh.it = 0;
+    sh.start = 1;
+    sh.rz_old = sh.rhs2 = sh.rr = sh.rz = sh.alpha = sh.beta = sh.pq = VT(0);
+}
+
 template <int P, int NCH>
 __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs a, const int rps, const int nst_cap) {
     using AS = AStore<P>;
@@ -740,22 +791,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
     // earlier kernel in the stream, so every CTA reads the same value)
     if (a.loop != nullptr && a.loop->stop != 0) return;
     if (tid == 0) {
-        if (a.loop != nullptr) {
-            sh.rho = a.loop->rho;
-            sh.u_scale = a.loop->u_scale;
-            sh.nu = a.loop->nu;
-            sh.tol = a.loop->tol;
-            sh.zu_rho = a.loop->rho;
-            sh.zu_lam1 = a.loop->lam1;
-            if (b == 0) a.loop->last_cg = a.loop->k;
-        } else {
-            sh.rho = a.rho;
-            sh.u_scale = a.u_scale;
-            sh.nu = a.nu;
-            sh.tol = a.tol;
-            sh.zu_rho = a.zu_rho;
-            sh.zu_lam1 = a.zu_lam1;
-        }
+        xstep_begin<VT>(a, sh);
         for (int s = 0; s < nst_cap; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], RP_CWARPS);
@@ -768,17 +804,17 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
         const int64_t j0 = rp.n * b / G, j1 = rp.n * (b + 1) / G;
         sh.j0 = j0;
         sh.ns = (int)(j1 - j0);
-        sh.it = 0;
-        sh.start = 1;
         sh.epoch = 0;
         sh.stop = 0;
-        sh.rz_old = sh.rhs2 = sh.rr = sh.rz = sh.alpha = sh.beta = sh.pq = VT(0);
         sh.t_start = 0ull;
         if (a.timed && b == 0) {   // before this CTA's first arrival: no H phase has begun
             sh.t_start = gtimer();
             sh.t_mark = sh.t_start;
             S->hv_t0 = ~0ull;
             S->hv_t1 = 0ull;
+            S->cgl_t0 = sh.t_start;
+            const unsigned long long prev = S->cgl_last_end;
+            if (prev != 0ull && sh.t_start > prev) S->cgl_gap_ns += (double)(sh.t_start - prev);
         }
     }
     for (int i = tid; i < 128; i += RP_THREADS) sh.lamsh[i] = i < a.sk ? (VT)a.lam[i] : VT(0);
@@ -945,33 +981,29 @@ __global__ void __launch_bounds__(RP_THREADS, 1) cgloop_kernel(const CgLoopArgs 
         S->nu = sh.nu;
         S->tol = sh.tol;
         S->cg_max = a.cg_max;
-        if (a.timed && !gradp) {
-            S->cgl_ns += (double)(gtimer() - sh.t_start);
-            S->cgl_count += 1;
-            S->cgl_iters += sh.it;
-        }
+        if (a.timed) S->cgl_iters += sh.it;
     }
-    if (!gradp) return;
 
     // ---- gradient pass at the new x over the CTA's rows (the ring already holds its first
     // stages), then its finish and the loop's decisions
-    phase_mark(a, sh, 4);   // the final stop test and the z/u update count as direction work
-    if constexpr (kGradCapable) {
-        bool gok = grid_sync(a, sh);   // x is complete in every slice
-        if (gok) {
-            gok = fused_grad_pass<P, NCH>(a, sh, smem, full, empty, rps, nst_cap, cs, par);
-            if (gok) gok = grid_sync(a, sh);   // every partial row is written
-        } else if (tid == 0) {
-            *reinterpret_cast<volatile int32_t*>(&sh.stop) = 1;
+    if (gradp) {
+        phase_mark(a, sh, 4);   // the final stop test and the z/u update count as direction work
+        if constexpr (kGradCapable) {
+            bool gok = grid_sync(a, sh);   // x is complete in every slice
+            if (gok) {
+                gok = fused_grad_pass<P, NCH>(a, sh, smem, full, empty, rps, nst_cap, cs, par);
+                if (gok) gok = grid_sync(a, sh);   // every partial row is written
+            }
+            phase_mark(a, sh, 6);
+            if (a.timed && b == 0 && tid == 0) a.S->cgl_fin0 = gtimer();
+            if (gok) grad_finish_phase<VT>(a, sh);
+            phase_mark(a, sh, 7);
         }
-        phase_mark(a, sh, 6);
-        if (gok) grad_finish_phase<VT>(a, sh);
-        phase_mark(a, sh, 7);
     }
+    if (tid == 0) *reinterpret_cast<volatile int32_t*>(&sh.stop) = 1;   // the producer leaves
     if (b == 0 && tid == 0 && a.timed) {
         S->cgl_ns += (double)(gtimer() - sh.t_start);
         S->cgl_count += 1;
-        S->cgl_iters += sh.it;
     }
 }
 

@@ -82,9 +82,16 @@ GENIOS_DEV void loop_phase_a(DevLoop* L, const DevState* S) {
     }
 }
 
+// k^gamma of iteration k's CG tolerance: from the host's table (a float64 pow on this part costs
+// microseconds of one thread's time, on the critical path of every iteration), else pow.
+GENIOS_DEV double loop_kpow(const DevLoop* L, int k) {
+    return k >= 0 && k < L->kpow_len ? __ldcg(L->kpow + k) : pow((double)k, L->gamma);
+}
+
 // Phase b, after the KKT pass when one was due (thread 0 of kkt_finish's last block), else right
 // after phase a: the KKT stop test, the penalty update of §2.5 and the CG tolerance of §2.1.
-GENIOS_DEV void loop_phase_b(DevLoop* L, const DevState* S) {
+// kpow_k: loop_kpow(L, k) for the k of this phase (read ahead by the caller to hide its latency).
+GENIOS_DEV void loop_phase_b(DevLoop* L, const DevState* S, double kpow_k) {
     if (L->stop) return;
     const int k = L->k;
     if (!L->skip_kkt) {   // relative KKT at z (reading R6)
@@ -113,7 +120,7 @@ GENIOS_DEV void loop_phase_b(DevLoop* L, const DevState* S) {
     L->u_scale = u_scale;
     L->nu = rho + L->lam2 + L->sigma;
     // CG tolerance (§2.1)
-    double tol = k <= 1 ? L->cg_first : fmin(sqrt(L->last_rp * L->last_rd), 1.0) / pow((double)k, L->gamma);
+    double tol = k <= 1 ? L->cg_first : fmin(sqrt(L->last_rp * L->last_rd), 1.0) / kpow_k;
     L->tol = fmax(tol, L->cg_floor);
     // graph form: no gradient pass after the last x-step; leave the loop before an x-step whose
     // re-sketch (§2.2, every resketch_every iterations) the host runs
@@ -121,6 +128,56 @@ GENIOS_DEV void loop_phase_b(DevLoop* L, const DevState* S) {
     const bool sketch_due = L->use_pc && !L->quadratic && L->resketch_every > 0 && k > 1 &&
                             (k - 1) % L->resketch_every == 0;
     L->cont = sketch_due ? 0 : 1;
+}
+
+// The sum (or max) over cnt entries src[0], src[stride], ... by one warp: lane l takes entries
+// l, l + 32, ... in order (loads issued eight at a time), then a butterfly; valid in every lane.
+// One short chain per warp and total: float64 runs at a small fraction of the float32 rate on
+// this part, and a finishing kernel sits on the critical path of its ADMM iteration.
+GENIOS_DEV double warp_total(const double* src, int cnt, int stride, bool is_max) {
+    const int lane = threadIdx.x & 31;
+    double acc = is_max ? -1e300 : 0.0;
+    for (int b0 = lane; b0 < cnt; b0 += 256) {
+        double w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) w[u] = b0 + 32 * u < cnt ? __ldcg(src + (size_t)(b0 + 32 * u) * stride) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (b0 + 32 * u < cnt) acc = is_max ? fmax(acc, w[u]) : acc + w[u];
+    }
+    return is_max ? warp_max(acc) : warp_sum(acc);
+}
+
+// Bytes of the state's scalar head (everything before the preconditioner vectors), which holds
+// the loop state and every value its decisions read.
+constexpr size_t kStateHeadBytes = offsetof(DevState, w);
+static_assert(kStateHeadBytes % 8 == 0 && offsetof(DevState, loop) % 8 == 0 && sizeof(DevLoop) % 8 == 0,
+              "the state head is copied in 8-byte words");
+
+// The loop's decisions taken on a shared-memory copy of the state's head: the threads 0 .. nthr-1
+// of a block read the head with one parallel load (from the L2: other blocks wrote parts of it),
+// thread 0 writes the finishing kernel's own results into the copy (fill), takes the decisions
+// (decide, on the copy's DevLoop and values), and the threads write the DevLoop back.  One thread
+// deciding on global memory walked a chain of dependent L2 round trips, one per field it read
+// after a store (about 15 us per ADMM iteration).  bar: a barrier over the nthr threads; buf:
+// kStateHeadBytes of shared memory, 8-byte aligned.  Only the DevLoop is written back: the other
+// fields of the head may be updated by other blocks meanwhile (timers).
+template <class Bar, class Fill, class Decide>
+GENIOS_DEV void loop_decide_shared(DevState* S, unsigned long long* buf, int tid, int nthr, Bar bar, Fill fill,
+                                   Decide decide) {
+    constexpr int nw = (int)(kStateHeadBytes / 8);
+    constexpr int l0 = (int)(offsetof(DevState, loop) / 8), lw = (int)(sizeof(DevLoop) / 8);
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(S);
+    for (int i = tid; i < nw; i += nthr) buf[i] = __ldcg(src + i);
+    bar();
+    if (tid == 0) {
+        DevState* Ss = reinterpret_cast<DevState*>(buf);
+        fill(Ss);
+        decide(&Ss->loop, Ss);
+    }
+    bar();
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(S);
+    for (int i = tid; i < lw; i += nthr) dst[l0 + i] = buf[l0 + i];
 }
 
 }  // namespace genios

@@ -88,7 +88,7 @@ struct genios_ctx {
     int loss = 0;
     int64_t m = 0, n = 0;
     int prec = P_FP32;   // Hv storage precision
-    int gprec = P_FP32;  // gradient-pass storage precision (P_FP64 or P_FP32; BF16 / FP8 modes keep the float32 A)
+    int gprec = P_FP32;  // gradient-pass storage precision (P_FP64, P_FP32, or P_HILO for wide BF16 / FP8 rows)
     bool dbl = false;
     size_t vt = 4;
     int64_t lda = 0, lda_g = 0, ldp = 0;
@@ -109,6 +109,11 @@ struct genios_ctx {
     void* U = nullptr;
     double* lam = nullptr;
     void* nyswork = nullptr;
+    // k^gamma, k < kpow_len, for the device-side loop's CG tolerance (computed here with the host
+    // loop's pow)
+    double* kpow = nullptr;
+    int kpow_len = 0;
+    double kpow_gamma = NAN;
     CgvPlan cgv{};              // cluster CG vector kernel
     CgLoopPlan cgl{};           // persistent CG kernel (ok = false: per-iteration kernels)
     void* tcbuf = nullptr;      // tensor-core sketch operands (value type float only)
@@ -245,7 +250,7 @@ extern "C" genios_status genios_create(const genios_options* opts, int device, v
     ctx->prec = o.precision;
     ctx->dbl = (o.precision == GENIOS_FP64);
     ctx->vt = ctx->dbl ? 8 : 4;
-    ctx->gprec = o.precision == GENIOS_FP64 ? P_FP64 : P_FP32;   // BF16 / FP8: the float32 A
+    ctx->gprec = o.precision == GENIOS_FP64 ? P_FP64 : P_FP32;   // BF16 / FP8: set by set_data
     if (cudaMalloc(&ctx->S, sizeof(DevState)) != cudaSuccess ||
         cudaMallocHost(&ctx->Sh, sizeof(DevState)) != cudaSuccess ||
         cudaMalloc(&ctx->sc.part, 262144 * sizeof(double)) != cudaSuccess ||
@@ -289,6 +294,7 @@ extern "C" void genios_destroy(genios_ctx* ctx) {
     if (ctx->sc.part) cudaFree(ctx->sc.part);
     if (ctx->sc.counter) cudaFree(ctx->sc.counter);
     if (ctx->dbg) cudaFree(ctx->dbg);
+    if (ctx->kpow) cudaFree(ctx->kpow);
     cudaGetLastError();
     delete ctx;
 }
@@ -387,6 +393,7 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
     ctx->loop_graph = nullptr;
     ctx->loop_graph_sk = -1;
     ctx->mem.free_all();
+    ctx->A_glo = nullptr;   // set again only where the gradient keeps the hi + lo split
     ctx->has_data = false;
     ctx->solved = false;
     ctx->have_precond = false;
@@ -431,10 +438,24 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
             CK(tc_setup(ctx, P_FP32, A32, ld32, nullptr, M, N));
         } else {
             // The gradient streams the float32 matrix itself (the problem's own A, and the
-            // cheapest row pass to decode); the Hessian streams the quantised copy
-            ctx->A_g = A32;
-            ctx->lda_g = ld32;
-            if (ctx->prec == GENIOS_BF16) {
+            // cheapest row pass to decode) and the Hessian the quantised copy.  Rows too wide
+            // for the float32 row pass (n > 20480) keep the bfloat16 hi + lo split of A for the
+            // gradient instead (the same 4 bytes per element, in two 2-byte planes).
+            const bool g32 = rowpass_plan(P_FP32, M, N, ld32).ok;
+            ctx->gprec = g32 ? P_FP32 : P_HILO;
+            if (g32) {
+                ctx->A_g = A32;
+                ctx->lda_g = ld32;
+            } else {
+                ctx->lda_g = padded_lda(P_BF16, N);
+                CK(ctx->mem.get(&ctx->A_g, (size_t)M * ctx->lda_g * 2));
+                CK(ctx->mem.get(&ctx->A_glo, (size_t)M * ctx->lda_g * 2));
+                CK(quantize_bf16_hilo(M, N, A32, ld32, ctx->A_g, ctx->A_glo, ctx->lda_g, s));
+            }
+            if (ctx->prec == GENIOS_BF16 && !g32) {
+                ctx->A_hv = ctx->A_g;   // the hi plane is the BF16 copy
+                ctx->lda = ctx->lda_g;
+            } else if (ctx->prec == GENIOS_BF16) {
                 ctx->lda = padded_lda(P_BF16, N);
                 void* lo = nullptr;   // the low half of the split is not kept
                 CK(ctx->mem.get(&ctx->A_hv, (size_t)M * ctx->lda * 2));
@@ -450,6 +471,10 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
                                      ctx->lda, s));
             }
             CK(tc_setup(ctx, P_FP32, A32, ld32, nullptr, M, N));
+            if (!g32) {   // the float32 copy has served the quantisation and the sketch operands
+                CK(cudaStreamSynchronize(s));
+                ctx->mem.release(A32);
+            }
         }
     }
     // b in the value type
@@ -1081,6 +1106,22 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
         L.eps_rel = o.eps_rel;
         L.eps_kkt = o.eps_kkt;
         L.gamma = o.gamma;
+        {   // the table of k^gamma, k <= max_iter + 1
+            const int len = (int)std::min<int64_t>((int64_t)o.max_iter + 2, 1 << 22);
+            if (ctx->kpow_len < len || !(ctx->kpow_gamma == o.gamma)) {
+                if (ctx->kpow) cudaFree(ctx->kpow);
+                ctx->kpow = nullptr;
+                ctx->kpow_len = 0;
+                CK(cudaMalloc(&ctx->kpow, (size_t)len * sizeof(double)));
+                std::vector<double> kp((size_t)len);
+                for (int k = 0; k < len; ++k) kp[k] = std::pow((double)k, o.gamma);
+                CK(cudaMemcpy(ctx->kpow, kp.data(), (size_t)len * sizeof(double), cudaMemcpyHostToDevice));
+                ctx->kpow_len = len;
+                ctx->kpow_gamma = o.gamma;
+            }
+            L.kpow = ctx->kpow;
+            L.kpow_len = ctx->kpow_len;
+        }
         L.cg_first = o.cg_tol_first;
         L.cg_floor = floor;
         L.rho_tau = o.rho_tau;
@@ -1145,6 +1186,8 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
                     st = build_loop_graph(ctx, dvec, sk_now);
                     if (st != GENIOS_OK) return st;
                 }
+                // the launch gaps are counted within one run of the loop (not across the host's work)
+                CK(cudaMemsetAsync(&ctx->S->cgl_last_end, 0, sizeof(unsigned long long), s));
                 CK(cudaGraphLaunch(ctx->loop_exec, s));
             }
             {
@@ -1189,6 +1232,7 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
                     if (st != GENIOS_OK) return st;
                     inf.sketches++;
                     since = 0;
+                    CK(cudaMemsetAsync(&ctx->S->cgl_last_end, 0, sizeof(unsigned long long), s));
                 }
             }
             // x-step (§2.1) and z/u update (Eq. (5)) in one persistent launch, parameters from Ld
@@ -1460,6 +1504,9 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
     inf.cg_ms = o.profile ? cg_ev_ms : ctx->Sh->cgl_ns * 1e-6;
     for (int k = 0; k < 6; ++k) inf.cg_phase_ms[k] = ctx->Sh->cgl_phase_ns[k] * 1e-6;
     for (int k = 0; k < 2; ++k) inf.fused_phase_ms[k] = ctx->Sh->cgl_phase_ns[6 + k] * 1e-6;
+    inf.cg_span_ms = ctx->Sh->cgl_span_ns * 1e-6;
+    inf.cg_gap_ms = ctx->Sh->cgl_gap_ns * 1e-6;
+    for (int k = 0; k < 4; ++k) inf.cg_tail_ms[k] = ctx->Sh->cgl_tail_ns[k] * 1e-6;
     {
         const size_t es = ctx->prec == GENIOS_FP64 ? 8 : ctx->prec == GENIOS_FP32 ? 4
                           : ctx->prec == GENIOS_BF16 ? 2 : 1;

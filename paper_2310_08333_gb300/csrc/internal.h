@@ -23,7 +23,9 @@ namespace genios {
 struct DevLoop {
     // configuration
     int32_t max_iter, stop_resid, stop_kkt, kkt_every;
-    int32_t rho_every, rho_max, rho_until, pad0;
+    int32_t rho_every, rho_max, rho_until, kpow_len;
+    const double* kpow;  // kpow[k] = k^gamma for k < kpow_len (the host's pow: the CG tolerance's
+                         // divisor, the same value in the host and device loops)
     double eps_abs, eps_rel, eps_kkt, gamma, cg_first, cg_floor;
     double rho_tau, rho_mu, sigma, lam1, lam2, sqn;
     // state
@@ -94,6 +96,11 @@ struct DevState {
                                     // direction, barrier; the fused gradient pass (from the
                                     // barrier after the z/u update to the one after the pass's
                                     // partial rows) and the finish
+    unsigned long long cgl_t0;      // CTA 0's first instruction in the current launch (ns)
+    unsigned long long cgl_last_end;// the last CTA's end of the previous fused launch (0: none)
+    double cgl_span_ns, cgl_gap_ns; // sums of (last end - cgl_t0) and of (cgl_t0 - previous end)
+    unsigned long long cgl_fin0;    // start of the current finish (CTA 0, after the pass barrier)
+    double cgl_tail_ns[4];          // the last CTA's finish: arrival, reductions, decisions, conditionals
     DevLoop loop;                   // device-side ADMM loop (device_loop = 1)
     double w[256];    // U^T r (Nystrom preconditioner), s <= 256 (op-level preconditioner)
     double cgc[128];  // preconditioner coefficients c_i w_i for the next direction

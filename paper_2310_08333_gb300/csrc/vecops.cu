@@ -202,11 +202,13 @@ __global__ void grad_finish_kernel(const VT* P, int G, int64_t ldp, const double
                                    double lam1, VT* g, DevState* S, Scratch sc, DevLoop* loop,
                                    cudaGraphConditionalHandle kkt_cond, cudaGraphConditionalHandle loop_cond,
                                    int use_cond) {
+    double kpow_next = 0.0;   // k^gamma for phase b (phase a makes this iteration k + 1), read early
     if (loop != nullptr) {   // device-side loop: nothing to do once it halted (uniform across the grid)
         if (loop->halt) return;
         rho = loop->rho;
         mu = loop->lam2;
         lam1 = loop->lam1;
+        if (threadIdx.x == 0) kpow_next = loop_kpow(loop, loop->k + 1);
     }
     __shared__ double sh[8 * 33];
     const int64_t j = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
@@ -235,24 +237,35 @@ __global__ void grad_finish_kernel(const VT* P, int G, int64_t ldp, const double
         double ls[1] = {0.0};
         for (int b = threadIdx.x; b < G; b += blockDim.x) ls[0] += loss_part[b];
         block_sum<1>(ls);
-        if (threadIdx.x == 0) {
-            S->loss_sum = ls[0];
-            S->rd2 = out[0];
-            S->rhou2 = out[1];
-            S->g2 = out[2];
-            S->excess2 = out[3];
-            S->gx1 = out[4];
-            S->gx2 = out[5];
-            S->atw_inf = outm[0];
-            if (loop != nullptr) {
-                loop_phase_a(loop, S);
-                if (loop->skip_kkt) loop_phase_b(loop, S);
-                if (use_cond) {
-                    cudaGraphSetConditional(kkt_cond, loop->skip_kkt ? 0u : 1u);
-                    if (loop->skip_kkt) cudaGraphSetConditional(loop_cond, loop->cont ? 1u : 0u);
-                }
-            }
+        auto fill = [&](DevState* T) {
+            T->loss_sum = ls[0];
+            T->rd2 = out[0];
+            T->rhou2 = out[1];
+            T->g2 = out[2];
+            T->excess2 = out[3];
+            T->gx1 = out[4];
+            T->gx2 = out[5];
+            T->atw_inf = outm[0];
+        };
+        if (loop == nullptr) {
+            if (threadIdx.x == 0) fill(S);
+            return;
         }
+        __shared__ unsigned long long head[kStateHeadBytes / 8];
+        loop_decide_shared(
+            S, head, threadIdx.x, blockDim.x, [] { __syncthreads(); },
+            [&](DevState* Ss) {
+                fill(Ss);
+                fill(S);
+            },
+            [&](DevLoop* Lc, DevState* Ss) {
+                loop_phase_a(Lc, Ss);
+                if (Lc->skip_kkt) loop_phase_b(Lc, Ss, kpow_next);
+                if (use_cond) {
+                    cudaGraphSetConditional(kkt_cond, Lc->skip_kkt ? 0u : 1u);
+                    if (Lc->skip_kkt) cudaGraphSetConditional(loop_cond, Lc->cont ? 1u : 0u);
+                }
+            });
     }
 }
 
@@ -261,10 +274,12 @@ __global__ void kkt_finish_kernel(const VT* P, int G, int64_t ldp, int64_t n, co
                                   double mu, double lam1, DevState* S, Scratch sc, int box, double lo,
                                   double hi, DevLoop* loop, cudaGraphConditionalHandle loop_cond,
                                   int use_cond) {
+    double kpow_k = 0.0;   // k^gamma for phase b, read early
     if (loop != nullptr) {
         if (loop->skip_kkt) return;   // no check due (uniform across the grid)
         mu = loop->lam2;
         lam1 = loop->lam1;
+        if (threadIdx.x == 0) kpow_k = loop_kpow(loop, loop->k);
     }
     __shared__ double sh[8 * 33];
     const int64_t j = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
@@ -286,17 +301,55 @@ __global__ void kkt_finish_kernel(const VT* P, int G, int64_t ldp, int64_t n, co
         v[1] = gj * gj;
         mx[0] = d;
     }
-    double out[2], outm[1];
-    if (grid_sum_max<2, 1>(v, mx, sc.part, sc.counter, out, outm)) {
+    // the block's butterfly sums (warp 0 holds its 32 columns), then in the last block to finish
+    // one warp per total over the blocks (warp_total)
+    __shared__ unsigned s_last;
+    __shared__ double tot[3];
+    if ((threadIdx.x >> 5) == 0) {
+        v[0] = warp_sum(v[0]);
+        v[1] = warp_sum(v[1]);
+        mx[0] = warp_max(mx[0]);
         if (threadIdx.x == 0) {
-            S->kd2 = out[0];
-            S->kg2 = out[1];
-            S->kdmax = outm[0];
-            if (loop != nullptr) {
-                loop_phase_b(loop, S);
-                if (use_cond) cudaGraphSetConditional(loop_cond, loop->cont ? 1u : 0u);
-            }
+            sc.part[(size_t)blockIdx.x * 4 + 0] = v[0];
+            sc.part[(size_t)blockIdx.x * 4 + 1] = v[1];
+            sc.part[(size_t)blockIdx.x * 4 + 2] = mx[0];
+            __threadfence();
+            s_last = atomicAdd(sc.counter, 1u) == gridDim.x - 1 ? 1u : 0u;
         }
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    {
+        const int wid = threadIdx.x >> 5;
+        if (wid < 3) {
+            const double t = warp_total(sc.part + wid, (int)gridDim.x, 4, wid == 2);
+            if ((threadIdx.x & 31) == 0) tot[wid] = t;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *sc.counter = 0u;
+    {
+        auto fill = [&](DevState* T) {
+            T->kd2 = tot[0];
+            T->kg2 = tot[1];
+            T->kdmax = tot[2];
+        };
+        if (loop == nullptr) {
+            if (threadIdx.x == 0) fill(S);
+            return;
+        }
+        __shared__ unsigned long long head[kStateHeadBytes / 8];
+        loop_decide_shared(
+            S, head, threadIdx.x, blockDim.x, [] { __syncthreads(); },
+            [&](DevState* Ss) {
+                fill(Ss);
+                fill(S);
+            },
+            [&](DevLoop* Lc, DevState* Ss) {
+                loop_phase_b(Lc, Ss, kpow_k);
+                if (use_cond) cudaGraphSetConditional(loop_cond, Lc->cont ? 1u : 0u);
+            });
     }
 }
 

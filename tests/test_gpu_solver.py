@@ -350,6 +350,27 @@ def test_mixed_precision_reaches_kkt_and_reports_error(G, prec):
     assert err <= 5e-2
 
 
+def test_wide_rows_gradient_on_hilo_split(G):
+    """Rows wider than the float32 row pass (n = 22000 > 20480): BF16 mode streams the gradient
+    from the bfloat16 hi + lo split of A instead of the float32 A, and still reaches the stopping
+    tolerance, certified by the oracle's float64 KKT residual at z (to the float32 rounding of the
+    GPU's own evaluation); FP32 refuses the size.  (FP8 takes the same gradient path; on this
+    300 x 22000 problem at rho = 30 its E4M3 Hessian does not let the x-step contract, the
+    failure mode of the mixed modes' proximal-term reading.)"""
+    prec = 2
+    P = problems.logistic_lowrank(300, 22000, nnz=20, sketch_rank=40, seed=problems.seed_for(3, 21))
+    A, b = rounded(P, 1)
+    lam = P.lam_frac * checks.lambda_max(A, b, "logistic")
+    with pytest.raises(G.GeniosError) as e:
+        gpu_solve(G, P, 1, lam, rho=30.0, eps_kkt=1e-4)
+    assert e.value.status == 8             # EUNSUPPORTED
+    z, info, _ = gpu_solve(G, P, prec, lam, rho=30.0, eps_kkt=1e-4)
+    kkt = checks.rel_kkt(A, b, z, "logistic", lam)
+    print(f"precision {prec}, n = 22000: GPU rel KKT {info['rel_kkt']:.3e}, oracle {kkt:.3e}, iters {info['iters']}")
+    assert info["status"] == 0, info
+    assert kkt <= 1.05e-4, kkt
+
+
 def test_config3_full_size_kkt_property(G):
     """Full 20000 x 8000 logistic workload in the benchmark's configuration (FP32, rho = 240 held
     fixed, CG floor 0.8, rank 100 re-sketched every 60 iterations, KKT checks at most 80 apart,
