@@ -18,6 +18,8 @@
 #include "internal.h"
 
 #include <cmath>
+#include <cstdint>
+#include <type_traits>
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -547,12 +549,13 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min,
     const int se = sk + (sk & 1);
     const int half = se / 2;
     const int ld = sk | 1;
+    using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
     T* M = reinterpret_cast<T*>(jsm);                   // s x ld
     T* Vs_ = M + sk * ld;                               // s x ld (VS only)
-    T* cs = VS ? Vs_ + sk * ld : Vs_;                   // half
-    T* sn = cs + half;                                  // half
-    int* pp = reinterpret_cast<int*>(sn + half);        // half
-    int* qq = pp + half;                                // half
+    // the round's rotations, one 8- or 16-byte load each: (c, s) and the pair p | q << 16
+    T2* rot = reinterpret_cast<T2*>(
+        (reinterpret_cast<uintptr_t>(VS ? Vs_ + sk * ld : Vs_) + 15) & ~static_cast<uintptr_t>(15));   // half
+    int* pqs = reinterpret_cast<int*>(rot + half);      // half
     const int vld = VS ? ld : sk;
     T* V = VS ? Vs_ : Vout;
     __shared__ int nrot;
@@ -561,28 +564,34 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min,
         M[i * ld + j] = (T)(0.5 * (Min[i * sk + j] + Min[j * sk + i]));
         V[i * vld + j] = Vinit ? Vinit[e] : ((i == j) ? T(1) : T(0));
     }
-    // this thread's (pair, index) work items, fixed for the whole iteration
-    int wk[JAC_MAX_PER_THREAD], wj[JAC_MAX_PER_THREAD];
+    // this thread's (pair k, row i of V) work items, fixed for the whole iteration, packed as
+    // k | (i * vld) << 16 (one register each: the kernel runs at the 64-register cap)
+    int wkj[JAC_MAX_PER_THREAD];
     int nw = 0;
 #pragma unroll
     for (int r = 0; r < JAC_MAX_PER_THREAD; ++r) {
         const int e = threadIdx.x + r * blockDim.x;
-        wk[r] = 0; wj[r] = 0;
-        if (e < half * sk) { wk[r] = e / sk; wj[r] = e % sk; nw = r + 1; }
+        wkj[r] = 0;
+        if (e < half * sk) { wkj[r] = (e / sk) | (((e % sk) * vld) << 16); nw = r + 1; }
     }
     const T tol = (T)rot_tol;
     const T ctol = (T)sqrt(rot_tol);
+    // float: the tests on squares (no square root) and the rotation from the fast reciprocal,
+    // square root and division: this phase runs in two warps while the other thirty wait at the
+    // barrier, so its latency is each round's; the rotation need not be exact (c^2 + s^2 = 1 to a
+    // few ulp, and the polar step after the sweeps restores V's orthogonality)
+    const float tol2 = (float)(rot_tol * rot_tol), ctol2 = (float)rot_tol;
     // this thread's pair blocks (a, b), b >= a, of the one-pass two-sided update, fixed for the
     // whole iteration (half (half + 1) / 2 <= 2080 blocks for s <= 128)
-    int ba[JAC_MAX_BLK], bbv[JAC_MAX_BLK];
+    int bab[JAC_MAX_BLK];   // a | b << 16
     int nb = 0;
     {
         int a = 0, rem = threadIdx.x;
         while (a < half && rem >= half - a) { rem -= half - a; ++a; }
 #pragma unroll
         for (int r = 0; r < JAC_MAX_BLK; ++r) {
-            ba[r] = 0; bbv[r] = 0;
-            if (a < half) { ba[r] = a; bbv[r] = a + rem; nb = r + 1; }
+            bab[r] = 0;
+            if (a < half) { bab[r] = a | ((a + rem) << 16); nb = r + 1; }
             // advance by blockDim.x blocks
             int step = blockDim.x;
             while (a < half && step > 0) {
@@ -599,25 +608,50 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min,
         __syncthreads();
         for (int round = 0; round < se - 1; ++round) {
             for (int k = threadIdx.x; k < half; k += blockDim.x) {
+                // round-robin pairing: (round + k) and (round - k) mod (se - 1), with se - 1 last
+                const int m1 = se - 1;
                 int p, q;
-                if (k == 0) { p = round; q = se - 1; }
-                else { p = (round + k) % (se - 1); q = (round - k + (se - 1)) % (se - 1); }
+                if (k == 0) { p = round; q = m1; }
+                else {
+                    p = round + k;
+                    if (p >= m1) p -= m1;
+                    q = round - k;
+                    if (q < 0) q += m1;
+                }
                 if (p > q) { int t = p; p = q; q = t; }
                 T c = T(1), s = T(0);
                 if (q < sk) {
                     const T apq = M[p * ld + q];
                     const T app = M[p * ld + p], aqq = M[q * ld + q];
-                    const T scale = sqrt(fabs(app * aqq));
-                    if (apq != T(0) && fabs(apq) > tol * scale) {
-                        if (fabs(apq) > ctol * scale) nrot = 1;   // benign race: writers store 1
-                        const T tau = (aqq - app) / (T(2) * apq);
-                        const T t = tau >= T(0) ? T(1) / (tau + sqrt(T(1) + tau * tau))
-                                                : T(-1) / (-tau + sqrt(T(1) + tau * tau));
-                        c = T(1) / sqrt(T(1) + t * t);
-                        s = t * c;
+                    if constexpr (sizeof(T) == 4) {
+                        const float a2 = apq * apq, pq = fabsf(app * aqq);
+                        if (apq != 0.f && a2 > tol2 * pq) {
+                            if (a2 > ctol2 * pq) nrot = 1;   // benign race: writers store 1
+                            const float tau = __fdividef(aqq - app, 2.f * apq);
+                            const float at = fabsf(tau);
+                            // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), about sign(tau) / (2 |tau|) for huge |tau|
+                            float t = at < 1e18f ? __frcp_rn(at + __fsqrt_rn(fmaf(at, at, 1.f))) : __fdividef(0.5f, at);
+                            t = tau >= 0.f ? t : -t;
+                            c = rsqrtf(fmaf(t, t, 1.f));
+                            s = t * c;
+                        }
+                    } else {
+                        const T scale = sqrt(fabs(app * aqq));
+                        if (apq != T(0) && fabs(apq) > tol * scale) {
+                            if (fabs(apq) > ctol * scale) nrot = 1;   // benign race: writers store 1
+                            const T tau = (aqq - app) / (T(2) * apq);
+                            const T t = tau >= T(0) ? T(1) / (tau + sqrt(T(1) + tau * tau))
+                                                    : T(-1) / (-tau + sqrt(T(1) + tau * tau));
+                            c = T(1) / sqrt(T(1) + t * t);
+                            s = t * c;
+                        }
                     }
                 }
-                cs[k] = c; sn[k] = s; pp[k] = p; qq[k] = q;
+                T2 cr;
+                cr.x = c;
+                cr.y = s;
+                rot[k] = cr;
+                pqs[k] = p | (q << 16);
             }
             __syncthreads();
             // M <- R M R^T in one pass: the 2 x 2 block of rows {p_a, q_a} and columns {p_b, q_b}
@@ -626,11 +660,13 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min,
 #pragma unroll
             for (int r = 0; r < JAC_MAX_BLK; ++r) {
                 if (r >= nb) break;
-                const int a = ba[r], bb = bbv[r];
-                const T sa = sn[a], sb = sn[bb];
+                const int a = bab[r] & 0xffff, bb = bab[r] >> 16;
+                const T2 ra = rot[a], rb = rot[bb];
+                const T sa = ra.y, sb = rb.y;
                 if (sa == T(0) && sb == T(0)) continue;
-                const T ca = cs[a], cb = cs[bb];
-                const int pa = pp[a], qa = qq[a], pb = pp[bb], qb = qq[bb];
+                const T ca = ra.x, cb = rb.x;
+                const int pqa = pqs[a], pqb = pqs[bb];
+                const int pa = pqa & 0xffff, qa = pqa >> 16, pb = pqb & 0xffff, qb = pqb >> 16;
                 const bool qa_ok = qa < sk, qb_ok = qb < sk;
                 const T x00 = M[pa * ld + pb];
                 const T x01 = qb_ok ? M[pa * ld + qb] : T(0);
@@ -656,14 +692,16 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int sk, const double* Min,
 #pragma unroll
             for (int r = 0; r < JAC_MAX_PER_THREAD; ++r) {            // V <- V R^T
                 if (r >= nw) break;
-                const int k = wk[r], i = wj[r];
-                const T sv = sn[k];
+                const int k = wkj[r] & 0xffff, io = wkj[r] >> 16;
+                const T2 rk = rot[k];
+                const T sv = rk.y;
                 if (sv == T(0)) continue;
-                const int p = pp[k], q = qq[k];
-                const T cv = cs[k];
-                const T vp = V[i * vld + p], vq = V[i * vld + q];
-                V[i * vld + p] = cv * vp - sv * vq;
-                V[i * vld + q] = sv * vp + cv * vq;
+                const int pqk = pqs[k];
+                const int p = pqk & 0xffff, q = pqk >> 16;
+                const T cv = rk.x;
+                const T vp = V[io + p], vq = V[io + q];
+                V[io + p] = cv * vp - sv * vq;
+                V[io + q] = sv * vp + cv * vq;
             }
             __syncthreads();
         }
