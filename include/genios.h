@@ -166,6 +166,14 @@ typedef struct genios_options {
                                 plans made for SMs / lanes of the device, largest problems first,
                                 the CG loop as ordinary launches (cooperative launches from several
                                 streams do not overlap); 1: in turn on the context's stream */
+    int32_t autotune;        /* 0 (default): row passes copy A in stages of about 48 KB of rows
+                                (whole barrier groups of rows).  1: genios_set_data times the
+                                Hessian pass over A (the persistent CG kernel's ring: its
+                                shared-memory budget and one CTA per SM) at 1 to 8 barrier groups
+                                of rows per stage (as many as leave room for two stages) and keeps
+                                the fastest for every row pass and the persistent CG kernel of
+                                the data set; the sizes tried and their times are reported in
+                                genios_info (tune_*) */
     int32_t fuse_gradient;   /* 1 (default): in the device-side loop (graph or stream form) with
                                 the persistent CG kernel, and when the gradient reads the same matrix
                                 as the Hessian (FP64, FP32), each launch of that kernel goes on
@@ -215,6 +223,10 @@ typedef struct genios_info {
     double cg_gap_ms;        /* the device time between one such launch's end and the next one's
                                 first instruction, within one run of the device-side loop: launch,
                                 graph-node and kernel set-up overhead */
+    int32_t stage_kb;        /* bytes of rows per copy stage of the Hessian pass in use, in KB */
+    int32_t tune_n;          /* autotune: stage sizes timed (0 without autotune) */
+    int32_t tune_kb[8];      /* autotune: those stage sizes (KB of rows per stage, as planned) */
+    double tune_us[8];       /* autotune: the Hessian pass's time at each (us, mean of 3 launches) */
     double cg_tail_ms[4];    /* the finish of those launches in the last CTA to arrive: from the
                                 previous mark (CTA 0's end of the pass barrier) to its arrival, its
                                 reductions, the loop's decisions, the graph conditionals */

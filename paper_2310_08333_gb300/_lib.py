@@ -43,6 +43,7 @@ class Options(C.Structure):
         ("box_lo", C.c_double), ("box_hi", C.c_double), ("sketch_adaptive", C.c_int32),
         ("sketch_rank_max", C.c_int32), ("sketch_theta", C.c_double), ("device_loop", C.c_int32),
         ("batch_streams", C.c_int32),
+        ("autotune", C.c_int32),
         ("fuse_gradient", C.c_int32),
     ]
 
@@ -59,7 +60,9 @@ class Info(C.Structure):
         ("hv_bytes", C.c_double), ("sketch_rank_used", C.c_int32), ("fused_grad_passes", C.c_int32),
         ("sketch_bound", C.c_double), ("cg_launches", C.c_int64), ("cg_ms", C.c_double),
         ("cg_phase_ms", C.c_double * 6), ("fused_phase_ms", C.c_double * 2),
-        ("cg_span_ms", C.c_double), ("cg_gap_ms", C.c_double), ("cg_tail_ms", C.c_double * 4),
+        ("cg_span_ms", C.c_double), ("cg_gap_ms", C.c_double),
+        ("stage_kb", C.c_int32), ("tune_n", C.c_int32), ("tune_kb", C.c_int32 * 8), ("tune_us", C.c_double * 8),
+        ("cg_tail_ms", C.c_double * 4),
     ]
 
     def as_dict(self) -> dict:

@@ -1042,11 +1042,11 @@ static bool occupancy_nch(int nch, size_t smem) {
     }
 }
 
-CgLoopPlan cgloop_plan(int prec, int64_t m, int64_t n, int64_t lda, int sk) {
+CgLoopPlan cgloop_plan(int prec, int64_t m, int64_t n, int64_t lda, int sk, size_t stage_target) {
     CgLoopPlan cp{};
     cp.ok = false;
     if (prec == P_HILO || sk < 0 || sk > 128) return cp;
-    RowpassPlan p = rowpass_plan(prec, m, n, lda, CGL_SMEM_BUDGET);
+    RowpassPlan p = rowpass_plan(prec, m, n, lda, CGL_SMEM_BUDGET, stage_target);
     if (!p.ok) return cp;
     const int sms = device_sm_count();
     if ((n + sms - 1) / sms > CGL_SLICE_MAX) return cp;

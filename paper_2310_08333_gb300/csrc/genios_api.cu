@@ -114,6 +114,11 @@ struct genios_ctx {
     double* kpow = nullptr;
     int kpow_len = 0;
     double kpow_gamma = NAN;
+    // row passes: bytes of rows per copy stage (0: the planner's default), and the autotuner's table
+    size_t stage_target = 0;
+    int tune_n = 0;
+    int tune_kb[8] = {};
+    double tune_us[8] = {};
     CgvPlan cgv{};              // cluster CG vector kernel
     CgLoopPlan cgl{};           // persistent CG kernel (ok = false: per-iteration kernels)
     void* tcbuf = nullptr;      // tensor-core sketch operands (value type float only)
@@ -212,6 +217,7 @@ extern "C" void genios_default_options(genios_options* o) {
     o->sketch_theta = 10.0;
     o->device_loop = 1;
     o->batch_streams = 8;
+    o->autotune = 0;
     o->fuse_gradient = 1;
 }
 
@@ -371,6 +377,90 @@ static cudaError_t tc_setup(genios_ctx* ctx, int src_prec, const void* A, int64_
     return cudaSuccess;
 }
 
+static cudaError_t hv_pass(genios_ctx* ctx, const void* v, const void* d, const int* skip, bool timed);
+
+// The stage size of the row passes, measured (autotune): the Hessian pass over A with the
+// persistent CG kernel's ring (its shared-memory budget, one CTA per SM) at 1, 2, ..., 8 barrier
+// groups of rows per copy stage (as many as leave room for two stages), one warm-up and three
+// timed launches each (CUDA events on the context's stream); the fastest is kept for the row
+// passes and the persistent CG kernel of the data set.  The vectors are the context's (x = 0, D
+// as allocated): the time of a pass does not depend on them.  Rows of 32 KB and more leave one
+// group per stage, and nothing to choose.
+static genios_status autotune_stages(genios_ctx* ctx, int hvp) {
+    const int64_t M = ctx->m, N = ctx->n;
+    const int64_t es = hvp == P_FP64 ? 8 : hvp == P_FP32 ? 4 : hvp == P_BF16 ? 2 : 1;
+    const int64_t group_bytes = (int64_t)std::max(1, ctx->cgl.rp.rb) * ctx->lda * es;
+    size_t kTargets[8];
+    for (int g = 0; g < 8; ++g) kTargets[g] = (size_t)((g + 1) * group_bytes);
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const RowpassPlan saved = ctx->plan_hv;
+    const int64_t saved_launches = ctx->launches;
+    double best = INFINITY;
+    size_t best_t = 0;
+    int last_rps = -1;
+    cudaError_t e = cudaSuccess;
+    for (size_t t : kTargets) {
+        if (ctx->tune_n >= 8) break;
+        const CgLoopPlan cp = cgloop_plan(hvp, M, N, ctx->lda, ctx->sk_alloc, t);
+        if (!cp.ok || cp.rp.rows_per_stage == last_rps) continue;
+        last_rps = cp.rp.rows_per_stage;
+        // the ring of the persistent kernel in a standalone row pass: its stages and budget, the
+        // row pass's own grid (no CTA without rows)
+        RowpassPlan tp = cp.rp;
+        tp.grid = (int)std::max<int64_t>(1, std::min<int64_t>(cp.rp.grid, (M + tp.rows_per_stage - 1) / tp.rows_per_stage));
+        ctx->plan_hv = tp;
+        e = hv_pass(ctx, ctx->x, ctx->D, nullptr, false);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = hv_pass(ctx, ctx->x, ctx->D, nullptr, false);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        const double us = 1e3 * ms / 3.0;
+        ctx->tune_kb[ctx->tune_n] = (int)((tp.rows_per_stage * ctx->lda * es + 512) / 1024);
+        ctx->tune_us[ctx->tune_n] = us;
+        ctx->tune_n++;
+        if (us < best) {
+            best = us;
+            best_t = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->plan_hv = saved;
+    ctx->launches = saved_launches;
+    CK(e);
+    if (ctx->S && ctx->Sh) {   // a bounded wait that ran out while timing leaves its word set
+        CK(cudaMemcpyAsync(&ctx->Sh->rp_fault, &ctx->S->rp_fault, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (ctx->Sh->rp_fault != 0) {
+            CK(cudaMemsetAsync(&ctx->S->rp_fault, 0, sizeof(int32_t), s));
+            FAIL(GENIOS_ETIMEOUT, "autotune: a bounded device wait of the row pass ran out");
+        }
+    }
+    if (best_t == 0) return GENIOS_OK;
+    // the chosen stage size for every plan of the data set (grids stay within the partial buffer:
+    // the persistent kernel's grid, one CTA per SM, is the largest)
+    ctx->stage_target = best_t;
+    const int gprec = ctx->gprec;
+    ctx->plan_hv = rowpass_plan(hvp, M, N, ctx->lda, 0, best_t);
+    ctx->plan_g = rowpass_plan(gprec, M, N, ctx->lda_g, 0, best_t);
+    ctx->cgl = cgloop_plan(hvp, M, N, ctx->lda, ctx->sk_alloc, best_t);
+    if (!ctx->plan_hv.ok || !ctx->plan_g.ok || !ctx->cgl.ok) {   // cannot happen: each was planned above
+        ctx->stage_target = 0;
+        ctx->plan_hv = rowpass_plan(hvp, M, N, ctx->lda);
+        ctx->plan_g = rowpass_plan(gprec, M, N, ctx->lda_g);
+        ctx->cgl = cgloop_plan(hvp, M, N, ctx->lda, ctx->sk_alloc);
+    }
+    if (ctx->cgl.ok && ctx->A_g == ctx->A_hv && ctx->lda_g == ctx->lda && ctx->gprec == hvp)
+        ctx->plan_g.grid = ctx->cgl.rp.grid;
+    return GENIOS_OK;
+}
+
 static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, const int64_t* n,
                                   const void* const* A, int A_dtype, const int64_t* lda, const void* const* b) {
     if (!m || !n || !A || !lda || !b || !A[0] || !b[0]) FAIL(GENIOS_EINVAL, "NULL argument");
@@ -492,6 +582,8 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
     // plans
     const int hvp = ctx->prec == GENIOS_FP64 ? P_FP64 : ctx->prec == GENIOS_FP32 ? P_FP32
                     : ctx->prec == GENIOS_BF16 ? P_BF16 : P_FP8;
+    ctx->stage_target = 0;
+    ctx->tune_n = 0;
     ctx->plan_hv = rowpass_plan(hvp, M, N, ctx->lda);
     ctx->plan_g = rowpass_plan(ctx->gprec, M, N, ctx->lda_g);
     if (!ctx->plan_hv.ok || !ctx->plan_g.ok)
@@ -519,6 +611,10 @@ static genios_status set_data_one(genios_ctx* ctx, int loss, const int64_t* m, c
     }
     CK(ctx->mem.get(&ctx->D, (size_t)M * vt));
     CK(ctx->mem.get(&ctx->W, (size_t)M * vt));
+    if (ctx->opt.autotune && ctx->cgl.ok) {
+        st = autotune_stages(ctx, hvp);
+        if (st != GENIOS_OK) return st;
+    }
     // Nystrom
     ctx->cgv = cgv_plan(ctx->dbl, N, ctx->sk_alloc);
     if (!ctx->cgv.ok) FAIL(GENIOS_EUNSUPPORTED, "no thread-block cluster configuration for the CG vector kernel");
@@ -1499,6 +1595,16 @@ static genios_status solve_one(genios_ctx* ctx, const double* lambda1, const dou
         inf.hv_launches = ctx->Sh->hv_count;
     }
     inf.sketch_rank_used = ctx->sk;
+    {
+        const RowpassPlan& hp = ctx->cgl.ok ? ctx->cgl.rp : ctx->plan_hv;
+        const int64_t es = ctx->dbl ? 8 : ctx->prec == GENIOS_FP32 ? 4 : ctx->prec == GENIOS_BF16 ? 2 : 1;
+        inf.stage_kb = (int)((hp.rows_per_stage * ctx->lda * es + 512) / 1024);
+        inf.tune_n = ctx->tune_n;
+        for (int k = 0; k < 8; ++k) {
+            inf.tune_kb[k] = k < ctx->tune_n ? ctx->tune_kb[k] : 0;
+            inf.tune_us[k] = k < ctx->tune_n ? ctx->tune_us[k] : 0.0;
+        }
+    }
     inf.sketch_bound = ctx->sketch_bound;
     inf.cg_launches = ctx->Sh->cgl_count;
     inf.cg_ms = o.profile ? cg_ev_ms : ctx->Sh->cgl_ns * 1e-6;

@@ -182,7 +182,9 @@ cudaError_t op_fault_address(int** out);
 // Message returned by genios_last_error(NULL) on this thread.
 void set_last_error(const std::string& msg);
 // smem_budget: bytes of dynamic shared memory for the stage ring (0: the rowpass default)
-RowpassPlan rowpass_plan(int prec, int64_t m, int64_t n, int64_t lda, size_t smem_budget = 0);
+// stage_target: bytes of rows per copy stage (0: the default 48 KB; the stage holds at least one
+// barrier group of rows and at most a CTA's share)
+RowpassPlan rowpass_plan(int prec, int64_t m, int64_t n, int64_t lda, size_t smem_budget = 0, size_t stage_target = 0);
 cudaError_t rowpass_launch(const RowpassArgs& a, const RowpassPlan& p, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
@@ -237,7 +239,7 @@ struct CgLoopArgs {
 };
 // ok = false when the shape does not fit (n > 1024 per SM, s > 128, the split-BF16 stream, or a
 // ring that does not fit one CTA per SM); the caller then uses the per-kernel CG path.
-CgLoopPlan cgloop_plan(int prec, int64_t m, int64_t n, int64_t lda, int sk);
+CgLoopPlan cgloop_plan(int prec, int64_t m, int64_t n, int64_t lda, int sk, size_t stage_target = 0);
 size_t cgloop_part_elems(int grid);
 // byte offset in the partials buffer where the z/u norm partials start
 size_t cgloop_zu_offset_bytes(int grid);

@@ -200,8 +200,9 @@ int device_sm_count() {
     return t_sm_cap > 0 && t_sm_cap < n ? t_sm_cap : n;
 }
 
-RowpassPlan rowpass_plan(int prec, int64_t m, int64_t n, int64_t lda, size_t smem_budget) {
+RowpassPlan rowpass_plan(int prec, int64_t m, int64_t n, int64_t lda, size_t smem_budget, size_t stage_target) {
     const size_t budget = smem_budget > 0 ? smem_budget : RP_SMEM_BUDGET;
+    const int64_t target = (int64_t)(stage_target > 0 ? stage_target : RP_STAGE_TARGET);
     RowpassPlan p{};
     p.ok = false;
     const int64_t es = elem_bytes(prec == P_HILO ? P_BF16 : prec);
@@ -215,7 +216,7 @@ RowpassPlan rowpass_plan(int prec, int64_t m, int64_t n, int64_t lda, size_t sme
     if (nch < 0) return p;
     const int rb = rp_rb(prec, nch);
     const int64_t per_row = row_bytes * (prec == P_HILO ? 2 : 1);
-    int64_t rps = rb * std::max<int64_t>(1, (int64_t)RP_STAGE_TARGET / (rb * per_row));
+    int64_t rps = rb * std::max<int64_t>(1, target / (rb * per_row));
     const int sms = device_sm_count();
     // no stage larger than a CTA's share of rows (rounded up to the barrier group)
     int64_t share = (m + sms - 1) / sms;

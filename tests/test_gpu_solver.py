@@ -375,6 +375,30 @@ def test_wide_rows_gradient_on_hilo_split(G):
     assert kkt <= 1.05e-4, kkt
 
 
+def test_autotune_keeps_the_fastest_stage_and_the_solution(G):
+    """autotune = 1: set_data times the Hessian pass at several copy-stage sizes, reports them, and
+    the plan in use is the fastest of those; the solve then reaches the same tolerance as with the
+    default stage, its z equal to the untuned one within that tolerance (the stage size changes
+    only the order of the row sums within a CTA).  Rows of 1.6 KB: barrier groups of 8 rows
+    (12.8 KB), up to four per stage within a CTA's share of the 4000 rows."""
+    P = problems.logistic_lowrank(4000, 400, nnz=20, sketch_rank=40, seed=problems.seed_for(3, 22))
+    A, b = rounded(P, 1)
+    lam = P.lam_frac * checks.lambda_max(A, b, "logistic")
+    z0, i0, _ = gpu_solve(G, P, 1, lam, rho=30.0, eps_kkt=1e-5)
+    z1, i1, _ = gpu_solve(G, P, 1, lam, rho=30.0, eps_kkt=1e-5, autotune=1)
+    print("stage KB / us:", list(zip(i1["tune_kb"][:i1["tune_n"]], [round(t, 1) for t in i1["tune_us"][:i1["tune_n"]]])),
+          "chosen", i1["stage_kb"], "default", i0["stage_kb"], "iters", i0["iters"], i1["iters"])
+    assert i0["tune_n"] == 0 and i1["tune_n"] >= 2
+    n = i1["tune_n"]
+    best = int(np.argmin(i1["tune_us"][:n]))
+    assert i1["stage_kb"] == i1["tune_kb"][best], (i1["stage_kb"], i1["tune_kb"][:n])
+    assert all(t > 0 for t in i1["tune_us"][:n])
+    assert i1["status"] == i0["status"] == 0
+    assert abs(i1["iters"] - i0["iters"]) <= 0.02 * i0["iters"] + 2
+    assert checks.rel_kkt(A, b, z1, "logistic", lam) <= 1.05e-5
+    assert np.linalg.norm(z1 - z0) <= 1e-3 * np.linalg.norm(z0)
+
+
 def test_config3_full_size_kkt_property(G):
     """Full 20000 x 8000 logistic workload in the benchmark's configuration (FP32, rho = 240 held
     fixed, CG floor 0.8, rank 100 re-sketched every 60 iterations, KKT checks at most 80 apart,
