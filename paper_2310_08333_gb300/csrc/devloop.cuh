@@ -159,7 +159,7 @@ static_assert(kStateHeadBytes % 8 == 0 && offsetof(DevState, loop) % 8 == 0 && s
 // thread 0 writes the finishing kernel's own results into the copy (fill), takes the decisions
 // (decide, on the copy's DevLoop and values), and the threads write the DevLoop back.  One thread
 // deciding on global memory walked a chain of dependent L2 round trips, one per field it read
-// after a store (about 15 us per ADMM iteration).  bar: a barrier over the nthr threads; buf:
+// after a store (about 2 us more per ADMM iteration).  bar: a barrier over the nthr threads; buf:
 // kStateHeadBytes of shared memory, 8-byte aligned.  Only the DevLoop is written back: the other
 // fields of the head may be updated by other blocks meanwhile (timers).
 template <class Bar, class Fill, class Decide>
